@@ -1,0 +1,290 @@
+"""Seeded synthetic workloads for the CC-MSAV vesicle step.
+
+This module only builds inputs: the parameter sets of the paper's parameter
+table (Appendix G, Table "Parameter values used in benchmark simulations")
+and seeded diffuse-interface initial states.  It holds none of the scheme's
+arithmetic, so both the CUDA path's tests/benchmark and the CPU oracle can
+take their inputs from here without sharing any of the method.
+
+Conventions
+-----------
+* Fields are ``float64`` arrays of shape ``(N, N)``, row-major, ``a[j, i]``
+  with ``j`` the y index and ``i`` the x index.  Cell ``(i, j)`` has its
+  centre at ``((i + 1/2) h, (j + 1/2) h)`` with ``h = L / N``.
+* The phase field of one vesicle is ``tanh((R(theta) - r) / (sqrt(2) eps))``
+  (+1 inside, -1 outside).  Several vesicles are united by a pointwise max.
+* The concentration follows the paper's benchmark profiles (Sec. 4.2):
+  ``psi0 = -0.35 phi0 + 0.45`` for growth and ``psi0 = -0.1 phi0 + 0.7`` for
+  shrinkage, i.e. 0.8 outside and 0.1 (growth) or 0.6 (shrinkage) inside.
+  A workload's concentration ratio ``r`` labels each vesicle: ``r >= 1`` is
+  a growing vesicle, ``r < 1`` a shrinking one.  With several vesicles,
+  ``psi0 = 0.8 + sum_k (inside_k - 0.8) (1 + phi_k) / 2``.
+* The random draws use ``numpy.random.Generator(PCG64(seed))`` in a fixed
+  order, so a (workload, seed) pair always gives the same arrays.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import List, Optional, Sequence
+
+import numpy as np
+
+__all__ = [
+    "Params", "growth_params", "shrinkage_params", "Workload",
+    "vesicle_phi", "concentration", "workload", "WORKLOADS",
+]
+
+
+@dataclasses.dataclass
+class Params:
+    """Model and scheme parameters (names follow the paper's symbols).
+
+    The defaults are the growth column of the paper's parameter table
+    (Appendix G); ``L`` is the side of the square domain (the paper does not
+    state it; the workloads below use ``2 pi``) and ``eps`` is usually set to
+    ``4 h``.
+    """
+    gamma_surf: float = 1.0
+    gamma_bend: float = 0.05
+    gamma_area: float = 5.0e4
+    gamma_in: float = 1.0e5
+    gamma_out: float = 1.0e5
+    psi_in: float = 0.65
+    psi_out: float = 0.8
+    beta_in: float = 0.0
+    beta_out: float = 0.0
+    eps: float = 0.03125
+    M_phi: float = 1.0
+    M0: float = 0.5
+    theta: float = 1.5
+    beta: float = 0.0
+    lam: float = 1.0e5
+    dt: float = 1.0e-6
+    L: float = 1.0
+
+    def replace(self, **kw) -> "Params":
+        return dataclasses.replace(self, **kw)
+
+    def as_tuple(self):
+        return dataclasses.astuple(self)
+
+
+def growth_params(**kw) -> Params:
+    """Growth column of the parameter table (gamma_bend = 0.05, psi_in = 0.65)."""
+    return Params(**kw)
+
+
+def shrinkage_params(**kw) -> Params:
+    """Shrinkage column of the parameter table (gamma_bend = 1, psi_in = 0.1)."""
+    base = dict(gamma_bend=1.0, psi_in=0.1)
+    base.update(kw)
+    return Params(**base)
+
+
+def _cell_centres(N: int, L: float):
+    h = L / N
+    c = (np.arange(N, dtype=np.float64) + 0.5) * h
+    X, Y = np.meshgrid(c, c, indexing="xy")   # X[j, i] = x_i, Y[j, i] = y_j
+    return X, Y
+
+
+def vesicle_phi(N: int, L: float, eps: float, centre, radius_fn) -> np.ndarray:
+    """``tanh((R(theta) - r) / (sqrt 2 eps))`` around ``centre``.
+
+    ``radius_fn`` maps the polar angle array to the boundary radius R(theta).
+    """
+    X, Y = _cell_centres(N, L)
+    dx, dy = X - centre[0], Y - centre[1]
+    r = np.hypot(dx, dy)
+    th = np.arctan2(dy, dx)
+    return np.tanh((radius_fn(th) - r) / (math.sqrt(2.0) * eps))
+
+
+PSI_OUTSIDE = 0.8          # outside value of both benchmark profiles
+PSI_INSIDE_GROWTH = 0.1    # -0.35 * 1 + 0.45
+PSI_INSIDE_SHRINK = 0.6    # -0.1 * 1 + 0.7
+
+
+def concentration(phis: Sequence[np.ndarray], ratios: Sequence[float]) -> np.ndarray:
+    """``0.8 + sum_k (inside_k - 0.8)(1 + phi_k)/2`` with ``inside_k`` the
+    benchmark growth (0.1) or shrinkage (0.6) inside value chosen by the
+    ratio label of vesicle ``k``."""
+    psi = np.full_like(phis[0], PSI_OUTSIDE)
+    for ph, r in zip(phis, ratios):
+        inside = PSI_INSIDE_GROWTH if r >= 1.0 else PSI_INSIDE_SHRINK
+        psi = psi + (inside - PSI_OUTSIDE) * (1.0 + ph) / 2.0
+    return psi
+
+
+def _perturbed(R0: float, amps, phases):
+    amps = np.asarray(amps, dtype=np.float64)
+    phases = np.asarray(phases, dtype=np.float64)
+    ms = np.arange(2, 2 + len(amps))
+
+    def fn(th):
+        s = np.ones_like(th)
+        for m, a, p in zip(ms, amps, phases):
+            s = s + a * np.cos(m * th + p)
+        return R0 * s
+    return fn
+
+
+@dataclasses.dataclass
+class Workload:
+    """One simulation: its parameters, initial state and run length."""
+    name: str
+    N: int
+    params: Params
+    phi0: np.ndarray
+    psi0: np.ndarray
+    steps: int
+    precision: str          # "fp64" or "fp32"
+
+    @property
+    def points(self) -> int:
+        return self.N * self.N
+
+
+def _params_for(ratios, N, L, dt, **kw) -> Params:
+    # Growth column when any vesicle grows (ratio >= 1), shrinkage otherwise.
+    grows = any(r >= 1.0 for r in ratios)
+    mk = growth_params if grows else shrinkage_params
+    return mk(eps=4.0 * L / N, dt=dt, L=L, **kw)
+
+
+def one_vesicle_circle(N: int = 64, seed: int = 1001, dt: float = 1e-4,
+                       steps: int = 200, ratio: float = 1.2,
+                       precision: str = "fp64", L: float = 2 * math.pi,
+                       R0: float = math.pi / 3, name: str = "one_vesicle") -> Workload:
+    """Perturbed circle: R(theta) = R0 (1 + sum_{m=2..6} a_m cos(m theta + p_m)),
+    a_m ~ U(0, 0.03), p_m ~ U(0, 2 pi), centred in the domain."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    amps = rng.uniform(0.0, 0.03, 5)
+    phases = rng.uniform(0.0, 2 * math.pi, 5)
+    p = _params_for([ratio], N, L, dt)
+    phi = vesicle_phi(N, L, p.eps, (L / 2, L / 2), _perturbed(R0, amps, phases))
+    psi = concentration([phi], [ratio])
+    return Workload(name, N, p, phi, psi, steps, precision)
+
+
+def ellipse_shrink(N: int = 512, seed: int = 1002, dt: float = 1e-5,
+                   steps: int = 1000, ratio: float = 0.8,
+                   precision: str = "fp64", L: float = 2 * math.pi) -> Workload:
+    """Ellipse with semi-axes 0.9 pi/2 and 0.6 pi/2 whose polar radius is
+    scaled by (1 + sum_{m=2..8} a_m cos(m theta + p_m)), a_m ~ U(0, 0.02)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    amps = rng.uniform(0.0, 0.02, 7)
+    phases = rng.uniform(0.0, 2 * math.pi, 7)
+    a, b = 0.9 * math.pi / 2, 0.6 * math.pi / 2
+    pert = _perturbed(1.0, amps, phases)
+
+    def radius(th):
+        return a * b / np.sqrt((b * np.cos(th)) ** 2 + (a * np.sin(th)) ** 2) * pert(th)
+
+    p = _params_for([ratio], N, L, dt)
+    phi = vesicle_phi(N, L, p.eps, (L / 2, L / 2), radius)
+    psi = concentration([phi], [ratio])
+    return Workload("ellipse_shrink", N, p, phi, psi, steps, precision)
+
+
+def _place(rng, n, rmin, rmax, L, gap, margin_extra, max_tries=100000):
+    placed = []
+    tries = 0
+    while len(placed) < n:
+        tries += 1
+        if tries > max_tries:
+            raise RuntimeError("could not place vesicles without overlap")
+        R = rng.uniform(rmin, rmax)
+        m = R * 1.15 + margin_extra
+        if 2 * m >= L:
+            continue
+        cx, cy = rng.uniform(m, L - m, 2)
+        ok = all(math.hypot(cx - x, cy - y) >= R * 1.15 + r * 1.15 + gap
+                 for (x, y, r) in placed)
+        if ok:
+            placed.append((cx, cy, R))
+    return placed
+
+
+def three_vesicles(N: int = 2048, seed: int = 1003, dt: float = 1e-5,
+                   steps: int = 1000, ratio: float = 1.3,
+                   precision: str = "fp32", L: float = 2 * math.pi) -> Workload:
+    """Three perturbed circles, R ~ U(0.5, 1.0), centres by rejection sampling
+    (gap >= 8 eps between perturbed outlines, wall margin >= R + 8 eps)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    eps = 4.0 * L / N
+    placed = _place(rng, 3, 0.5, 1.0, L, 8 * eps, 8 * eps)
+    phis = []
+    for (cx, cy, R) in placed:
+        amps = rng.uniform(0.0, 0.03, 5)
+        phases = rng.uniform(0.0, 2 * math.pi, 5)
+        phis.append(vesicle_phi(N, L, eps, (cx, cy), _perturbed(R, amps, phases)))
+    phi = np.maximum.reduce(phis)
+    psi = concentration(phis, [ratio] * 3)
+    p = _params_for([ratio], N, L, dt)
+    return Workload(f"three_vesicles_N{N}", N, p, phi, psi, steps, precision)
+
+
+def lattice_16(N: int = 8192, seed: int = 1005, dt: float = 5e-6,
+               steps: int = 200, precision: str = "fp32",
+               L: float = 2 * math.pi) -> Workload:
+    """16 perturbed circles, R ~ U(0.2, 0.4), on a jittered 4 x 4 lattice with
+    concentration ratios alternating 0.8 / 1.25."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    eps = 4.0 * L / N
+    cell = L / 4
+    phis, ratios = [], []
+    for k in range(16):
+        gx, gy = k % 4, k // 4
+        R = rng.uniform(0.2, 0.4)
+        jit = (cell / 2 - R * 1.15 - 4 * eps)
+        jx, jy = rng.uniform(-jit, jit, 2) if jit > 0 else (0.0, 0.0)
+        cx, cy = (gx + 0.5) * cell + jx, (gy + 0.5) * cell + jy
+        amps = rng.uniform(0.0, 0.03, 5)
+        phases = rng.uniform(0.0, 2 * math.pi, 5)
+        phis.append(vesicle_phi(N, L, eps, (cx, cy), _perturbed(R, amps, phases)))
+        ratios.append(0.8 if k % 2 == 0 else 1.25)
+    phi = np.maximum.reduce(phis)
+    psi = concentration(phis, ratios)
+    p = _params_for(ratios, N, L, dt)
+    return Workload(f"lattice16_N{N}", N, p, phi, psi, steps, precision)
+
+
+def batch_64(seed: int = 1004, n_sims: int = 64, steps: int = 500,
+             dt: float = 1e-5, sizes=(128, 256, 512),
+             L: float = 2 * math.pi) -> List[Workload]:
+    """64 independent single-vesicle simulations with N drawn from ``sizes``,
+    concentration ratio ~ U(0.7, 1.4), eps = 4 h each."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    out = []
+    for s in range(n_sims):
+        N = int(rng.choice(np.asarray(sizes)))
+        ratio = float(rng.uniform(0.7, 1.4))
+        sub = int(rng.integers(0, 2 ** 31 - 1))
+        w = one_vesicle_circle(N=N, seed=sub, dt=dt, steps=steps, ratio=ratio,
+                               precision="fp32", L=L, name=f"batch{s}_N{N}")
+        out.append(w)
+    return out
+
+
+WORKLOADS = {
+    "one_vesicle_N64": lambda: one_vesicle_circle(),
+    "ellipse_shrink_N512": lambda: ellipse_shrink(),
+    "three_vesicles_N2048": lambda: three_vesicles(N=2048),
+    "three_vesicles_N4096": lambda: three_vesicles(N=4096),
+    "lattice16_N8192": lambda: lattice_16(),
+}
+
+
+def workload(name: str, N: Optional[int] = None, **kw) -> Workload:
+    """Build a named workload; ``N`` (and other keywords) override its size."""
+    if name.startswith("one_vesicle"):
+        return one_vesicle_circle(N=N or 64, **kw)
+    if name.startswith("ellipse_shrink"):
+        return ellipse_shrink(N=N or 512, **kw)
+    if name.startswith("three_vesicles"):
+        return three_vesicles(N=N or 2048, **kw)
+    if name.startswith("lattice16"):
+        return lattice_16(N=N or 8192, **kw)
+    raise KeyError(name)
