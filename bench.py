@@ -1,0 +1,365 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the CC-MSAV time step on GB300.
+
+Workload: three seeded perturbed-circle vesicles on an N = 2048 grid
+(FP32-bulk precision, dt = 1e-5), the configuration the throughput metric is
+quoted on.  A "step" is one full CC-MSAV time step over the grid.  The
+metric is grid-point-steps per second (N^2 per step), whole job over all
+ranks.  Prints one JSON line (rank 0).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+With torchrun (N > 1) every rank advances its own independent simulation
+(replicas: the step has no data exchange between GPUs); the time is the
+maximum over ranks.  ``--impl reference`` times the CPU FP64 oracle on the
+host cores instead (rank 0 only), on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK_GBS = 6800.0
+PASSES = {  # algorithmic field passes (reads + writes of N x N fields) per launch
+    "k_stencil": 12, "k_rowdct_T": 16, "k_coldct_gram": 15, "k_solve": 0,
+    "k_comb_icolT": 9, "k_irow": 4,
+}
+STEP_PASSES_MIN_SCHEDULE = 40   # dependency-minimal schedule of one step
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=10)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=2048)
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return HBM_FALLBACK_GBS, "fallback"
+
+
+def source_hash():
+    h = hashlib.sha1()
+    csrc = os.path.join(ROOT, "paper_2601_10057_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel, workload):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, or
+    None if missing or taken on different kernel sources."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        if d.get("source_hash") != source_hash():
+            return None
+        return d["workloads"][workload][kernel]["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed regions."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smmax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); smmax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smmax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def aggregate(local_seconds, local_units, world):
+    """Whole-job throughput: sum of units over ranks / max time over ranks."""
+    if world == 1:
+        return local_units / local_seconds, local_seconds, local_units
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([local_seconds], dtype=torch.float64, device=dev)
+    u = torch.tensor([float(local_units)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(u.item()) / float(t.item()), float(t.item()), float(u.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def cpu_oracle_sample(w, seconds, max_steps=None):
+    """Time the FP64 oracle (as it stands) on the host cores."""
+    from oracle import ccmsav_oracle as O
+    m = O.Model.from_params(w.N, w.params)
+    s = O.initial_state(w.phi0, w.psi0, m)
+    s = O.step(s, m)                    # the BDF1 start step, untimed
+    n, t0 = 0, time.perf_counter()
+    while True:
+        s = O.step(s, m)
+        n += 1
+        el = time.perf_counter() - t0
+        if el >= seconds or (max_steps and n >= max_steps):
+            break
+    return w.N * w.N * n / el, n, el
+
+
+def run_reference(args, world, rank):
+    from paper_2601_10057_gb300 import inputs as I
+    if rank != 0:
+        return
+    w = I.workload("three_vesicles", N=args.N)
+    budget = 150.0
+    t0 = time.perf_counter()
+    from oracle import ccmsav_oracle as O
+    m = O.Model.from_params(w.N, w.params)
+    s = O.initial_state(w.phi0, w.psi0, m)
+    s = O.step(s, m)
+    t_one = time.perf_counter() - t0
+    warm = min(args.warmup, 1)
+    for _ in range(warm):
+        s = O.step(s, m)
+    k = max(1, min(args.steps, int(budget / max(t_one, 1e-3))))
+    t1 = time.perf_counter()
+    for _ in range(k):
+        s = O.step(s, m)
+    el = time.perf_counter() - t1
+    value = w.N * w.N * k / el
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": "grid-point-steps/s", "value": value, "unit": "grid-point-steps/s",
+        "n_gpus": args.gpus, "steps": k, "warmup": warm, "ms_per_step": 1e3 * el / k,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": f"three_vesicles_N{w.N}", "N": w.N,
+                                        "precision": "fp64-oracle", "dt": w.params.dt},
+        "cpu_baseline": {"value": value, "unit": "grid-point-steps/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{k} BDF2 steps of the FP64 CPU oracle at N={w.N} (of {args.steps} "
+                                   f"requested; bounded to ~{budget:.0f} s), after {warm} warm-up step(s)"},
+        "e2e": {"value": value, "unit": "grid-point-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    from paper_2601_10057_gb300 import build as B
+    from paper_2601_10057_gb300 import ccmsav as cc
+    from paper_2601_10057_gb300 import inputs as I
+
+    B.build()
+    cc.load()
+    torch.cuda.set_device(local)
+    stream = torch.cuda.current_stream()
+    sh = stream.cuda_stream
+    w = I.three_vesicles(N=args.N, seed=1003 + rank, precision=args.precision)
+    NN = w.N * w.N
+    esize = 4 if args.precision == "fp32" else 8
+
+    def make(prec):
+        sim = cc.Simulation(w.params, w.N, precision=prec, stream=sh)
+        sim.set_state(w.phi0, w.psi0)
+        return sim
+
+    clocks = ClockSampler(local)
+    sim = make(args.precision)
+    sim.step(max(args.warmup, 3))
+    sim.sync()
+    # ---- timed region: K steps, device events on the launching stream
+    clocks.start()
+    barrier(world)
+    torch.cuda.synchronize()
+    l0 = sim.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    secs = e0.elapsed_time(e1) / 1e3
+    launches = sim.launches() - l0
+    sim.sync()
+    value, tmax, units = aggregate(secs, NN * args.steps, world)
+    # ---- per-kernel device times (second pass with event marks between kernels)
+    kprof = min(args.steps, 200)
+    cc.ccmsav_profile(sim.h, True)
+    sim.step(kprof)
+    st, ms, nst = cc.ccmsav_profile_read(sim.h, 0)
+    cc.ccmsav_profile(sim.h, False)
+    sim.sync()
+    per_launch = {cc.KERNEL_NAMES[i]: ms[i] / max(nst, 1) for i in range(6)}
+    dom = max(per_launch, key=per_launch.get)
+    peak, peak_kind = measured_peaks()
+    alg_bytes = PASSES[dom] * NN * esize
+    achieved = alg_bytes / (per_launch[dom] * 1e-3) / 1e9
+    kernels = {k: {"ms_per_launch": round(v, 5), "share": round(v / sum(per_launch.values()), 4),
+                   "alg_GBps": (round(PASSES[k] * NN * esize / (v * 1e-3) / 1e9, 1) if v > 0 and PASSES[k] else None)}
+               for k, v in per_launch.items()}
+    sim.close()
+    # ---- FP64 step on the same workload (secondary)
+    fp64 = None
+    if not args.no_fp64 and args.precision == "fp32":
+        s64 = make("fp64")
+        s64.step(3)
+        s64.sync()
+        k64 = min(args.steps, 60)
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        s64.step(k64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        t64 = f0.elapsed_time(f1) / 1e3
+        s64.sync()
+        s64.close()
+        fp64 = {"value": NN * k64 / t64, "ms_per_step": 1e3 * t64 / k64, "steps": k64,
+                "speedup_fp32_over_fp64": (NN * args.steps / secs) / (NN * k64 / t64)}
+    # ---- end to end through the C ABI with pinned host buffers
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).pin_memory().numpy()
+    phi_h, psi_h = pin(w.phi0), pin(w.psi0)
+    out_phi, out_psi = pin(np.zeros_like(w.phi0)), pin(np.zeros_like(w.psi0))
+    e2e_sim = cc.Simulation(w.params, w.N, precision=args.precision, stream=sh)
+    e2e_sim.set_state(phi_h, psi_h)
+    e2e_sim.step(3)
+    e2e_sim.sync()
+    k_e2e = min(args.steps, 200)
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_sim.set_state(phi_h, psi_h)
+    aux = None
+    for _ in range(k_e2e):
+        e2e_sim.step(1)
+        aux = e2e_sim.aux()
+    st = cc.load().ccmsav_get_state(e2e_sim.h, 0, cc._ptr(out_phi), cc._ptr(out_psi))
+    t_e2e = time.perf_counter() - t0
+    barrier(world)
+    clk = clocks.stop()
+    e2e_sim.close()
+    e2e_value, _, _ = aggregate(t_e2e, NN * k_e2e, world)
+    h2d = 2 * NN * 8 / k_e2e
+    d2h = 12 * 8 + 2 * NN * 8 / k_e2e
+    # ---- CPU baseline (oracle on the host cores, rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, n, el = cpu_oracle_sample(w, args.cpu_seconds)
+        cpu = {"value": v, "unit": "grid-point-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{n} BDF2 step(s) of the FP64 CPU oracle on the same N={w.N} workload "
+                         f"({el:.1f} s; numpy/OpenBLAS on all host cores)"}
+    if rank != 0:
+        return
+    traffic = ncu_traffic(dom, f"three_vesicles_N{w.N}_{args.precision}")
+    line = {
+        "metric": "grid-point-steps/s", "value": value, "unit": "grid-point-steps/s",
+        "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
+        "config": {"workload": f"three_vesicles_N{w.N}", "N": w.N, "precision":
+                   ("fp32-bulk/fp64-reductions" if args.precision == "fp32" else "fp64"),
+                   "dt": w.params.dt, "vesicles": 3, "parallelism": f"replicas{world}",
+                   "l2": "per-step working set > L2 (no flush needed)"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": traffic, "alg_bytes_per_launch": alg_bytes},
+        "step_roofline": {"alg_bytes_per_point": STEP_PASSES_MIN_SCHEDULE * esize,
+                          "achieved_GBps": round(value / world * STEP_PASSES_MIN_SCHEDULE * esize / 1e9, 1),
+                          "frac": round(value / world * STEP_PASSES_MIN_SCHEDULE * esize / 1e9 / peak, 4)},
+        "kernels": kernels,
+        "fp64": fp64,
+        "e2e": {"value": e2e_value, "unit": "grid-point-steps/s", "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h, "steps": k_e2e,
+                "what": "set_state from pinned host FP64 arrays, per step ccmsav_step(1) + ccmsav_get_aux "
+                        "(scalar read-back), final ccmsav_get_state to pinned host arrays"},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_setup(args)
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

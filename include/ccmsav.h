@@ -1,0 +1,190 @@
+/*
+ * ccmsav.h -- C ABI of the GB300 (sm_103a) CC-MSAV vesicle time stepper.
+ *
+ * The library advances the coupled Allen-Cahn (membrane phase phi) /
+ * variable-mobility Cahn-Hilliard (concentration psi) system with the
+ * constant-coefficient MSAV scheme of Zhang, Li, Lowengrub and Wise,
+ * "An Efficient Constant-Coefficient MSAV Scheme for Computing Vesicle Growth
+ * and Shrinkage" (arXiv 2601.10057):
+ *   - model and energy: Sec. 2.1 (eqs. AC, CH, energy_functional,
+ *     energy_densities) with the MSAV reformulation of Sec. 2.2 (eqs.
+ *     modified_energy, aux_vars, msav_mu, msav_nu);
+ *   - time step: CC-MSAV-BDF2 of Sec. 3.2 (eqs. AC_BDF2 ... Z_BDF2); the first
+ *     step after ccmsav_set_state is the CC-MSAV-BDF1 variant (Appendix B,
+ *     remark on the BDF1 scheme);
+ *   - space: cell-centred staggered grid with homogeneous Neumann ghost cells
+ *     (Sec. 3.4, Appendix D), face mobility and nonlocal bending terms of
+ *     Sec. 3.4.1;
+ *   - solution procedure: Appendix B (Steps 1-4, Algorithm "BDF2 MSAV Solution
+ *     Procedure") with the constant-coefficient operators chi and zeta solved
+ *     by DCT-II / eigenvalue divide / DCT-III (Appendix C).
+ *
+ * Conventions for every call:
+ *   - Return value: 0 on success, a negative CCMSAV_E* code otherwise;
+ *     ccmsav_strerror() gives a message.  No call aborts the process.
+ *   - Fields are N*N arrays, row-major: a[j*N + i] is cell (i, j) with centre
+ *     ((i + 1/2) h, (j + 1/2) h), h = L / N.
+ *   - The library owns all of its device memory and frees it in
+ *     ccmsav_destroy().  It never frees or keeps caller memory: host pointers
+ *     are read or written only during the call.
+ *   - Work is queued on the CUDA stream given to ccmsav_create(); calls that
+ *     return data to the host synchronise that stream.
+ *   - After a device-side error (CCMSAV_ENONFINITE) the handle refuses to
+ *     step until the next ccmsav_set_state().
+ *   - A handle must not be used from two host threads at once.
+ */
+#ifndef CCMSAV_H
+#define CCMSAV_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes. */
+#define CCMSAV_OK           0
+#define CCMSAV_EINVAL      -1   /* bad argument (size, parameter, index, NULL) */
+#define CCMSAV_ENOMEM      -2   /* device or host allocation failed */
+#define CCMSAV_ECUDA       -3   /* a CUDA runtime call failed */
+#define CCMSAV_ESTATE      -4   /* call out of order (e.g. step before set_state) */
+#define CCMSAV_ENONFINITE  -5   /* NaN/Inf input or state, a SAV radicand <= 0,
+                                   or a face mobility M_psi(A phi*) <= 0 */
+#define CCMSAV_ETIMEOUT    -6   /* a bounded device-side wait gave up */
+
+/* Precision of the field arithmetic. */
+#define CCMSAV_FP64       0     /* fields, stencils, DCTs and reductions in FP64 */
+#define CCMSAV_FP32_BULK  1     /* fields, stencils and DCTs in FP32; SAV inner
+                                   products, scalar updates, the 5x5 solve and
+                                   mass/energy reductions accumulated in FP64 */
+
+/* Flags for ccmsav_create(). */
+#define CCMSAV_TRACK_ENERGY 1   /* accumulate the lambda-sum of the modified
+                                   energy each BDF2 step (one extra reduction
+                                   kernel per step); needed for E_mod in
+                                   ccmsav_energy() */
+
+/* Model and scheme parameters.  Symbols and default values are those of the
+ * paper's parameter table (Appendix G): gamma_surf, gamma_bend, gamma_area
+ * (surface, bending and arc-length penalty), gamma_in/out, psi_in/out,
+ * beta_in/out (osmotic densities f_in/out, Sec. 2.1), eps (interface width),
+ * M_phi (Allen-Cahn mobility), M0 (Cahn-Hilliard mobility parameter in
+ * M_psi = 1 - M0 (phi^2 - 1)^2), theta and lam (Allen-Cahn and Cahn-Hilliard
+ * stabilisation, Sec. 3.2), beta (SAV splitting parameter), dt (time step)
+ * and L (side of the square domain [0, L]^2). */
+typedef struct {
+    double gamma_surf, gamma_bend, gamma_area;
+    double gamma_in, gamma_out;
+    double psi_in, psi_out;
+    double beta_in, beta_out;
+    double eps, M_phi, M0;
+    double theta, beta, lam;
+    double dt, L;
+} ccmsav_params;
+
+typedef struct ccmsav ccmsav_t;   /* opaque handle */
+
+/* Create a stepper for n_sims independent simulations (n_sims >= 1).
+ *   N[s]      grid size of simulation s: a power of two in [8, 8192].
+ *   params    parameters shared by all simulations; per_sim (may be NULL)
+ *             gives one parameter set per simulation instead.
+ *   precision CCMSAV_FP64 or CCMSAV_FP32_BULK.
+ *   flags     0 or CCMSAV_TRACK_ENERGY.
+ *   stream    a cudaStream_t (NULL: the legacy default stream).
+ * Validates every parameter (eps, dt, L, lam, M_phi > 0; theta, beta,
+ * gamma_* >= 0; 0 < M0 < 1) and returns CCMSAV_EINVAL otherwise.
+ * Allocates all device memory; no device compute is queued.
+ * On success *out receives the handle. */
+int ccmsav_create(ccmsav_t** out, const ccmsav_params* params, int n_sims,
+                  const int* N, const ccmsav_params* per_sim, int precision,
+                  int flags, void* stream);
+
+/* Load the initial state of simulation `sim` from host FP64 arrays phi, psi
+ * (N*N each; copied before return).  Computes V^0, W^0, Z^0 from their
+ * definitions (Sec. 2.2, eq. msav_ic) and sets the target arc length A of
+ * U to the initial arc length int f_surf(phi^0) (so U^0 = 0; the paper does
+ * not state A).  Resets the step counter, the lambda-sum and the error
+ * state; the next step of this simulation is the BDF1 start step.
+ * Returns CCMSAV_ENONFINITE if an input value is not finite. */
+int ccmsav_set_state(ccmsav_t* h, int sim, const double* phi, const double* psi);
+
+/* As ccmsav_set_state, from device memory of the handle's precision (FP64
+ * for CCMSAV_FP64, FP32 for CCMSAV_FP32_BULK).  The pointers are only read
+ * during the call (stream-ordered). */
+int ccmsav_set_state_device(ccmsav_t* h, int sim, const void* phi, const void* psi);
+
+/* Advance every simulation by nsteps >= 0 time steps.  Asynchronous: work is
+ * queued on the handle's stream; device-side errors are reported by the next
+ * synchronising call (ccmsav_sync, get_state, energy, mass, get_aux).
+ * Returns CCMSAV_ESTATE if some simulation has no state yet or is in error. */
+int ccmsav_step(ccmsav_t* h, int nsteps);
+
+/* Wait for queued work and return the first device-side error, if any. */
+int ccmsav_sync(ccmsav_t* h);
+
+/* Copy the current phi^n, psi^n of simulation `sim` into caller-owned host
+ * FP64 arrays (N*N each; FP32 fields are widened).  Synchronises. */
+int ccmsav_get_state(ccmsav_t* h, int sim, double* phi, double* psi);
+
+/* Diagnostics of simulation `sim` at the current level (synchronises):
+ *   out[0] E_mod   modified discrete energy E^{n+1,n}_mod (eq.
+ *                  modified_discrete_energy, discrete norms of Appendix D);
+ *                  includes the lambda-sum only with CCMSAV_TRACK_ENERGY
+ *   out[1] F_surf  gamma_surf * int f_surf
+ *   out[2] F_bend  gamma_bend * int f_bend
+ *   out[3] F_area  gamma_area/2 (int f_surf - A)^2
+ *   out[4] F_osm   int f_osm
+ *   out[5] arc     int f_surf (the diffuse arc length)
+ *   out[6] lamsum  sum_{j>=2} dt/2 ||d^j||^2 (0 without CCMSAV_TRACK_ENERGY)
+ *   out[7] F       F_surf + F_bend + F_area + F_osm
+ * All sums are accumulated in FP64. */
+int ccmsav_energy(ccmsav_t* h, int sim, double out[8]);
+
+/* Discrete mass h^2 sum_ij psi_ij of the stored concentration, summed in FP64
+ * (Sec. 3.4.2, remark on mass conservation).  Synchronises. */
+int ccmsav_mass(ccmsav_t* h, int sim, double* mass);
+
+/* Scalar state of simulation `sim`:
+ *   aux[0..3]  V^n, U^n, W^n, Z^n      aux[4..7]  V^{n-1}, U^{n-1}, W^{n-1}, Z^{n-1}
+ *   aux[8]     A (target arc length)   aux[9]     lambda-sum
+ *   aux[10]    steps taken since set_state
+ *   aux[11]    the conserved mean of psi (FP64) that the FP32-bulk path keeps
+ *              exactly (restored by set_aux when nonzero)
+ * get synchronises; set replaces the scalars (the fields are untouched), for
+ * example to restore a checkpoint together with set_state_levels. */
+int ccmsav_get_aux(ccmsav_t* h, int sim, double aux[12]);
+int ccmsav_set_aux(ccmsav_t* h, int sim, const double aux[12]);
+
+/* Two-level field access for exact checkpoint/resume: the previous level
+ * phi^{n-1}, psi^{n-1} (host FP64, N*N each). */
+int ccmsav_get_prev_state(ccmsav_t* h, int sim, double* phi_prev, double* psi_prev);
+int ccmsav_set_state_levels(ccmsav_t* h, int sim, const double* phi, const double* psi,
+                            const double* phi_prev, const double* psi_prev);
+
+/* Grid size of simulation `sim`, or a negative code. */
+int ccmsav_grid_size(ccmsav_t* h, int sim);
+
+/* Number of CUDA kernel launches queued by this handle since creation. */
+long long ccmsav_launch_count(ccmsav_t* h);
+
+/* Per-kernel tracing with CUDA events recorded on the handle's stream around
+ * every kernel of every step while enabled (enable = 1; 0 stops recording).
+ * ccmsav_profile_read() synchronises and returns, for simulation `sim`, the
+ * accumulated device time in milliseconds of each step kernel in the order
+ *   [0] stencil/pointwise + reductions   [1] forward row DCT (transposed)
+ *   [2] forward column DCT + Gram sums   [3] 5x5 solve + SAV update
+ *   [4] recovery + inverse column DCT    [5] inverse row DCT
+ *   [6] lambda-sum reduction (CCMSAV_TRACK_ENERGY only)   [7] reserved
+ * and in *nsteps the number of steps traced; it then resets the counters. */
+int ccmsav_profile(ccmsav_t* h, int enable);
+int ccmsav_profile_read(ccmsav_t* h, int sim, double ms[8], long long* nsteps);
+
+/* Message for a status code (static storage). */
+const char* ccmsav_strerror(int status);
+
+/* Free all device memory of the handle (synchronises its stream first).
+ * NULL is accepted. */
+void ccmsav_destroy(ccmsav_t* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CCMSAV_H */

@@ -1,0 +1,274 @@
+"""Python binding of the C ABI in ``include/ccmsav.h`` (ctypes; argument
+marshalling only -- every step of the method runs in the CUDA library).
+
+The functions keep the C names.  ``Simulation`` is a small convenience
+wrapper that owns one handle and converts numpy arrays.  Loading fails
+loudly (``RuntimeError``) when the compiled library is missing: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libccmsav.so")
+
+CCMSAV_OK = 0
+CCMSAV_EINVAL = -1
+CCMSAV_ENOMEM = -2
+CCMSAV_ECUDA = -3
+CCMSAV_ESTATE = -4
+CCMSAV_ENONFINITE = -5
+CCMSAV_ETIMEOUT = -6
+CCMSAV_FP64 = 0
+CCMSAV_FP32_BULK = 1
+CCMSAV_TRACK_ENERGY = 1
+
+PARAM_FIELDS = ["gamma_surf", "gamma_bend", "gamma_area", "gamma_in", "gamma_out",
+                "psi_in", "psi_out", "beta_in", "beta_out", "eps", "M_phi", "M0",
+                "theta", "beta", "lam", "dt", "L"]
+
+
+class ccmsav_params(C.Structure):
+    _fields_ = [(n, C.c_double) for n in PARAM_FIELDS]
+
+    @classmethod
+    def from_obj(cls, p) -> "ccmsav_params":
+        return cls(*[float(getattr(p, n)) for n in PARAM_FIELDS])
+
+
+class CCMSAVError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {ccmsav_strerror(status)} ({status})")
+        self.status = status
+
+
+_lib = None
+_DP = C.POINTER(C.c_double)
+
+
+def load(path: Optional[str] = None) -> C.CDLL:
+    """Load libccmsav.so (built by ``paper_2601_10057_gb300.build``)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with "
+                           "`python -m paper_2601_10057_gb300.build` (nvcc, sm_103a)")
+    lib = C.CDLL(path)
+    vp, i, d = C.c_void_p, C.c_int, C.c_double
+    sig = {
+        "ccmsav_create": (i, [C.POINTER(vp), C.POINTER(ccmsav_params), i, C.POINTER(i),
+                              C.POINTER(ccmsav_params), i, i, vp]),
+        "ccmsav_set_state": (i, [vp, i, _DP, _DP]),
+        "ccmsav_set_state_device": (i, [vp, i, vp, vp]),
+        "ccmsav_set_state_levels": (i, [vp, i, _DP, _DP, _DP, _DP]),
+        "ccmsav_step": (i, [vp, i]),
+        "ccmsav_sync": (i, [vp]),
+        "ccmsav_get_state": (i, [vp, i, _DP, _DP]),
+        "ccmsav_get_prev_state": (i, [vp, i, _DP, _DP]),
+        "ccmsav_energy": (i, [vp, i, _DP]),
+        "ccmsav_mass": (i, [vp, i, _DP]),
+        "ccmsav_get_aux": (i, [vp, i, _DP]),
+        "ccmsav_set_aux": (i, [vp, i, _DP]),
+        "ccmsav_grid_size": (i, [vp, i]),
+        "ccmsav_launch_count": (C.c_longlong, [vp]),
+        "ccmsav_strerror": (C.c_char_p, [i]),
+        "ccmsav_profile": (i, [vp, i]),
+        "ccmsav_profile_read": (i, [vp, i, _DP, C.POINTER(C.c_longlong)]),
+        "ccmsav_destroy": (None, [vp]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data_as(_DP)
+
+
+def _f64(a) -> np.ndarray:
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# ---------------------------------------------------------------- C names
+
+def ccmsav_strerror(status: int) -> str:
+    return load().ccmsav_strerror(int(status)).decode()
+
+
+def ccmsav_create(params, N: Sequence[int], precision: int = CCMSAV_FP64, flags: int = 0,
+                  stream: Optional[int] = None, per_sim: Optional[Sequence] = None):
+    """Returns (status, handle)."""
+    lib = load()
+    n = len(N)
+    Ns = (C.c_int * n)(*[int(x) for x in N])
+    h = C.c_void_p()
+    p = C.byref(ccmsav_params.from_obj(params)) if params is not None else None
+    ps = None
+    if per_sim is not None:
+        arr = (ccmsav_params * n)(*[ccmsav_params.from_obj(q) for q in per_sim])
+        ps = C.cast(arr, C.POINTER(ccmsav_params))
+    st = lib.ccmsav_create(C.byref(h), p, n, Ns, ps, int(precision), int(flags),
+                           C.c_void_p(stream) if stream else None)
+    return st, h
+
+
+def ccmsav_set_state(h, sim: int, phi, psi) -> int:
+    phi, psi = _f64(phi), _f64(psi)
+    return load().ccmsav_set_state(h, sim, _ptr(phi), _ptr(psi))
+
+
+def ccmsav_set_state_device(h, sim: int, phi_ptr: int, psi_ptr: int) -> int:
+    return load().ccmsav_set_state_device(h, sim, C.c_void_p(phi_ptr), C.c_void_p(psi_ptr))
+
+
+def ccmsav_set_state_levels(h, sim: int, phi, psi, phi_prev, psi_prev) -> int:
+    a = [_f64(x) for x in (phi, psi, phi_prev, psi_prev)]
+    return load().ccmsav_set_state_levels(h, sim, *[_ptr(x) for x in a])
+
+
+def ccmsav_step(h, nsteps: int) -> int:
+    return load().ccmsav_step(h, int(nsteps))
+
+
+def ccmsav_sync(h) -> int:
+    return load().ccmsav_sync(h)
+
+
+def ccmsav_get_state(h, sim: int, N: int, prev: bool = False):
+    phi = np.empty((N, N), np.float64)
+    psi = np.empty((N, N), np.float64)
+    fn = load().ccmsav_get_prev_state if prev else load().ccmsav_get_state
+    st = fn(h, sim, _ptr(phi), _ptr(psi))
+    return st, phi, psi
+
+
+def ccmsav_energy(h, sim: int):
+    out = np.zeros(8, np.float64)
+    st = load().ccmsav_energy(h, sim, _ptr(out))
+    return st, out
+
+
+def ccmsav_mass(h, sim: int):
+    out = np.zeros(1, np.float64)
+    st = load().ccmsav_mass(h, sim, _ptr(out))
+    return st, float(out[0])
+
+
+def ccmsav_get_aux(h, sim: int):
+    out = np.zeros(12, np.float64)
+    st = load().ccmsav_get_aux(h, sim, _ptr(out))
+    return st, out
+
+
+def ccmsav_set_aux(h, sim: int, aux) -> int:
+    aux = _f64(aux)
+    return load().ccmsav_set_aux(h, sim, _ptr(aux))
+
+
+def ccmsav_grid_size(h, sim: int) -> int:
+    return load().ccmsav_grid_size(h, sim)
+
+
+def ccmsav_launch_count(h) -> int:
+    return int(load().ccmsav_launch_count(h))
+
+
+def ccmsav_profile(h, enable: bool) -> int:
+    return load().ccmsav_profile(h, 1 if enable else 0)
+
+
+KERNEL_NAMES = ["k_stencil", "k_rowdct_T", "k_coldct_gram", "k_solve", "k_comb_icolT",
+                "k_irow", "k_dnorm+k_add_lamsum", "reserved"]
+
+
+def ccmsav_profile_read(h, sim: int = 0):
+    """Returns (status, ms[8], nsteps)."""
+    ms = np.zeros(8, np.float64)
+    n = C.c_longlong(0)
+    st = load().ccmsav_profile_read(h, sim, _ptr(ms), C.byref(n))
+    return st, ms, int(n.value)
+
+
+def ccmsav_destroy(h) -> None:
+    if h:
+        load().ccmsav_destroy(h)
+
+
+# ---------------------------------------------------------------- wrapper
+
+class Simulation:
+    """Owns one handle for one or more simulations; raises on error codes."""
+
+    def __init__(self, params, N, precision: str = "fp64", track_energy: bool = False,
+                 stream: Optional[int] = None, per_sim=None):
+        Ns = [int(N)] if np.isscalar(N) else [int(x) for x in N]
+        prec = CCMSAV_FP64 if precision == "fp64" else CCMSAV_FP32_BULK
+        flags = CCMSAV_TRACK_ENERGY if track_energy else 0
+        st, h = ccmsav_create(params, Ns, prec, flags, stream, per_sim)
+        if st != CCMSAV_OK:
+            raise CCMSAVError(st, "ccmsav_create")
+        self.h, self.N, self.precision = h, Ns, precision
+
+    def _check(self, st, where):
+        if st != CCMSAV_OK:
+            raise CCMSAVError(st, where)
+
+    def set_state(self, phi, psi, sim: int = 0):
+        self._check(ccmsav_set_state(self.h, sim, phi, psi), "ccmsav_set_state")
+
+    def set_levels(self, phi, psi, phi_prev, psi_prev, sim: int = 0):
+        self._check(ccmsav_set_state_levels(self.h, sim, phi, psi, phi_prev, psi_prev),
+                    "ccmsav_set_state_levels")
+
+    def step(self, n: int = 1):
+        self._check(ccmsav_step(self.h, n), "ccmsav_step")
+
+    def sync(self):
+        self._check(ccmsav_sync(self.h), "ccmsav_sync")
+
+    def state(self, sim: int = 0, prev: bool = False):
+        st, phi, psi = ccmsav_get_state(self.h, sim, self.N[sim], prev)
+        self._check(st, "ccmsav_get_state")
+        return phi, psi
+
+    def energy(self, sim: int = 0):
+        st, out = ccmsav_energy(self.h, sim)
+        self._check(st, "ccmsav_energy")
+        return out
+
+    def mass(self, sim: int = 0) -> float:
+        st, m = ccmsav_mass(self.h, sim)
+        self._check(st, "ccmsav_mass")
+        return m
+
+    def aux(self, sim: int = 0):
+        st, a = ccmsav_get_aux(self.h, sim)
+        self._check(st, "ccmsav_get_aux")
+        return a
+
+    def set_aux(self, aux, sim: int = 0):
+        self._check(ccmsav_set_aux(self.h, sim, aux), "ccmsav_set_aux")
+
+    def launches(self) -> int:
+        return ccmsav_launch_count(self.h)
+
+    def close(self):
+        if self.h:
+            ccmsav_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,124 @@
+// diag_kernels.cuh -- FP64 reductions outside the time step: initial SAVs,
+// mass, the modified discrete energy and physical energy components, and
+// the lambda-sum increment ||d^{n+1}||^2 of the modified energy.
+#pragma once
+#include "step_kernels.cuh"
+
+namespace ccm {
+
+enum { NDIAG = 14 };
+// Sums (times h^2 where noted by the host):
+//  0 (a^2-1-beta)^2/(4 eps)   1 6 a^2 gbar + (a^3-a)^2/eps^2   2 (1+p)f_in + (1-p)f_out
+//  3 g(a)                     4 face sum (D a)^2               5 (Lap a)^2
+//  6 (2 Lap a - Lap b)^2      7 face sum (D(2a-b))^2           8 face sum (D(a-b))^2
+//  9 a^2                      10 (2a-b)^2                       11 ((a^3-a)/eps - eps Lap a)^2
+//  12 f_osm                   13 psi
+struct DiagCoef {
+    double inv_h, inv_h2, eps, inv_eps, beta;
+    double gin, gout, psin, psout, bin, bout;
+};
+
+template <typename T>
+__device__ __forceinline__ double at(const T* u, int N, int i, int j) {
+    i = i < 0 ? 0 : (i >= N ? N - 1 : i);
+    j = j < 0 ? 0 : (j >= N ? N - 1 : j);
+    return (double)u[(size_t)j * N + i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_diag(const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ psi,
+       double* __restrict__ part, int N, DiagCoef c) {
+    __shared__ double sred[8 * NDIAG];
+    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
+    double v[NDIAG];
+    for (int q = 0; q < NDIAG; ++q) v[q] = 0.0;
+    if (i < N && j < N) {
+        const double aC = at(a, N, i, j), aE = at(a, N, i + 1, j), aW = at(a, N, i - 1, j);
+        const double aN = at(a, N, i, j + 1), aS = at(a, N, i, j - 1);
+        const double bC = at(b, N, i, j), bE = at(b, N, i + 1, j), bW = at(b, N, i - 1, j);
+        const double bN = at(b, N, i, j + 1), bS = at(b, N, i, j - 1);
+        const double la = (aE + aW + aN + aS - 4 * aC) * c.inv_h2;
+        const double lb = (bE + bW + bN + bS - 4 * bC) * c.inv_h2;
+        const double gE = (aE - aC) * c.inv_h, gW = (aC - aW) * c.inv_h, gN = (aN - aC) * c.inv_h, gS = (aC - aS) * c.inv_h;
+        const double gbar = 0.5 * (gE * gE + gW * gW) + 0.5 * (gN * gN + gS * gS);
+        const double vv = aC * aC - 1.0 - c.beta;
+        const double a3 = aC * aC * aC - aC;
+        const double ps = (double)psi[(size_t)j * N + i];
+        double sp, cp;
+        sincospi(0.5 * aC, &sp, &cp);
+        const double fin = 0.5 * c.gin * (ps - c.psin) * (ps - c.psin) + c.bin;
+        const double fout = 0.5 * c.gout * (ps - c.psout) * (ps - c.psout) + c.bout;
+        v[0] = vv * vv * 0.25 * c.inv_eps;
+        v[1] = 6.0 * aC * aC * gbar + a3 * a3 * c.inv_eps * c.inv_eps;
+        v[2] = (1.0 + sp) * fin + (1.0 - sp) * fout;
+        v[3] = 0.25 * (aC * aC - 1.0) * (aC * aC - 1.0);
+        // interior faces owned by this cell: east (i+1/2) and north (j+1/2)
+        const double cE = 2 * aC - bC, cEe = 2 * aE - bE, cNn = 2 * aN - bN;
+        const double dC = aC - bC, dEe = aE - bE, dNn = aN - bN;
+        if (i + 1 < N) {
+            v[4] += gE * gE;
+            v[7] += (cEe - cE) * (cEe - cE) * c.inv_h2;
+            v[8] += (dEe - dC) * (dEe - dC) * c.inv_h2;
+        }
+        if (j + 1 < N) {
+            v[4] += gN * gN;
+            v[7] += (cNn - cE) * (cNn - cE) * c.inv_h2;
+            v[8] += (dNn - dC) * (dNn - dC) * c.inv_h2;
+        }
+        v[5] = la * la;
+        v[6] = (2 * la - lb) * (2 * la - lb);
+        v[9] = aC * aC;
+        v[10] = cE * cE;
+        const double w = a3 * c.inv_eps - c.eps * la;
+        v[11] = w * w;
+        v[12] = 0.5 * (1.0 + sp) * fin + 0.5 * (1.0 - sp) * fout;
+        v[13] = ps;
+    }
+    block_sum_store<NDIAG, double>(v, part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * NDIAG, sred);
+}
+
+// ||d||^2 / (lam^2 h^2): sum over interior faces of (D w)^2 / M_psi(A phi*),
+// w = psi^{n+1} - psi*, phi* = 2 phi^n - phi^{n-1}, psi* = 2 psi^n - psi^{n-1}.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_dnorm(const T* __restrict__ phn, const T* __restrict__ pho, const T* __restrict__ psnew,
+        const T* __restrict__ psn, const T* __restrict__ pso, double* __restrict__ part, int N, double M0) {
+    __shared__ double sred[8];
+    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+    const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
+    double v[1] = {0.0};
+    if (i < N && j < N) {
+        auto ph = [&](int ii, int jj) { return 2.0 * at(phn, N, ii, jj) - at(pho, N, ii, jj); };
+        auto w = [&](int ii, int jj) { return at(psnew, N, ii, jj) - (2.0 * at(psn, N, ii, jj) - at(pso, N, ii, jj)); };
+        const double pC = ph(i, j), wC = w(i, j);
+        auto mob = [&](double x) { double s = x * x - 1.0; return 1.0 - M0 * s * s; };
+        if (i + 1 < N) { double d = w(i + 1, j) - wC; v[0] += d * d / mob(0.5 * (pC + ph(i + 1, j))); }
+        if (j + 1 < N) { double d = w(i, j + 1) - wC; v[0] += d * d / mob(0.5 * (pC + ph(i, j + 1))); }
+    }
+    block_sum_store<1, double>(v, part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x), sred);
+}
+
+// lamsum += scale * sum(part[0..nb)) in a fixed order (one block).
+static __global__ void __launch_bounds__(256)
+k_add_lamsum(const double* __restrict__ part, int nb, double scale, DevScalars* sc) {
+    __shared__ double red[256];
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nb; b += blockDim.x) s += part[b];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) red[threadIdx.x] += red[threadIdx.x + k];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && sc->status == 0) sc->lamsum += scale * red[0];
+}
+
+template <typename Tsrc, typename Tdst>
+__global__ void k_convert(const Tsrc* __restrict__ in, Tdst* __restrict__ out, size_t n) {
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)
+        out[q] = (Tdst)in[q];
+}
+
+}  // namespace ccm

@@ -1,0 +1,34 @@
+// sim.h -- precision-independent interface between the C ABI and the
+// per-precision implementations of one simulation.
+#pragma once
+#include <cuda_runtime.h>
+#include "../../include/ccmsav.h"
+
+namespace ccm {
+
+class SimBase {
+public:
+    virtual ~SimBase() {}
+    // phi_prev/psi_prev may be NULL (both levels set to phi/psi; next step is BDF1).
+    virtual int set_state_host(const double* phi, const double* psi,
+                               const double* phi_prev, const double* psi_prev) = 0;
+    virtual int set_state_device(const void* phi, const void* psi) = 0;
+    virtual int queue_steps(int nsteps) = 0;
+    virtual int get_fields(double* phi, double* psi, bool previous) = 0;
+    virtual int energy(double out[8]) = 0;
+    virtual int mass(double* m) = 0;
+    virtual int get_aux(double aux[12]) = 0;
+    virtual int set_aux(const double aux[12]) = 0;
+    virtual int device_status() = 0;      // synchronises the stream
+    virtual bool has_state() const = 0;
+    virtual bool in_error() const = 0;
+    virtual long long launches() const = 0;
+    virtual int profile(bool enable) = 0;
+    virtual int profile_read(double ms[8], long long* nsteps) = 0;
+    int N = 0;
+};
+
+SimBase* make_sim_f32(const ccmsav_params& p, int N, int flags, cudaStream_t s, int* err);
+SimBase* make_sim_f64(const ccmsav_params& p, int N, int flags, cudaStream_t s, int* err);
+
+}  // namespace ccm

@@ -1,0 +1,489 @@
+// sim_impl.cuh -- host orchestration of one simulation in precision T.
+//
+// Device memory per simulation (T = field precision):
+//   phi[3], psi[3]   three time levels in rotation (n+1 is written into the
+//                    spare level, so n-1 stays readable for the optional
+//                    lambda-sum reduction)
+//   bufA             8 N x N fields: stencil outputs, later the spectra
+//   bufB             8 N x N fields: row-transformed (transposed) fields,
+//                    later the two inverse-column-transformed fields
+//   part1/part2      FP64 per-block partial sums of the stencil and Gram
+//                    reductions (reduced in a fixed order by k_solve)
+//   twM, twP, ev     FFT twiddles, DCT pre/post twiddles and the 1D Laplacian
+//                    eigenvalues 4 sin^2(pi k / 2N) / h^2 (computed on the host
+//                    in FP64)
+//   sc               DevScalars (SAVs, recovery coefficients, status)
+#pragma once
+#include <cmath>
+#include <cstring>
+#include <vector>
+#include "sim.h"
+#include "diag_kernels.cuh"
+
+namespace ccm {
+
+#define CCM_CUDA(call)                                  \
+    do {                                                \
+        cudaError_t e_ = (call);                        \
+        if (e_ != cudaSuccess) return CCMSAV_ECUDA;     \
+    } while (0)
+
+static inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+static const size_t kSmemMax = 227 * 1024;
+
+template <typename T>
+class SimImpl : public SimBase {
+public:
+    ccmsav_params p{};
+    int flags = 0;
+    cudaStream_t st = nullptr;
+    int M = 0;
+    size_t NN = 0;
+    T* phi[3] = {nullptr, nullptr, nullptr};
+    T* psi[3] = {nullptr, nullptr, nullptr};
+    int cur = 0, prev = 1, spare = 2;
+    T* bufA = nullptr;
+    T* bufB = nullptr;
+    double* part1 = nullptr;
+    double* part2 = nullptr;
+    double* partd = nullptr;
+    cplx<T>* twM = nullptr;
+    PostTw<T>* twP = nullptr;
+    double* ev = nullptr;
+    DevScalars* sc = nullptr;
+    DevScalars* sc_host = nullptr;   // pinned
+    double* h_part = nullptr;        // pinned, diag partial rows
+    void* tmp64 = nullptr;           // FP64 staging for host I/O
+    bool have_state = false, poisoned = false;
+    long long steps_taken = 0;
+    long long nlaunch = 0;
+    // launch geometry
+    dim3 g_st, b_st;
+    int nb1 = 0;
+    int RT = 1, lds_rt = 0; size_t sm_rt = 0;
+    int FG = 8; size_t sm_col = 0;
+    int RT4 = 1, lds_c = 0; size_t sm_comb = 0;
+    int PR = 1; size_t sm_irow = 0;
+    dim3 g_dg;
+    int nbd = 0;
+    // tracing: event marks between the kernels of traced steps
+    bool prof = false;
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<int> ev_kind;        // kernel slot of the interval that ends at this mark (-1: step start)
+    size_t ev_used = 0;
+    double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    long long prof_steps = 0;
+
+    ~SimImpl() override {
+        if (st) cudaStreamSynchronize(st); else cudaDeviceSynchronize();
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        release();
+    }
+
+    int mark(int kind) {
+        if (!prof) return CCMSAV_OK;
+        if (ev_used == ev_pool.size()) {
+            cudaEvent_t e;
+            CCM_CUDA(cudaEventCreate(&e));
+            ev_pool.push_back(e);
+            ev_kind.push_back(kind);
+        }
+        ev_kind[ev_used] = kind;
+        CCM_CUDA(cudaEventRecord(ev_pool[ev_used], st));
+        ++ev_used;
+        return CCMSAV_OK;
+    }
+
+    int profile_flush() {
+        if (ev_used == 0) return CCMSAV_OK;
+        CCM_CUDA(cudaStreamSynchronize(st));
+        for (size_t i = 1; i < ev_used; ++i) {
+            if (ev_kind[i] < 0) continue;
+            float ms = 0.f;
+            CCM_CUDA(cudaEventElapsedTime(&ms, ev_pool[i - 1], ev_pool[i]));
+            prof_ms[ev_kind[i]] += ms;
+        }
+        ev_used = 0;
+        return CCMSAV_OK;
+    }
+
+    int profile(bool enable) override {
+        int r = profile_flush();
+        prof = enable;
+        return r;
+    }
+
+    int profile_read(double ms[8], long long* nsteps) override {
+        int r = profile_flush();
+        for (int i = 0; i < 8; ++i) { ms[i] = prof_ms[i]; prof_ms[i] = 0; }
+        *nsteps = prof_steps;
+        prof_steps = 0;
+        return r;
+    }
+
+    void release() {
+        for (int i = 0; i < 3; ++i) { cudaFree(phi[i]); cudaFree(psi[i]); phi[i] = psi[i] = nullptr; }
+        cudaFree(bufA); cudaFree(bufB); cudaFree(part1); cudaFree(part2); cudaFree(partd);
+        cudaFree(twM); cudaFree(twP); cudaFree(ev); cudaFree(sc); cudaFree(tmp64);
+        if (sc_host) cudaFreeHost(sc_host);
+        if (h_part) cudaFreeHost(h_part);
+        bufA = bufB = nullptr; part1 = part2 = partd = nullptr; twM = nullptr; twP = nullptr;
+        ev = nullptr; sc = nullptr; tmp64 = nullptr; sc_host = nullptr; h_part = nullptr;
+    }
+
+    static int set_smem_limit(const void* fn, size_t needed) {
+        int dev = 0, optin = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+        if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 1;
+        cudaFuncAttributes fa;
+        if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 1;
+        const int lim = optin - (int)fa.sharedSizeBytes;
+        if ((size_t)lim < needed) return 1;
+        return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess;
+    }
+
+    static int lines_per_batch(int M_) { int E = M_ < 8 ? M_ : 8; return 512 / (M_ / E); }
+
+    int init(const ccmsav_params& pp, int N_, int flags_, cudaStream_t s) {
+        p = pp; N = N_; flags = flags_; st = s;
+        M = N / 2; NN = (size_t)N * N;
+        const size_t fb = NN * sizeof(T);
+        for (int i = 0; i < 3; ++i) {
+            if (cudaMalloc(&phi[i], fb) != cudaSuccess) return CCMSAV_ENOMEM;
+            if (cudaMalloc(&psi[i], fb) != cudaSuccess) return CCMSAV_ENOMEM;
+        }
+        if (cudaMalloc(&bufA, 8 * fb) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaMalloc(&bufB, 8 * fb) != cudaSuccess) return CCMSAV_ENOMEM;
+        b_st = dim3(TX, TY);
+        g_st = dim3((N + TX - 1) / TX, (N + TY - 1) / TY);
+        nb1 = g_st.x * g_st.y;
+        g_dg = dim3((N + 31) / 32, (N + 7) / 8);
+        nbd = g_dg.x * g_dg.y;
+        if (cudaMalloc(&part1, (size_t)nb1 * NRED1 * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaMalloc(&part2, (size_t)N * NRED2 * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaMalloc(&partd, (size_t)nbd * NDIAG * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaMalloc(&tmp64, 2 * NN * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaMalloc(&sc, sizeof(DevScalars)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaHostAlloc(&sc_host, sizeof(DevScalars), cudaHostAllocDefault) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaHostAlloc(&h_part, (size_t)nbd * NDIAG * sizeof(double), cudaHostAllocDefault) != cudaSuccess) return CCMSAV_ENOMEM;
+        std::memset(sc_host, 0, sizeof(DevScalars));
+        CCM_CUDA(cudaMemcpyAsync(sc, sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
+        // tables (FP64 on the host, rounded to T)
+        std::vector<cplx<T>> hM(M);
+        for (int t = 0; t < M; ++t) {
+            const double a = 2.0 * M_PI * t / M;
+            hM[t].x = (T)std::cos(a); hM[t].y = (T)(-std::sin(a));
+        }
+        std::vector<PostTw<T>> hP(M / 2 + 1);
+        for (int k = 0; k <= M / 2; ++k) {
+            const double a = 2.0 * M_PI * k / N, b = M_PI * k / (2.0 * N);
+            hP[k].cN = (T)std::cos(a); hP[k].sN = (T)std::sin(a);
+            hP[k].c4 = (T)std::cos(b); hP[k].s4 = (T)std::sin(b);
+        }
+        std::vector<double> hE(N);
+        const double h = p.L / N;
+        for (int k = 0; k < N; ++k) { const double s = std::sin(M_PI * k / (2.0 * N)); hE[k] = 4.0 * s * s / (h * h); }
+        if (cudaMalloc(&twM, M * sizeof(cplx<T>)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaMalloc(&twP, (M / 2 + 1) * sizeof(PostTw<T>)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaMalloc(&ev, N * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
+        CCM_CUDA(cudaMemcpyAsync(twM, hM.data(), M * sizeof(cplx<T>), cudaMemcpyHostToDevice, st));
+        CCM_CUDA(cudaMemcpyAsync(twP, hP.data(), (M / 2 + 1) * sizeof(PostTw<T>), cudaMemcpyHostToDevice, st));
+        CCM_CUDA(cudaMemcpyAsync(ev, hE.data(), N * sizeof(double), cudaMemcpyHostToDevice, st));
+        // DCT kernel geometry
+        const int P = lines_per_batch(M);
+        const size_t ldc = padded_len(M);
+        const size_t lsz = ldc * sizeof(cplx<T>);
+        RT = (int)std::min<size_t>(64 / sizeof(T), std::max<size_t>(1, 131072 / (N * sizeof(T))));
+        if (RT > N) RT = N;
+        lds_rt = N + 1;
+        sm_rt = align16((size_t)RT * lds_rt * sizeof(T)) + (size_t)std::min(P, RT) * lsz;
+        FG = 8;
+        while (FG > 1 && (size_t)FG * lsz + 16 * NRED2 * sizeof(double) > kSmemMax) FG /= 2;
+        sm_col = (size_t)FG * lsz;
+        RT4 = (int)std::max<size_t>(1, std::min<size_t>(64 / sizeof(T), 65536 / (N * sizeof(T))));
+        if (RT4 > N) RT4 = N;
+        lds_c = N + 1;
+        sm_comb = align16((size_t)2 * RT4 * lds_c * sizeof(T)) + (size_t)std::min(P, 2 * RT4) * lsz;
+        PR = std::max(1, std::min(4, N / 8));
+        sm_irow = (size_t)std::min(P, 2 * PR) * lsz;
+        if (sm_rt > kSmemMax || sm_col > kSmemMax || sm_comb > kSmemMax || sm_irow > kSmemMax) return CCMSAV_EINVAL;
+        // opt in to the largest dynamic shared memory each kernel can take (the
+        // per-block opt-in limit minus the kernel's static shared memory); the
+        // attribute is per kernel, so it must not depend on this simulation's N
+        if (set_smem_limit((const void*)k_rowdct_T<T>, sm_rt) || set_smem_limit((const void*)k_coldct_gram<T>, sm_col) ||
+            set_smem_limit((const void*)k_comb_icolT<T>, sm_comb) || set_smem_limit((const void*)k_irow<T>, sm_irow))
+            return CCMSAV_ECUDA;
+        CCM_CUDA(cudaStreamSynchronize(st));
+        return CCMSAV_OK;
+    }
+
+    double h() const { return p.L / N; }
+    double theta_tilde() const { return p.theta + p.gamma_bend * 3.0 * M_SQRT2 / (4.0 * p.eps); }
+
+    DiagCoef diag_coef() const {
+        DiagCoef c;
+        c.inv_h = 1.0 / h(); c.inv_h2 = 1.0 / (h() * h()); c.eps = p.eps; c.inv_eps = 1.0 / p.eps; c.beta = p.beta;
+        c.gin = p.gamma_in; c.gout = p.gamma_out; c.psin = p.psi_in; c.psout = p.psi_out; c.bin = p.beta_in; c.bout = p.beta_out;
+        return c;
+    }
+
+    // Runs k_diag on (a, b, psi) and returns the NDIAG sums (FP64, fixed order).
+    int diag_sums(const T* a, const T* b, const T* ps, double out[NDIAG]) {
+        k_diag<T><<<g_dg, 256, 0, st>>>(a, b, ps, partd, N, diag_coef());
+        ++nlaunch;
+        CCM_CUDA(cudaGetLastError());
+        CCM_CUDA(cudaMemcpyAsync(h_part, partd, (size_t)nbd * NDIAG * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CCM_CUDA(cudaStreamSynchronize(st));
+        for (int q = 0; q < NDIAG; ++q) out[q] = 0.0;
+        for (int bk = 0; bk < nbd; ++bk)
+            for (int q = 0; q < NDIAG; ++q) out[q] += h_part[(size_t)bk * NDIAG + q];
+        return CCMSAV_OK;
+    }
+
+    int upload_levels(const double* phi0, const double* psi0, const double* phi1, const double* psi1) {
+        double* d = (double*)tmp64;
+        const size_t nb = NN * sizeof(double);
+        auto conv = [&](const double* host, T* dst) -> int {
+            CCM_CUDA(cudaMemcpyAsync(d, host, nb, cudaMemcpyHostToDevice, st));
+            k_convert<double, T><<<1024, 256, 0, st>>>(d, dst, NN);
+            ++nlaunch;
+            CCM_CUDA(cudaGetLastError());
+            CCM_CUDA(cudaStreamSynchronize(st));
+            return CCMSAV_OK;
+        };
+        int r;
+        if ((r = conv(phi0, phi[cur])) != CCMSAV_OK) return r;
+        if ((r = conv(psi0, psi[cur])) != CCMSAV_OK) return r;
+        if ((r = conv(phi1 ? phi1 : phi0, phi[prev])) != CCMSAV_OK) return r;
+        if ((r = conv(psi1 ? psi1 : psi0, psi[prev])) != CCMSAV_OK) return r;
+        return CCMSAV_OK;
+    }
+
+    int init_scalars_from_fields(double psi_sum_fp64) {
+        double s[NDIAG];
+        int r = diag_sums(phi[cur], phi[cur], psi[cur], s);
+        if (r) return r;
+        const double h2 = h() * h();
+        std::memset(sc_host, 0, sizeof(DevScalars));
+        sc_host->V = sc_host->Vo = std::sqrt(h2 * s[0]);
+        sc_host->W = sc_host->Wo = std::sqrt(h2 * s[1]);
+        sc_host->Z = sc_host->Zo = std::sqrt(h2 * s[2]);
+        const double arc = 3.0 * M_SQRT2 / 4.0 * (h2 * s[3] / p.eps + 0.5 * p.eps * h2 * s[4]);
+        sc_host->A = arc;
+        sc_host->U = sc_host->Uo = 0.0;
+        sc_host->mass_mode = psi_sum_fp64 / ((double)N * N);
+        sc_host->status = 0;
+        if (!(s[0] > 0 && s[1] > 0 && s[2] > 0) || !std::isfinite(arc)) return CCMSAV_ENONFINITE;
+        CCM_CUDA(cudaMemcpyAsync(sc, sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
+        CCM_CUDA(cudaStreamSynchronize(st));
+        return CCMSAV_OK;
+    }
+
+    int set_state_host(const double* phi0, const double* psi0, const double* phi1, const double* psi1) override {
+        for (size_t q = 0; q < NN; ++q)
+            if (!std::isfinite(phi0[q]) || !std::isfinite(psi0[q]) ||
+                (phi1 && !std::isfinite(phi1[q])) || (psi1 && !std::isfinite(psi1[q])))
+                return CCMSAV_ENONFINITE;
+        cur = 0; prev = 1; spare = 2;
+        int r = upload_levels(phi0, psi0, phi1, psi1);
+        if (r) return r;
+        double ssum = 0.0;
+        for (size_t q = 0; q < NN; ++q) ssum += psi0[q];
+        r = init_scalars_from_fields(ssum);
+        if (r) return r;
+        have_state = true; poisoned = false;
+        steps_taken = (phi1 && psi1) ? 1 : 0;   // two given levels: continue with BDF2
+        return CCMSAV_OK;
+    }
+
+    int set_state_device(const void* dphi, const void* dpsi) override {
+        cur = 0; prev = 1; spare = 2;
+        const size_t fb = NN * sizeof(T);
+        CCM_CUDA(cudaMemcpyAsync(phi[cur], dphi, fb, cudaMemcpyDeviceToDevice, st));
+        CCM_CUDA(cudaMemcpyAsync(psi[cur], dpsi, fb, cudaMemcpyDeviceToDevice, st));
+        CCM_CUDA(cudaMemcpyAsync(phi[prev], dphi, fb, cudaMemcpyDeviceToDevice, st));
+        CCM_CUDA(cudaMemcpyAsync(psi[prev], dpsi, fb, cudaMemcpyDeviceToDevice, st));
+        double s[NDIAG];
+        int r = diag_sums(phi[cur], phi[cur], psi[cur], s);
+        if (r) return r;
+        for (int q = 0; q < NDIAG; ++q) if (!std::isfinite(s[q])) return CCMSAV_ENONFINITE;
+        r = init_scalars_from_fields(s[13]);
+        if (r) return r;
+        have_state = true; poisoned = false; steps_taken = 0;
+        return CCMSAV_OK;
+    }
+
+    int queue_one_step() {
+        const bool bdf1 = (steps_taken == 0);
+        const double dt = p.dt;
+        StencilCoef c;
+        if (bdf1) { c.e1 = 1; c.e2 = 0; c.t1 = 1.0 / dt; c.t2 = 0; c.w1 = -1; c.w2 = 0; }
+        else { c.e1 = 2; c.e2 = -1; c.t1 = 2.0 / dt; c.t2 = -0.5 / dt; c.w1 = -4; c.w2 = 1; }
+        c.inv_h = 1.0 / h(); c.inv_h2 = 1.0 / (h() * h());
+        c.eps = p.eps; c.inv_eps = 1.0 / p.eps; c.inv_eps2 = 1.0 / (p.eps * p.eps); c.beta = p.beta;
+        c.Mth = p.M_phi * theta_tilde(); c.lam = p.lam;
+        c.gin = p.gamma_in; c.gout = p.gamma_out; c.psin = p.psi_in; c.psout = p.psi_out;
+        c.bin = p.beta_in; c.bout = p.beta_out; c.M0 = p.M0;
+        SpecCoef s;
+        const double a = bdf1 ? 1.0 / dt : 1.5 / dt;
+        s.C1 = a + p.M_phi * p.gamma_surf * 3.0 * M_SQRT2 * p.beta / (4.0 * p.eps);
+        s.C2 = p.M_phi * (p.gamma_surf * 3.0 * M_SQRT2 * p.eps / 4.0 + p.theta);
+        s.C3 = p.M_phi * p.gamma_bend * 3.0 * M_SQRT2 * p.eps / 8.0;
+        s.Ct = a; s.lam = p.lam;
+        SolveCoef so;
+        so.h2 = h() * h();
+        so.cgs = p.M_phi * p.gamma_surf * 3.0 * M_SQRT2 / 2.0;
+        so.cga = p.M_phi * p.gamma_area;
+        so.cgb = p.M_phi * p.gamma_bend * 3.0 * M_SQRT2 / (8.0 * p.eps);
+        so.cgo = p.M_phi;
+        so.bdf1 = bdf1 ? 1 : 0;
+        so.nb1 = nb1; so.nb2 = N;
+        const int anchor = (sizeof(T) == sizeof(float)) ? 1 : 0;
+
+        if (prof && ev_used + 16 > 4096) { int r = profile_flush(); if (r) return r; }
+        mark(-1);
+        k_stencil<T><<<g_st, b_st, 0, st>>>(phi[cur], phi[prev], psi[cur], psi[prev], bufA, part1, N, c);
+        mark(0);
+        k_rowdct_T<T><<<dim3(N / RT, NF), 512, sm_rt, st>>>(bufA, bufB, N, RT, lds_rt, twM, twP);
+        mark(1);
+        k_coldct_gram<T><<<N, 512, sm_col, st>>>(bufB, bufA, part2, N, FG, twM, twP, ev, s);
+        mark(2);
+        k_solve<<<1, 512, 0, st>>>(part1, part2, sc, so);
+        mark(3);
+        k_comb_icolT<T><<<N / RT4, 512, sm_comb, st>>>(bufA, bufB, N, RT4, lds_c, twM, twP, ev, s, sc, anchor);
+        mark(4);
+        k_irow<T><<<N / PR, 512, sm_irow, st>>>(bufB, phi[spare], psi[spare], N, PR, twM, twP, sc, anchor);
+        mark(5);
+        nlaunch += 6;
+        if (!bdf1 && (flags & CCMSAV_TRACK_ENERGY)) {
+            k_dnorm<T><<<g_dg, 256, 0, st>>>(phi[cur], phi[prev], psi[spare], psi[cur], psi[prev], partd, N, p.M0);
+            k_add_lamsum<<<1, 256, 0, st>>>(partd, nbd, 0.5 * dt * p.lam * p.lam, sc);
+            mark(6);
+            nlaunch += 2;
+        }
+        if (prof) ++prof_steps;
+        CCM_CUDA(cudaGetLastError());
+        const int nw = spare;
+        spare = prev; prev = cur; cur = nw;
+        ++steps_taken;
+        return CCMSAV_OK;
+    }
+
+    int queue_steps(int nsteps) override {
+        if (!have_state) return CCMSAV_ESTATE;
+        if (poisoned) return CCMSAV_ENONFINITE;
+        for (int i = 0; i < nsteps; ++i) {
+            int r = queue_one_step();
+            if (r) return r;
+        }
+        return CCMSAV_OK;
+    }
+
+    int device_status() override {
+        CCM_CUDA(cudaStreamSynchronize(st));
+        CCM_CUDA(cudaMemcpy(sc_host, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
+        if (sc_host->status != 0) { poisoned = true; return sc_host->status; }
+        return CCMSAV_OK;
+    }
+
+    int get_fields(double* ph, double* ps, bool previous) override {
+        if (!have_state) return CCMSAV_ESTATE;
+        int r = device_status();
+        if (r) return r;
+        double* d = (double*)tmp64;
+        const int lv = previous ? prev : cur;
+        k_convert<T, double><<<1024, 256, 0, st>>>(phi[lv], d, NN);
+        k_convert<T, double><<<1024, 256, 0, st>>>(psi[lv], d + NN, NN);
+        nlaunch += 2;
+        CCM_CUDA(cudaGetLastError());
+        CCM_CUDA(cudaMemcpyAsync(ph, d, NN * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CCM_CUDA(cudaMemcpyAsync(ps, d + NN, NN * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CCM_CUDA(cudaStreamSynchronize(st));
+        return CCMSAV_OK;
+    }
+
+    int energy(double out[8]) override {
+        if (!have_state) return CCMSAV_ESTATE;
+        int r = device_status();
+        if (r) return r;
+        double s[NDIAG];
+        if ((r = diag_sums(phi[cur], phi[prev], psi[cur], s))) return r;
+        const double h2 = h() * h();
+        const DevScalars& q = *sc_host;
+        const double cb = p.gamma_bend * 3.0 * M_SQRT2 * p.eps / 8.0;
+        const double cs = p.gamma_surf * 3.0 * M_SQRT2 * p.eps / 4.0 + p.theta;
+        const double cbeta = p.gamma_surf * 3.0 * M_SQRT2 * p.beta / (4.0 * p.eps);
+        const double tt = theta_tilde();
+        double E = 0.5 * cb * h2 * (s[5] + s[6]);
+        E += 0.5 * cs * h2 * (s[4] + s[7]);
+        E -= 0.5 * tt * h2 * (s[4] + s[7] - 2.0 * s[8]);
+        E += 0.5 * cbeta * h2 * (s[9] + s[10]);
+        E += 0.5 * p.gamma_surf * 3.0 * M_SQRT2 / 2.0 * (q.V * q.V + (2 * q.V - q.Vo) * (2 * q.V - q.Vo));
+        E += 0.5 * p.gamma_area * (q.U * q.U + (2 * q.U - q.Uo) * (2 * q.U - q.Uo));
+        E += 0.5 * p.gamma_bend * 3.0 * M_SQRT2 / (8.0 * p.eps) * (q.W * q.W + (2 * q.W - q.Wo) * (2 * q.W - q.Wo));
+        E += 0.5 * (q.Z * q.Z + (2 * q.Z - q.Zo) * (2 * q.Z - q.Zo));
+        E -= q.lamsum;
+        const double arc = 3.0 * M_SQRT2 / 4.0 * (h2 * s[3] / p.eps + 0.5 * p.eps * h2 * s[4]);
+        const double Fs = p.gamma_surf * arc;
+        const double Fb = p.gamma_bend * 3.0 * M_SQRT2 / (16.0 * p.eps) * h2 * s[11];
+        const double Fa = 0.5 * p.gamma_area * (arc - q.A) * (arc - q.A);
+        const double Fo = h2 * s[12];
+        out[0] = E; out[1] = Fs; out[2] = Fb; out[3] = Fa; out[4] = Fo; out[5] = arc;
+        out[6] = q.lamsum; out[7] = Fs + Fb + Fa + Fo;
+        return CCMSAV_OK;
+    }
+
+    int mass(double* m) override {
+        if (!have_state) return CCMSAV_ESTATE;
+        int r = device_status();
+        if (r) return r;
+        double s[NDIAG];
+        if ((r = diag_sums(phi[cur], phi[cur], psi[cur], s))) return r;
+        *m = h() * h() * s[13];
+        return CCMSAV_OK;
+    }
+
+    int get_aux(double aux[12]) override {
+        if (!have_state) return CCMSAV_ESTATE;
+        int r = device_status();
+        if (r && r != CCMSAV_ENONFINITE) return r;
+        const DevScalars& q = *sc_host;
+        aux[0] = q.V; aux[1] = q.U; aux[2] = q.W; aux[3] = q.Z;
+        aux[4] = q.Vo; aux[5] = q.Uo; aux[6] = q.Wo; aux[7] = q.Zo;
+        aux[8] = q.A; aux[9] = q.lamsum; aux[10] = (double)steps_taken; aux[11] = q.mass_mode;
+        return r;
+    }
+
+    int set_aux(const double aux[12]) override {
+        if (!have_state) return CCMSAV_ESTATE;
+        for (int i = 0; i < 11; ++i) if (!std::isfinite(aux[i])) return CCMSAV_ENONFINITE;
+        int r = device_status();
+        if (r && r != CCMSAV_ENONFINITE) return r;
+        DevScalars q = *sc_host;
+        q.V = aux[0]; q.U = aux[1]; q.W = aux[2]; q.Z = aux[3];
+        q.Vo = aux[4]; q.Uo = aux[5]; q.Wo = aux[6]; q.Zo = aux[7];
+        q.A = aux[8]; q.lamsum = aux[9]; q.steps = aux[10]; q.status = 0;
+        if (aux[11] != 0.0 && std::isfinite(aux[11])) q.mass_mode = aux[11];
+        *sc_host = q;
+        CCM_CUDA(cudaMemcpyAsync(sc, sc_host, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
+        CCM_CUDA(cudaStreamSynchronize(st));
+        steps_taken = (long long)aux[10];
+        poisoned = false;
+        return CCMSAV_OK;
+    }
+
+    bool has_state() const override { return have_state; }
+    bool in_error() const override { return poisoned; }
+    long long launches() const override { return nlaunch; }
+};
+
+template <typename T>
+SimBase* make_sim(const ccmsav_params& p, int N, int flags, cudaStream_t s, int* err) {
+    SimImpl<T>* sim = new SimImpl<T>();
+    int r = sim->init(p, N, flags, s);
+    if (r != CCMSAV_OK) { delete sim; *err = r; return nullptr; }
+    *err = CCMSAV_OK;
+    return sim;
+}
+
+}  // namespace ccm

@@ -1,0 +1,636 @@
+// step_kernels.cuh -- kernels of one CC-MSAV time step (templated on the
+// field precision T = float or double).
+//
+// One step n -> n+1 (Sec. 3.2 of the paper, solved as in Appendix B) runs as
+//   k_stencil     extrapolation phi* = e1 phi^n + e2 phi^{n-1} (same for psi),
+//                 the pointwise / 5-point terms of the explicit right-hand
+//                 sides and the unnormalised basis numerators
+//                   f0 = (t1 phi^n + t2 phi^{n-1})/dt - M_phi theta~ Lap phi*
+//                   S  = phi*(phi*^2 - 1 - beta)/eps
+//                   H  = 3 sqrt2/4 [(phi*^3 - phi*)/eps - eps Lap phi*]
+//                   Q  = 6[phi*|grad phi*|^2 - div(phi*^2 grad phi*)]
+//                        + (phi*^3 - phi*)(3 phi*^2 - 1)/eps^2
+//                   K  = p'(phi*)(f_in - f_out)/2
+//                   P  = [g_in(1+p)(psi*-psi_in) + g_out(1-p)(psi*-psi_out)]/2
+//                   g0 = (t1 psi^n + t2 psi^{n-1})/dt - lam Lap psi*
+//                   LP = div(M_psi(A phi*) grad P)           (eq. mobility_flux)
+//                 and per-block partial sums of the SAV radicands and of the
+//                 explicit inner products (F, w) with w = w1 phi^n + w2 phi^{n-1}
+//                 (Appendix B Step 1);
+//   k_rowdct_T    forward DCT-II along x of the 8 fields, written transposed;
+//   k_coldct_gram forward DCT-II along y (now contiguous), spectral Gram sums
+//                 (Parseval: (u, chi^{-1} v)_h = h^2 sum_k u^ v^ / sigma_k) and
+//                 the 7 spectra needed for recovery;
+//   k_solve       FP64 reduction of the partials, the 5x5 system (Appendix B
+//                 Step 4), the SAV update and the recovery coefficients;
+//   k_comb_icolT  recovery in spectral space
+//                   phi^ = (f0^ - aS S^ - aH H^ - aQ Q^ - aK K^) / sigma,
+//                   psi^ = (g0^ + aL LP^) / tau,
+//                 inverse DCT along y, written transposed;
+//   k_irow        inverse DCT along x -> phi^{n+1}, psi^{n+1}.
+#pragma once
+#include "dct_device.cuh"
+
+namespace ccm {
+
+enum { NRED1 = 10 };   // k_stencil partials: IV IW IZ rS rH rQ rK rP minM (pad)
+enum { NRED2 = 17 };   // gram partials: 15 chi pairs (a <= b over f0 S H Q K), PG, PL
+enum { NF = 8 };       // fields out of k_stencil: f0 S H Q K P g0 LP
+enum { NSPEC = 7 };    // stored spectra: f0 S H Q K g0 LP
+
+struct StencilCoef {
+    double e1, e2;        // phi* = e1 phi^n + e2 phi^{n-1}
+    double t1, t2;        // time part of f0/g0: (t1 u^n + t2 u^{n-1}) / dt  (t1, t2 already / dt)
+    double w1, w2;        // weight of the explicit inner products
+    double inv_h, inv_h2;
+    double eps, inv_eps, inv_eps2, beta;
+    double Mth;           // M_phi * theta~
+    double lam;
+    double gin, gout, psin, psout, bin, bout;
+    double M0;
+};
+
+struct SpecCoef {          // sigma = C1 + C2 s + C3 s^2, tau = Ct + lam s, s = ev[kx] + ev[ky]
+    double C1, C2, C3, Ct, lam;
+};
+
+// Device-resident scalar state of one simulation.
+struct DevScalars {
+    double V, U, W, Z;            // level n
+    double Vo, Uo, Wo, Zo;        // level n-1
+    double A;                     // target arc length
+    double lamsum;                // sum_{j>=2} dt/2 ||d^j||^2
+    double steps;                 // steps taken
+    double mass_mode;             // conserved mean of psi (FP64), added back per point by the FP32 path
+    double alpha[5];              // recovery coefficients aS aH aQ aK aL
+    double last[8];               // IV IW IZ and diagnostics of the last step
+    int status;                   // 0 or a CCMSAV_E* code set on the device
+    int pad;
+};
+
+struct SolveCoef {
+    double h2, cgs, cga, cgb, cgo;
+    int bdf1;
+    int nb1, nb2;                 // number of partial rows
+};
+
+// ------------------------------------------------------------------ helpers
+template <typename T> __device__ __forceinline__ void sincospi_(T x, T* s, T* c);
+template <> __device__ __forceinline__ void sincospi_<float>(float x, float* s, float* c) { sincospif(x, s, c); }
+template <> __device__ __forceinline__ void sincospi_<double>(double x, double* s, double* c) { sincospi(x, s, c); }
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+template <typename T> __device__ __forceinline__ T warp_min(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Reduce NV per-thread values over the block: the T-precision warp sum
+// (FP32 for the FP32 path: at most 32 terms), then FP64 across warps.
+// Writes NV doubles to out (one row of the partials array).
+template <int NV, typename T>
+__device__ void block_sum_store(T (&v)[NV], double* out, double* sm) {
+    const int tid = threadIdx.y * blockDim.x + threadIdx.x;     // blocks may be 2D
+    const int nthr = blockDim.x * blockDim.y;
+    const int lane = tid & 31, warp = tid >> 5, nw = (nthr + 31) >> 5;
+#pragma unroll
+    for (int i = 0; i < NV; ++i) {
+        T s = warp_sum(v[i]);
+        if (lane == 0) sm[warp * NV + i] = (double)s;
+    }
+    __syncthreads();
+    if (tid < NV) {
+        double s = 0.0;
+        for (int w = 0; w < nw; ++w) s += sm[w * NV + tid];
+        out[tid] = s;
+    }
+    __syncthreads();
+}
+
+// ------------------------------------------------------------------ k_stencil
+// Tile of TX x TY cells per block (one thread per cell) with a one-cell
+// halo of phi*, psi* and of the P numerator in shared memory.  Neumann ghost
+// cells are the mirrored boundary cells (index clamping).
+constexpr int TX = 32, TY = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(TX * TY)
+k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
+          const T* __restrict__ psn, const T* __restrict__ pso,
+          T* __restrict__ out, double* __restrict__ part, int N, StencilCoef c) {
+    __shared__ T sph[TY + 2][TX + 2];
+    __shared__ T sps[TY + 2][TX + 2];
+    __shared__ T sP[TY + 2][TX + 2];
+    __shared__ double sred[(TX * TY / 32) * NRED1];
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    const int tid = threadIdx.y * TX + threadIdx.x;
+    const T e1 = (T)c.e1, e2 = (T)c.e2;
+    const T hgin = (T)(0.5 * c.gin), hgout = (T)(0.5 * c.gout);
+    for (int q = tid; q < (TX + 2) * (TY + 2); q += TX * TY) {
+        const int lj = q / (TX + 2), li = q % (TX + 2);
+        int gi = i0 + li - 1, gj = j0 + lj - 1;
+        gi = gi < 0 ? 0 : (gi >= N ? N - 1 : gi);
+        gj = gj < 0 ? 0 : (gj >= N ? N - 1 : gj);
+        const size_t g = (size_t)gj * N + gi;
+        const T ph = e1 * phn[g] + e2 * pho[g];
+        const T ps = e1 * psn[g] + e2 * pso[g];
+        sph[lj][li] = ph;
+        sps[lj][li] = ps;
+        T sp, cp;
+        sincospi_<T>((T)0.5 * ph, &sp, &cp);
+        sP[lj][li] = (T)0.5 * ((T)c.gin * ((T)1 + sp) * (ps - (T)c.psin) + (T)c.gout * ((T)1 - sp) * (ps - (T)c.psout));
+    }
+    __syncthreads();
+    const int li = threadIdx.x + 1, lj = threadIdx.y + 1;
+    const int gi = i0 + threadIdx.x, gj = j0 + threadIdx.y;
+    const size_t g = (size_t)gj * N + gi;
+    const T ih = (T)c.inv_h, ih2 = (T)c.inv_h2;
+    const T pC = sph[lj][li], pE = sph[lj][li + 1], pW = sph[lj][li - 1], pN = sph[lj + 1][li], pS = sph[lj - 1][li];
+    const T qC = sps[lj][li], qE = sps[lj][li + 1], qW = sps[lj][li - 1], qN = sps[lj + 1][li], qS = sps[lj - 1][li];
+    const T lapp = (pE + pW + pN + pS - (T)4 * pC) * ih2;
+    const T lapq = (qE + qW + qN + qS - (T)4 * qC) * ih2;
+    const T p2 = pC * pC, p3m = pC * (p2 - (T)1);
+    const T eps = (T)c.eps, ieps = (T)c.inv_eps, ieps2 = (T)c.inv_eps2;
+    // face gradients (zero on boundary faces through the mirrored ghosts)
+    const T gE = (pE - pC) * ih, gW = (pC - pW) * ih, gN = (pN - pC) * ih, gS = (pC - pS) * ih;
+    const T gbar = (T)0.5 * (gE * gE + gW * gW) + (T)0.5 * (gN * gN + gS * gS);
+    const T divp2g = (((T)0.5 * (p2 + pE * pE)) * gE - ((T)0.5 * (p2 + pW * pW)) * gW
+                      + ((T)0.5 * (p2 + pN * pN)) * gN - ((T)0.5 * (p2 + pS * pS)) * gS) * ih;
+    const T Snum = pC * (p2 - (T)1 - (T)c.beta) * ieps;
+    const T Hv = (T)1.0606601717798212866 * (p3m * ieps - eps * lapp);   // 3 sqrt2 / 4
+    const T Qnum = (T)6 * (pC * gbar - divp2g) + p3m * ((T)3 * p2 - (T)1) * ieps2;
+    T sp, cp;
+    sincospi_<T>((T)0.5 * pC, &sp, &cp);
+    const T dp = (T)1.5707963267948966192 * cp;
+    const T fin = hgin * (qC - (T)c.psin) * (qC - (T)c.psin) + (T)c.bin;
+    const T fout = hgout * (qC - (T)c.psout) * (qC - (T)c.psout) + (T)c.bout;
+    const T Knum = (T)0.5 * dp * (fin - fout);
+    const T PC = sP[lj][li];
+    // face mobilities M(A phi*) and the flux divergence of P
+    const T M0 = (T)c.M0;
+    auto mob = [&](T a) { T s = a * a - (T)1; return (T)1 - M0 * s * s; };
+    const T mE = mob((T)0.5 * (pC + pE)), mW = mob((T)0.5 * (pC + pW));
+    const T mN = mob((T)0.5 * (pC + pN)), mS = mob((T)0.5 * (pC + pS));
+    const T LP = (mE * (sP[lj][li + 1] - PC) - mW * (PC - sP[lj][li - 1])
+                  + mN * (sP[lj + 1][li] - PC) - mS * (PC - sP[lj - 1][li])) * ih2;
+    const bool inside = gi < N && gj < N;     // tiles overhang grids smaller than TX x TY
+    const size_t gc = inside ? g : 0;
+    const T phn_c = phn[gc], pho_c = pho[gc], psn_c = psn[gc], pso_c = pso[gc];
+    const T f0 = (T)c.t1 * phn_c + (T)c.t2 * pho_c - (T)c.Mth * lapp;
+    const T g0 = (T)c.t1 * psn_c + (T)c.t2 * pso_c - (T)c.lam * lapq;
+    const size_t NN = (size_t)N * N;
+    if (inside) {
+        out[0 * NN + g] = f0;
+        out[1 * NN + g] = Snum;
+        out[2 * NN + g] = Hv;
+        out[3 * NN + g] = Qnum;
+        out[4 * NN + g] = Knum;
+        out[5 * NN + g] = PC;
+        out[6 * NN + g] = g0;
+        out[7 * NN + g] = LP;
+    }
+    // partial sums
+    const T wphi = (T)c.w1 * phn_c + (T)c.w2 * pho_c;
+    const T wpsi = (T)c.w1 * psn_c + (T)c.w2 * pso_c;
+    const T vv = p2 - (T)1 - (T)c.beta;
+    T red[NRED1];
+    red[0] = vv * vv * (T)(0.25 * c.inv_eps);
+    red[1] = (T)6 * p2 * gbar + p3m * p3m * ieps2;
+    red[2] = ((T)1 + sp) * fin + ((T)1 - sp) * fout;
+    red[3] = Snum * wphi;
+    red[4] = Hv * wphi;
+    red[5] = Qnum * wphi;
+    red[6] = Knum * wphi;
+    red[7] = PC * wpsi;
+    red[8] = 0;
+    red[9] = 0;
+    if (!inside) {
+#pragma unroll
+        for (int i = 0; i < NRED1; ++i) red[i] = 0;
+    }
+    // minimum face mobility over interior faces (boundary faces carry no flux)
+    T mm = (T)1e30;
+    if (inside) {
+        if (gi + 1 < N) mm = min(mm, mE);
+        if (gi > 0) mm = min(mm, mW);
+        if (gj + 1 < N) mm = min(mm, mN);
+        if (gj > 0) mm = min(mm, mS);
+    }
+    double* prow = part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * NRED1;
+    block_sum_store<NRED1, T>(red, prow, sred);
+    mm = warp_min(mm);
+    __shared__ T smin[TX * TY / 32];
+    if ((tid & 31) == 0) smin[tid >> 5] = mm;
+    __syncthreads();
+    if (tid == 0) {
+        T m = smin[0];
+        for (int w = 1; w < TX * TY / 32; ++w) m = min(m, smin[w]);
+        prow[8] = (double)m;
+    }
+}
+
+// The pair k (0 <= k <= M/2) of the line transforms touches the modes
+// k, N-k, M-k, M+k; u indexes them.  Each mode belongs to exactly one
+// (k, u): N-0 does not exist, M-0 = M+0 and, at k = M/2, M-k = k and
+// M+k = N-k.
+__device__ __forceinline__ bool pair_mode_valid(int u, int k, int M) {
+    switch (u) {
+        case 0: return true;
+        case 1: return k > 0;
+        case 2: return k < M / 2;
+        default: return k > 0 && k < M / 2;
+    }
+}
+
+// ------------------------------------------------------------------ DCT geometry
+struct Geo {
+    int N, M;
+    int ldc;            // padded complex line length
+};
+
+// ------------------------------------------------------------------ k_rowdct_T
+// Forward DCT-II along x of RT rows (y0 .. y0+RT-1) of field blockIdx.y, then
+// a transposed write: out[f][kx][y0 + r] = X_r[kx].
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_rowdct_T(const T* __restrict__ in, T* __restrict__ out, int N, int RT, int lds,
+           const cplx<T>* __restrict__ twM, const PostTw<T>* __restrict__ twP) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int M = N / 2, ldc = padded_len(M);
+    const int E = M < 8 ? M : 8, G = M / E, P = blockDim.x / G;
+    T* stage = reinterpret_cast<T*>(smraw);                                   // RT x lds
+    cplx<T>* fb = reinterpret_cast<cplx<T>*>(smraw + (((size_t)RT * lds * sizeof(T) + 15) & ~(size_t)15));
+    const size_t NN = (size_t)N * N;
+    const int f = blockIdx.y;
+    const int y0 = blockIdx.x * RT;
+    const T* src = in + f * NN;
+    const T cn0 = (T)sqrt(1.0 / N), cn = (T)sqrt(2.0 / N);
+    for (int r0 = 0; r0 < RT; r0 += P) {
+        const int nr = min(P, RT - r0);
+        // pack nr rows
+        for (int q = threadIdx.x; q < nr * (M / 2); q += blockDim.x) {
+            const int r = q / (M / 2), m = q % (M / 2);
+            pack4(fb + (size_t)r * ldc, M, m, ld4(src + (size_t)(y0 + r0 + r) * N + 4 * m));
+        }
+        __syncthreads();
+        fft_lines<T, false>(fb, ldc, nr, M, twM);
+        for (int q = threadIdx.x; q < nr * (M / 2 + 1); q += blockDim.x) {
+            const int r = q / (M / 2 + 1), k = q % (M / 2 + 1);
+            Quad<T> X = post_forward(fb + (size_t)r * ldc, M, k, twP[k], cn0, cn);
+            T* srow = stage + (size_t)(r0 + r) * lds;
+            srow[k] = X.xk;
+            if (pair_mode_valid(1, k, M)) srow[N - k] = X.xNk;
+            if (pair_mode_valid(2, k, M)) srow[M - k] = X.xMk;
+            if (pair_mode_valid(3, k, M)) srow[M + k] = X.xMpk;
+        }
+        __syncthreads();
+    }
+    T* dst = out + f * NN;
+    for (int q = threadIdx.x; q < RT * N; q += blockDim.x) {
+        const int r = q % RT, kx = q / RT;
+        dst[(size_t)kx * N + y0 + r] = stage[(size_t)r * lds + kx];
+    }
+}
+
+// ------------------------------------------------------------------ k_coldct_gram
+// One spectral row kx per block: forward DCT-II along y of the 8 transposed
+// fields, Gram partial sums, and the spectra spec[f][kx][ky] (slots in the
+// order f0 S H Q K P g0 LP; slot 5 (P) is only written when the fields are
+// transformed in groups, because P^ enters the Gram sums only).
+// FG = number of field lines that fit in shared memory at once (8, 4, 2, 1).
+template <typename T>
+__device__ __forceinline__ void gram_accumulate(T (&acc)[NRED2], const T (&v)[NF], T isig, T itau) {
+    int p = 0;
+#pragma unroll
+    for (int a = 0; a < 5; ++a)
+#pragma unroll
+        for (int b = a; b < 5; ++b) acc[p++] += v[a] * v[b] * isig;
+    acc[15] += v[5] * v[6] * itau;
+    acc[16] += v[5] * v[7] * itau;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_coldct_gram(const T* __restrict__ in, T* __restrict__ spec, double* __restrict__ part, int N, int FG,
+              const cplx<T>* __restrict__ twM, const PostTw<T>* __restrict__ twP,
+              const double* __restrict__ ev, SpecCoef sc) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    __shared__ double sred[16 * NRED2];
+    const int M = N / 2, ldc = padded_len(M);
+    cplx<T>* fb = reinterpret_cast<cplx<T>*>(smraw);
+    const size_t NN = (size_t)N * N;
+    const int kx = blockIdx.x;
+    const T cn0 = (T)sqrt(1.0 / N), cn = (T)sqrt(2.0 / N);
+    T acc[NRED2];
+#pragma unroll
+    for (int i = 0; i < NRED2; ++i) acc[i] = 0;
+    const double evx = ev[kx];
+    for (int fg0 = 0; fg0 < NF; fg0 += FG) {
+        for (int q = threadIdx.x; q < FG * (M / 2); q += blockDim.x) {
+            const int f = q / (M / 2), m = q % (M / 2);
+            pack4(fb + (size_t)f * ldc, M, m, ld4(in + (fg0 + f) * NN + (size_t)kx * N + 4 * m));
+        }
+        __syncthreads();
+        fft_lines<T, false>(fb, ldc, FG, M, twM);
+        if (FG == NF) {
+            for (int k = threadIdx.x; k <= M / 2; k += blockDim.x) {
+                Quad<T> X[NF];
+#pragma unroll
+                for (int f = 0; f < NF; ++f) X[f] = post_forward(fb + (size_t)f * ldc, M, k, twP[k], cn0, cn);
+                const int kys[4] = {k, N - k, M - k, M + k};
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    if (!pair_mode_valid(u, k, M)) continue;
+                    const int ky = kys[u];
+                    const double s = evx + ev[ky];
+                    const T isig = (T)(1.0 / (sc.C1 + sc.C2 * s + sc.C3 * s * s));
+                    const T itau = (T)(1.0 / (sc.Ct + sc.lam * s));
+                    T v[NF];
+#pragma unroll
+                    for (int f = 0; f < NF; ++f)
+                        v[f] = (u == 0) ? X[f].xk : (u == 1) ? X[f].xNk : (u == 2) ? X[f].xMk : X[f].xMpk;
+                    gram_accumulate(acc, v, isig, itau);
+                    const size_t o = (size_t)kx * N + ky;
+#pragma unroll
+                    for (int f = 0; f < NF; ++f)
+                        if (f != 5) spec[f * NN + o] = v[f];
+                }
+            }
+        } else {
+            for (int q = threadIdx.x; q < FG * (M / 2 + 1); q += blockDim.x) {
+                const int f = q / (M / 2 + 1), k = q % (M / 2 + 1);
+                Quad<T> X = post_forward(fb + (size_t)f * ldc, M, k, twP[k], cn0, cn);
+                T* row = spec + (fg0 + f) * NN + (size_t)kx * N;
+                row[k] = X.xk;
+                if (pair_mode_valid(1, k, M)) row[N - k] = X.xNk;
+                if (pair_mode_valid(2, k, M)) row[M - k] = X.xMk;
+                if (pair_mode_valid(3, k, M)) row[M + k] = X.xMpk;
+            }
+        }
+        __syncthreads();
+    }
+    if (FG != NF) {
+        // Gram sums from the row just written (visible to the block after the barrier)
+        for (int ky = threadIdx.x; ky < N; ky += blockDim.x) {
+            const double s = evx + ev[ky];
+            const T isig = (T)(1.0 / (sc.C1 + sc.C2 * s + sc.C3 * s * s));
+            const T itau = (T)(1.0 / (sc.Ct + sc.lam * s));
+            T v[NF];
+#pragma unroll
+            for (int f = 0; f < NF; ++f) v[f] = spec[f * NN + (size_t)kx * N + ky];
+            gram_accumulate(acc, v, isig, itau);
+        }
+    }
+    block_sum_store<NRED2, T>(acc, part + (size_t)kx * NRED2, sred);
+}
+
+// ------------------------------------------------------------------ k_solve
+// Single block: FP64 reduction of both partial arrays in a fixed order, then
+// (thread 0) the scalar algebra of Appendix B Steps 1 and 4.
+__device__ inline bool finite_(double x) { return isfinite(x); }
+
+static __global__ void __launch_bounds__(512)
+k_solve(const double* __restrict__ p1, const double* __restrict__ p2, DevScalars* sc, SolveCoef co) {
+    constexpr int NR = NRED1 + NRED2;
+    __shared__ double red[16][NR];
+    __shared__ double fin_[NR];
+    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
+    double acc[NR];
+#pragma unroll
+    for (int i = 0; i < NR; ++i) acc[i] = 0.0;
+    double mmin = 1e300;
+    for (int b = t; b < co.nb1; b += blockDim.x) {
+        const double* q = p1 + (size_t)b * NRED1;
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] += q[i];
+        mmin = fmin(mmin, q[8]);
+    }
+    for (int b = t; b < co.nb2; b += blockDim.x) {
+        const double* q = p2 + (size_t)b * NRED2;
+#pragma unroll
+        for (int i = 0; i < NRED2; ++i) acc[NRED1 + i] += q[i];
+    }
+    acc[8] = mmin;
+    // fixed-order tree: warp shuffles, then the 16 warp results in order
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        double v = acc[i];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double w = __shfl_xor_sync(0xffffffffu, v, o);
+            v = (i == 8) ? fmin(v, w) : v + w;
+        }
+        if (lane == 0) red[wp][i] = v;
+    }
+    __syncthreads();
+    if (t < NR) {
+        double v = red[0][t];
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = (t == 8) ? fmin(v, red[w][t]) : v + red[w][t];
+        fin_[t] = v;
+    }
+    __syncthreads();
+    if (t != 0) return;
+    if (sc->status != 0) return;
+    const double* r = fin_;
+    const double IV = r[0], IW = r[1], IZ = r[2];
+    const double rS = r[3], rH = r[4], rQ = r[5], rK = r[6], rP = r[7], minM = r[8];
+    const double* Gm = r + NRED1;
+    bool ok = true;
+    for (int i = 0; i < NRED1 + NRED2; ++i) ok = ok && finite_(r[i]);
+    ok = ok && IV > 0 && IW > 0 && IZ > 0 && minM > 0;
+    if (!ok) { sc->status = -5; return; }
+    const double h2 = co.h2;
+    const double nS = 0.5 / sqrt(h2 * IV), nQ = 1.0 / sqrt(h2 * IW), nK = 1.0 / sqrt(h2 * IZ);
+    const double nrm[4] = {nS, 1.0, nQ, nK};
+    double aV, aU, aW, aZ;
+    if (co.bdf1) {
+        aV = sc->V + h2 * nS * rS;
+        aU = sc->U + h2 * rH;
+        aW = sc->W + h2 * nQ * rQ;
+        aZ = sc->Z + h2 * nK * (rK + rP);
+    } else {
+        aV = (4.0 * sc->V - sc->Vo + h2 * nS * rS) / 3.0;
+        aU = (4.0 * sc->U - sc->Uo + h2 * rH) / 3.0;
+        aW = (4.0 * sc->W - sc->Wo + h2 * nQ * rQ) / 3.0;
+        aZ = (4.0 * sc->Z - sc->Zo + h2 * nK * (rK + rP)) / 3.0;
+    }
+    const double av[4] = {aV, aU, aW, aZ};
+    const double cc[4] = {co.cgs, co.cga, co.cgb, co.cgo};
+    // Gram index for a <= b over (f0, S, H, Q, K)
+    auto G = [&](int a, int b) {
+        if (a > b) { int x = a; a = b; b = x; }
+        int idx = 0;
+        for (int i = 0; i < a; ++i) idx += 5 - i;
+        return Gm[idx + (b - a)];
+    };
+    double A[5][6];
+    for (int i = 0; i < 4; ++i) {
+        double bi = G(0, i + 1);
+        for (int j = 0; j < 4; ++j) {
+            const double gij = h2 * nrm[i] * nrm[j] * G(i + 1, j + 1);
+            A[i][j] = (i == j ? 1.0 : 0.0) + cc[j] * gij;
+            bi -= cc[j] * av[j] * nrm[j] * G(i + 1, j + 1);
+        }
+        A[i][4] = co.cgo * h2 * nrm[i] * nK * G(i + 1, 4);
+        A[i][5] = h2 * nrm[i] * bi;
+    }
+    const double PL = h2 * nK * nK * Gm[16];
+    A[4][0] = A[4][1] = A[4][2] = 0.0;
+    A[4][3] = -PL;
+    A[4][4] = 1.0 - PL;
+    A[4][5] = h2 * nK * Gm[15] + aZ * PL;
+    // Gaussian elimination with partial pivoting
+    for (int k = 0; k < 5; ++k) {
+        int piv = k;
+        for (int i = k + 1; i < 5; ++i) if (fabs(A[i][k]) > fabs(A[piv][k])) piv = i;
+        if (piv != k) for (int j = 0; j < 6; ++j) { double x = A[k][j]; A[k][j] = A[piv][j]; A[piv][j] = x; }
+        const double d = A[k][k];
+        if (!(fabs(d) > 0)) { sc->status = -5; return; }
+        for (int i = k + 1; i < 5; ++i) {
+            const double f = A[i][k] / d;
+            for (int j = k; j < 6; ++j) A[i][j] -= f * A[k][j];
+        }
+    }
+    double x[5];
+    for (int i = 4; i >= 0; --i) {
+        double s = A[i][5];
+        for (int j = i + 1; j < 5; ++j) s -= A[i][j] * x[j];
+        x[i] = s / A[i][i];
+    }
+    const double Vn = aV + x[0], Un = aU + x[1], Wn = aW + x[2], Zn = aZ + x[3] + x[4];
+    bool ok2 = finite_(Vn) && finite_(Un) && finite_(Wn) && finite_(Zn);
+    if (!ok2) { sc->status = -5; return; }
+    sc->Vo = sc->V; sc->Uo = sc->U; sc->Wo = sc->W; sc->Zo = sc->Z;
+    sc->V = Vn; sc->U = Un; sc->W = Wn; sc->Z = Zn;
+    sc->alpha[0] = co.cgs * Vn * nS;
+    sc->alpha[1] = co.cga * Un;
+    sc->alpha[2] = co.cgb * Wn * nQ;
+    sc->alpha[3] = co.cgo * Zn * nK;
+    sc->alpha[4] = Zn * nK;
+    sc->last[0] = IV; sc->last[1] = IW; sc->last[2] = IZ; sc->last[3] = minM;
+    sc->steps += 1.0;
+}
+
+// ------------------------------------------------------------------ k_comb_icolT
+// Rows kx0 .. kx0+RT-1 of the spectra: recovery combination, inverse DCT
+// along ky (DCT-III), transposed write out[f][y][kx] for f = phi, psi.
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_comb_icolT(const T* __restrict__ spec, T* __restrict__ out, int N, int RT, int lds,
+             const cplx<T>* __restrict__ twM, const PostTw<T>* __restrict__ twP,
+             const double* __restrict__ ev, SpecCoef sc, const DevScalars* __restrict__ dsc,
+             int anchor_mass) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int M = N / 2, ldc = padded_len(M);
+    const int E = M < 8 ? M : 8, G = M / E, P = blockDim.x / G;
+    T* stage = reinterpret_cast<T*>(smraw);                                   // 2 RT x lds
+    cplx<T>* fb = reinterpret_cast<cplx<T>*>(smraw + (((size_t)2 * RT * lds * sizeof(T) + 15) & ~(size_t)15));
+    const size_t NN = (size_t)N * N;
+    const int kx0 = blockIdx.x * RT;
+    const T inv0 = (T)(1.0 / (M * sqrt(1.0 / N))), inv = (T)(1.0 / (M * sqrt(2.0 / N)));
+    const T aS = (T)dsc->alpha[0], aH = (T)dsc->alpha[1], aQ = (T)dsc->alpha[2], aK = (T)dsc->alpha[3], aL = (T)dsc->alpha[4];
+    const int nlines = 2 * RT;   // line l: row r = l / 2, field f = l % 2
+    for (int l0 = 0; l0 < nlines; l0 += P) {
+        const int nl = min(P, nlines - l0);
+        for (int q = threadIdx.x; q < nl * (M / 2 + 1); q += blockDim.x) {
+            const int l = l0 + q / (M / 2 + 1), k = q % (M / 2 + 1);
+            const int r = l >> 1, f = l & 1;
+            const int kx = kx0 + r;
+            const double evx = ev[kx];
+            const int kys[4] = {k, N - k, M - k, M + k};
+            T vals[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                int ky = kys[u];
+                if (u == 1 && k == 0) { vals[u] = 0; continue; }
+                const double s = evx + ev[ky];
+                const size_t o = (size_t)kx * N + ky;
+                if (f == 0) {
+                    const T isig = (T)(1.0 / (sc.C1 + sc.C2 * s + sc.C3 * s * s));
+                    vals[u] = (spec[0 * NN + o] - aS * spec[1 * NN + o] - aH * spec[2 * NN + o]
+                               - aQ * spec[3 * NN + o] - aK * spec[4 * NN + o]) * isig;
+                } else {
+                    const T itau = (T)(1.0 / (sc.Ct + sc.lam * s));
+                    vals[u] = (spec[6 * NN + o] + aL * spec[7 * NN + o]) * itau;
+                    // FP32 path: the mean of psi (the zero mode) is not carried through the
+                    // FP32 transforms; k_irow adds the conserved FP64 mean back per point.
+                    if (anchor_mass && kx == 0 && ky == 0) vals[u] = (T)0;
+                }
+            }
+            Quad<T> X{vals[0], vals[1], vals[2], vals[3]};
+            cplx<T> zk, zMk;
+            pre_inverse(X, k, twP[k], inv0, inv, zk, zMk);
+            cplx<T>* z = fb + (size_t)(l - l0) * ldc;
+            z[padc(k)] = zk;
+            if (k > 0) z[padc(M - k)] = zMk;
+        }
+        __syncthreads();
+        fft_lines<T, true>(fb, ldc, nl, M, twM);
+        for (int q = threadIdx.x; q < nl * (M / 2); q += blockDim.x) {
+            const int l = l0 + q / (M / 2), m = q % (M / 2);
+            vec4<T> v = unpack4(fb + (size_t)(l - l0) * ldc, M, m);
+            const int r = l >> 1, f = l & 1;
+            T* srow = stage + (size_t)(f * RT + r) * lds + 4 * m;
+            srow[0] = v.a; srow[1] = v.b; srow[2] = v.c; srow[3] = v.d;
+        }
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < 2 * RT * N; q += blockDim.x) {
+        const int r = q % RT, rest = q / RT;
+        const int y = rest % N, f = rest / N;
+        out[f * NN + (size_t)y * N + kx0 + r] = stage[(size_t)(f * RT + r) * lds + y];
+    }
+}
+
+// ------------------------------------------------------------------ k_irow
+// Inverse DCT along x of PR rows (2 fields each) of the transposed buffer:
+// in[f][y][kx] -> phi_new / psi_new [y][x].
+template <typename T>
+__global__ void __launch_bounds__(512)
+k_irow(const T* __restrict__ in, T* __restrict__ phi_new, T* __restrict__ psi_new, int N, int PR,
+       const cplx<T>* __restrict__ twM, const PostTw<T>* __restrict__ twP,
+       const DevScalars* __restrict__ dsc, int anchor_mass) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const int M = N / 2, ldc = padded_len(M);
+    const int E = M < 8 ? M : 8, G = M / E, P = blockDim.x / G;
+    cplx<T>* fb = reinterpret_cast<cplx<T>*>(smraw);
+    const size_t NN = (size_t)N * N;
+    const int y0 = blockIdx.x * PR;
+    const T inv0 = (T)(1.0 / (M * sqrt(1.0 / N))), inv = (T)(1.0 / (M * sqrt(2.0 / N)));
+    const int nlines = 2 * PR;
+    const double mean = anchor_mass ? dsc->mass_mode : 0.0;
+    for (int l0 = 0; l0 < nlines; l0 += P) {
+        const int nl = min(P, nlines - l0);
+        for (int q = threadIdx.x; q < nl * (M / 2 + 1); q += blockDim.x) {
+            const int l = l0 + q / (M / 2 + 1), k = q % (M / 2 + 1);
+            const int r = l >> 1, f = l & 1;
+            const T* row = in + f * NN + (size_t)(y0 + r) * N;
+            Quad<T> X{row[k], k > 0 ? row[N - k] : (T)0, row[M - k], row[M + k]};
+            cplx<T> zk, zMk;
+            pre_inverse(X, k, twP[k], inv0, inv, zk, zMk);
+            cplx<T>* z = fb + (size_t)(l - l0) * ldc;
+            z[padc(k)] = zk;
+            if (k > 0) z[padc(M - k)] = zMk;
+        }
+        __syncthreads();
+        fft_lines<T, true>(fb, ldc, nl, M, twM);
+        for (int q = threadIdx.x; q < nl * (M / 2); q += blockDim.x) {
+            const int l = l0 + q / (M / 2), m = q % (M / 2);
+            const int r = l >> 1, f = l & 1;
+            T* dst = (f == 0 ? phi_new : psi_new) + (size_t)(y0 + r) * N + 4 * m;
+            vec4<T> v = unpack4(fb + (size_t)(l - l0) * ldc, M, m);
+            if (f == 1 && anchor_mass) {
+                v.a = (T)((double)v.a + mean); v.b = (T)((double)v.b + mean);
+                v.c = (T)((double)v.c + mean); v.d = (T)((double)v.d + mean);
+            }
+            st4(dst, v);
+        }
+        __syncthreads();
+    }
+}
+
+}  // namespace ccm

