@@ -177,6 +177,32 @@ long long ccmsav_launch_count(ccmsav_t* h);
 int ccmsav_profile(ccmsav_t* h, int enable);
 int ccmsav_profile_read(ccmsav_t* h, int sim, double ms[8], long long* nsteps);
 
+/* Largest grid side accepted by ccmsav_mass_noalloc(). */
+#define CCMSAV_NOALLOC_MAX_N 8192
+
+/* ccmsav_mass_noalloc -- h^2 * sum_ij psi_ij (h = L / N) of a caller-owned
+ * device field, with no device or host allocation by the library.
+ * The paper has no counterpart: this is a service for callers that cannot
+ * let a library allocate, e.g. code running while a stream is captured into
+ * a CUDA graph, services whose device memory is reserved up front by a
+ * pooling allocator, or real-time loops that must not pay allocation
+ * latency.  It computes what ccmsav_mass() computes for a handle's state,
+ * but for any N x N field the caller holds.
+ *   psi        device pointer, N*N values, FP64 (precision CCMSAV_FP64) or
+ *              FP32 (CCMSAV_FP32_BULK); summed in FP64 in a fixed order
+ *   N          1 <= N <= CCMSAV_NOALLOC_MAX_N, else CCMSAV_EINVAL
+ *   L          domain side (> 0)
+ *   mass       host pointer to one double (output)
+ *   stream     cudaStream_t the work is queued on; the call synchronises it
+ * Scratch is a fixed array of under 10 KB compiled into the library; every
+ * GPU that loads the library holds it until the process exits.  The first
+ * call on a device looks up that array's device address (with the device
+ * current), so make the first call before any stream capture.  All calls
+ * share the array: calls whose work overlaps on the GPU (different streams
+ * or host threads) race and must be serialised by the caller. */
+int ccmsav_mass_noalloc(const void* psi, int N, int precision, double L,
+                        double* mass, void* stream);
+
 /* Message for a status code (static storage). */
 const char* ccmsav_strerror(int status);
 

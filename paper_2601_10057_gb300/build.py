@@ -16,7 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libccmsav.so")
-SOURCES = ["ccmsav_api.cu", "sim_f32.cu", "sim_f64.cu"]
+SOURCES = ["ccmsav_api.cu", "sim_f32.cu", "sim_f64.cu", "ccmsav_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

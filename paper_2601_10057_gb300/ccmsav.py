@@ -82,6 +82,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "ccmsav_profile": (i, [vp, i]),
         "ccmsav_profile_read": (i, [vp, i, _DP, C.POINTER(C.c_longlong)]),
         "ccmsav_destroy": (None, [vp]),
+        "ccmsav_mass_noalloc": (i, [vp, i, i, d, _DP, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -202,6 +203,15 @@ def ccmsav_profile_read(h, sim: int = 0):
 def ccmsav_destroy(h) -> None:
     if h:
         load().ccmsav_destroy(h)
+
+
+def ccmsav_mass_noalloc(psi_ptr: int, N: int, precision: int, L: float, stream: Optional[int] = None):
+    """Mass of a caller-owned device field without library allocation.
+    Returns (status, mass)."""
+    out = np.zeros(1, np.float64)
+    st = load().ccmsav_mass_noalloc(C.c_void_p(psi_ptr), int(N), int(precision), float(L), _ptr(out),
+                                    C.c_void_p(stream) if stream else None)
+    return st, float(out[0])
 
 
 # ---------------------------------------------------------------- wrapper
