@@ -115,6 +115,16 @@ k_add_lamsum(const double* __restrict__ part, int nb, double scale, DevScalars* 
     if (threadIdx.x == 0 && sc->status == 0) sc->lamsum += scale * red[0];
 }
 
+// FP64 -> FP32 with the dithered rounding of dither_round (initial psi of
+// the FP32 path, so its stored mass carries no coherent rounding error).
+static __global__ void k_convert_dither(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+    for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
+        const double x = in[q];
+        const float s = (float)x;
+        out[q] = dither_round(s, (float)(x - (double)s), dither_key(0xffffffffu, (uint32_t)q) | 1u);
+    }
+}
+
 template <typename Tsrc, typename Tdst>
 __global__ void k_convert(const Tsrc* __restrict__ in, Tdst* __restrict__ out, size_t n) {
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x)

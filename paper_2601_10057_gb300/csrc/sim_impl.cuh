@@ -15,10 +15,13 @@
 //   sc               DevScalars (SAVs, recovery coefficients, status)
 #pragma once
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 #include "sim.h"
 #include "diag_kernels.cuh"
+#include "warp_kernels.cuh"
+#include <type_traits>
 
 namespace ccm {
 
@@ -51,6 +54,12 @@ public:
     PostTw<T>* twP = nullptr;
     double* ev = nullptr;
     DevScalars* sc = nullptr;
+    // FP32 warp-FFT path (N = 128 .. 2048): twiddle matrix W_M^{n2 k1} and FP32 eigenvalues
+    bool warp_path = false;
+    cplx<float>* tw2 = nullptr;
+    float* evf = nullptr;
+    int wRT = 8, wlds = 0, wRT4 = 4, wlds4 = 0, wKC = 1, wRI = 4;
+    size_t wsm_rt = 0, wsm_col = 0, wsm_comb = 0, wsm_irow = 0;
     DevScalars* sc_host = nullptr;   // pinned
     double* h_part = nullptr;        // pinned, diag partial rows
     void* tmp64 = nullptr;           // FP64 staging for host I/O
@@ -125,6 +134,7 @@ public:
         for (int i = 0; i < 3; ++i) { cudaFree(phi[i]); cudaFree(psi[i]); phi[i] = psi[i] = nullptr; }
         cudaFree(bufA); cudaFree(bufB); cudaFree(part1); cudaFree(part2); cudaFree(partd);
         cudaFree(twM); cudaFree(twP); cudaFree(ev); cudaFree(sc); cudaFree(tmp64);
+        cudaFree(tw2); cudaFree(evf); tw2 = nullptr; evf = nullptr;
         if (sc_host) cudaFreeHost(sc_host);
         if (h_part) cudaFreeHost(h_part);
         bufA = bufB = nullptr; part1 = part2 = partd = nullptr; twM = nullptr; twP = nullptr;
@@ -213,8 +223,110 @@ public:
         if (set_smem_limit((const void*)k_rowdct_T<T>, sm_rt) || set_smem_limit((const void*)k_coldct_gram<T>, sm_col) ||
             set_smem_limit((const void*)k_comb_icolT<T>, sm_comb) || set_smem_limit((const void*)k_irow<T>, sm_irow))
             return CCMSAV_ECUDA;
+        const char* force_block = std::getenv("CCMSAV_FORCE_BLOCK_FFT");   // test switch: block-FFT kernels only
+        if (std::is_same<T, float>::value && M >= 64 && M <= 1024 && !(force_block && force_block[0] == '1')) {
+            int r = init_warp_path();
+            if (r) return r;
+        }
         CCM_CUDA(cudaStreamSynchronize(st));
         return CCMSAV_OK;
+    }
+
+    template <int MM> int setup_warp() {
+        using Gm = WGeo<MM>;
+        constexpr int G = Gm::G, E = Gm::E;
+        std::vector<cplx<float>> h2((size_t)MM);
+        for (int k1 = 0; k1 < E; ++k1)
+            for (int n2 = 0; n2 < G; ++n2) {
+                const double a = 2.0 * M_PI * (double)((long)n2 * k1 % MM) / MM;
+                h2[(size_t)k1 * G + n2].x = (float)std::cos(a);
+                h2[(size_t)k1 * G + n2].y = (float)(-std::sin(a));
+            }
+        if (cudaMalloc(&tw2, MM * sizeof(cplx<float>)) != cudaSuccess) return CCMSAV_ENOMEM;
+        CCM_CUDA(cudaMemcpyAsync(tw2, h2.data(), MM * sizeof(cplx<float>), cudaMemcpyHostToDevice, st));
+        const size_t bb = Gm::buf_bytes();
+        wRT = (N >= 2048) ? 8 : 16;
+        wlds = N + 32 / wRT;
+        wsm_rt = bb + (size_t)wRT * wlds * sizeof(float);
+        wKC = Gm::SLOTS / NF;
+        wsm_col = bb;
+        wRT4 = 4;
+        wlds4 = N + 8;
+        wsm_comb = bb + (size_t)2 * wRT4 * wlds4 * sizeof(float);
+        wRI = Gm::SLOTS / 2;
+        wsm_irow = bb;
+        if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col) ||
+            set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
+            return CCMSAV_ECUDA;
+        return CCMSAV_OK;
+    }
+
+    int init_warp_path() {
+        std::vector<float> he(N);
+        const double hh = p.L / N;
+        for (int k = 0; k < N; ++k) { const double s = std::sin(M_PI * k / (2.0 * N)); he[k] = (float)(4.0 * s * s / (hh * hh)); }
+        if (cudaMalloc(&evf, N * sizeof(float)) != cudaSuccess) return CCMSAV_ENOMEM;
+        CCM_CUDA(cudaMemcpyAsync(evf, he.data(), N * sizeof(float), cudaMemcpyHostToDevice, st));
+        int r = CCMSAV_EINVAL;
+        if constexpr (std::is_same<T, float>::value)
+        switch (M) {
+            case 64: r = setup_warp<64>(); break;
+            case 128: r = setup_warp<128>(); break;
+            case 256: r = setup_warp<256>(); break;
+            case 512: r = setup_warp<512>(); break;
+            case 1024: r = setup_warp<1024>(); break;
+        }
+        if (r == CCMSAV_OK) warp_path = true;
+        return r;
+    }
+
+    // The FFT kernels of one step on the warp path (FP32 only).
+    template <int MM>
+    void launch_warp_ffts(const SpecCoef& s, int anchor) {
+        SpecCoefF sf{(float)s.C1, (float)s.C2, (float)s.C3, (float)s.Ct, (float)s.lam};
+        const float* fin = reinterpret_cast<const float*>(bufA);
+        float* fB = reinterpret_cast<float*>(bufB);
+        const cplx<float>* t2 = tw2;
+        const PostTw<float>* tp = reinterpret_cast<const PostTw<float>*>(twP);
+        kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, wRT, wlds, t2, tp);
+        mark(1);
+        kw_coldct_gram<MM><<<N / wKC, kWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2, t2, tp, evf, sf);
+        mark(2);
+    }
+    int bdf1_launch = 0;
+    template <int MM>
+    void launch_warp_inverse(const SpecCoef& s, int anchor) {
+        SpecCoefF sf{(float)s.C1, (float)s.C2, (float)s.C3, (float)s.Ct, (float)s.lam};
+        const PostTw<float>* tp = reinterpret_cast<const PostTw<float>*>(twP);
+        kw_comb_icolT<MM><<<N / wRT4, kWarps * 32, wsm_comb, st>>>(reinterpret_cast<const float*>(bufA),
+            reinterpret_cast<float*>(bufB), wRT4, wlds4, tw2, tp, evf, sf, sc, anchor);
+        mark(4);
+        kw_irow<MM><<<N / wRI, kWarps * 32, wsm_irow, st>>>(reinterpret_cast<const float*>(bufB),
+            reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), wRI, tw2, tp,
+            reinterpret_cast<const float*>(phi[cur]), reinterpret_cast<const float*>(phi[prev]),
+            reinterpret_cast<const float*>(psi[cur]), reinterpret_cast<const float*>(psi[prev]),
+            bdf1_launch, sc, anchor, (uint32_t)steps_taken);
+        mark(5);
+    }
+    void warp_forward(const SpecCoef& s, int anchor) {
+        if constexpr (std::is_same<T, float>::value)
+        switch (M) {
+            case 64: launch_warp_ffts<64>(s, anchor); break;
+            case 128: launch_warp_ffts<128>(s, anchor); break;
+            case 256: launch_warp_ffts<256>(s, anchor); break;
+            case 512: launch_warp_ffts<512>(s, anchor); break;
+            default: launch_warp_ffts<1024>(s, anchor); break;
+        }
+    }
+    void warp_inverse(const SpecCoef& s, int anchor) {
+        if constexpr (std::is_same<T, float>::value)
+        switch (M) {
+            case 64: launch_warp_inverse<64>(s, anchor); break;
+            case 128: launch_warp_inverse<128>(s, anchor); break;
+            case 256: launch_warp_inverse<256>(s, anchor); break;
+            case 512: launch_warp_inverse<512>(s, anchor); break;
+            default: launch_warp_inverse<1024>(s, anchor); break;
+        }
     }
 
     double h() const { return p.L / N; }
@@ -245,7 +357,10 @@ public:
         const size_t nb = NN * sizeof(double);
         auto conv = [&](const double* host, T* dst) -> int {
             CCM_CUDA(cudaMemcpyAsync(d, host, nb, cudaMemcpyHostToDevice, st));
-            k_convert<double, T><<<1024, 256, 0, st>>>(d, dst, NN);
+            if (std::is_same<T, float>::value && (dst == psi[cur] || dst == psi[prev]))
+                k_convert_dither<<<1024, 256, 0, st>>>(d, reinterpret_cast<float*>(dst), NN);
+            else
+                k_convert<double, T><<<1024, 256, 0, st>>>(d, dst, NN);
             ++nlaunch;
             CCM_CUDA(cudaGetLastError());
             CCM_CUDA(cudaStreamSynchronize(st));
@@ -317,11 +432,13 @@ public:
         const bool bdf1 = (steps_taken == 0);
         const double dt = p.dt;
         StencilCoef c;
-        if (bdf1) { c.e1 = 1; c.e2 = 0; c.t1 = 1.0 / dt; c.t2 = 0; c.w1 = -1; c.w2 = 0; }
-        else { c.e1 = 2; c.e2 = -1; c.t1 = 2.0 / dt; c.t2 = -0.5 / dt; c.w1 = -4; c.w2 = 1; }
+        c.bdf1 = bdf1 ? 1 : 0;
         c.inv_h = 1.0 / h(); c.inv_h2 = 1.0 / (h() * h());
         c.eps = p.eps; c.inv_eps = 1.0 / p.eps; c.inv_eps2 = 1.0 / (p.eps * p.eps); c.beta = p.beta;
         c.Mth = p.M_phi * theta_tilde(); c.lam = p.lam;
+        c.C2 = p.M_phi * (p.gamma_surf * 3.0 * M_SQRT2 * p.eps / 4.0 + p.theta);
+        c.C3 = p.M_phi * p.gamma_bend * 3.0 * M_SQRT2 * p.eps / 8.0;
+        c.betap = p.M_phi * p.gamma_surf * 3.0 * M_SQRT2 * p.beta / (4.0 * p.eps);
         c.gin = p.gamma_in; c.gout = p.gamma_out; c.psin = p.psi_in; c.psout = p.psi_out;
         c.bin = p.beta_in; c.bout = p.beta_out; c.M0 = p.M0;
         SpecCoef s;
@@ -338,22 +455,36 @@ public:
         so.cgo = p.M_phi;
         so.bdf1 = bdf1 ? 1 : 0;
         so.nb1 = nb1; so.nb2 = N;
+        so.NN = (double)NN;
         const int anchor = (sizeof(T) == sizeof(float)) ? 1 : 0;
+        so.anchor = anchor;
 
         if (prof && ev_used + 16 > 4096) { int r = profile_flush(); if (r) return r; }
         mark(-1);
         k_stencil<T><<<g_st, b_st, 0, st>>>(phi[cur], phi[prev], psi[cur], psi[prev], bufA, part1, N, c);
         mark(0);
-        k_rowdct_T<T><<<dim3(N / RT, NF), 512, sm_rt, st>>>(bufA, bufB, N, RT, lds_rt, twM, twP);
-        mark(1);
-        k_coldct_gram<T><<<N, 512, sm_col, st>>>(bufB, bufA, part2, N, FG, twM, twP, ev, s);
-        mark(2);
+        if (warp_path) {
+            warp_forward(s, anchor);
+            so.nb2 = N / wKC;
+        } else {
+            k_rowdct_T<T><<<dim3(N / RT, NF), 512, sm_rt, st>>>(bufA, bufB, N, RT, lds_rt, twM, twP);
+            mark(1);
+            k_coldct_gram<T><<<N, 512, sm_col, st>>>(bufB, bufA, part2, N, FG, twM, twP, ev, s);
+            mark(2);
+        }
         k_solve<<<1, 512, 0, st>>>(part1, part2, sc, so);
         mark(3);
-        k_comb_icolT<T><<<N / RT4, 512, sm_comb, st>>>(bufA, bufB, N, RT4, lds_c, twM, twP, ev, s, sc, anchor);
-        mark(4);
-        k_irow<T><<<N / PR, 512, sm_irow, st>>>(bufB, phi[spare], psi[spare], N, PR, twM, twP, sc, anchor);
-        mark(5);
+        if (warp_path) {
+            bdf1_launch = so.bdf1;
+            warp_inverse(s, anchor);
+        } else {
+            k_comb_icolT<T><<<N / RT4, 512, sm_comb, st>>>(bufA, bufB, N, RT4, lds_c, twM, twP, ev, s, sc, anchor);
+            mark(4);
+            k_irow<T><<<N / PR, 512, sm_irow, st>>>(bufB, phi[spare], psi[spare], N, PR, twM, twP,
+                                                    phi[cur], phi[prev], psi[cur], psi[prev], so.bdf1, sc, anchor,
+                                                    (uint32_t)steps_taken);
+            mark(5);
+        }
         nlaunch += 6;
         if (!bdf1 && (flags & CCMSAV_TRACK_ENERGY)) {
             k_dnorm<T><<<g_dg, 256, 0, st>>>(phi[cur], phi[prev], psi[spare], psi[cur], psi[prev], partd, N, p.M0);

@@ -1,50 +1,62 @@
 // step_kernels.cuh -- kernels of one CC-MSAV time step (templated on the
 // field precision T = float or double).
 //
-// One step n -> n+1 (Sec. 3.2 of the paper, solved as in Appendix B) runs as
-//   k_stencil     extrapolation phi* = e1 phi^n + e2 phi^{n-1} (same for psi),
-//                 the pointwise / 5-point terms of the explicit right-hand
-//                 sides and the unnormalised basis numerators
-//                   f0 = (t1 phi^n + t2 phi^{n-1})/dt - M_phi theta~ Lap phi*
+// One step n -> n+1 (Sec. 3.2 of the paper, solved as in Appendix B) is
+// computed in increment form: with the reference levels
+//   phi_bar = (4 phi^n - phi^{n-1})/3   (BDF1 start step: phi_bar = phi^n),
+//   X_bar   = (4 X^n - X^{n-1})/3 for each SAV X in V, U, W, Z (BDF1: X^n),
+// the unknowns are d_phi = phi^{n+1} - phi_bar, d_psi = psi^{n+1} - psi_bar
+// and the SAV increments.  The scheme's equations are unchanged: since
+// chi phi_bar = C1 phi_bar - C2 Lap phi_bar + C3 Lap^2 phi_bar and C1 contains
+// 3/(2 dt), the explicit right-hand sides of Appendix B Step 2 become
+//   chi d_phi = f0' - sum_j c_j X_j^{n+1} F_j,
+//     f0' = -beta' phi_bar - M_phi theta~ Lap phi* + C2 Lap phi_bar - C3 Lap^2 phi_bar,
+//   zeta d_psi = g0' + Z^{n+1} LP,   g0' = lam Lap(psi_bar - psi*),
+// and the SAV updates (eqs. V_BDF2 .. Z_BDF2) become X^{n+1} = X_bar +
+// (F, d_phi) (+ (P, d_psi) for Z): 3 phi^{n+1} - 4 phi^n + phi^{n-1} = 3 d_phi.
+// The 5x5 matrix of Step 4 is the same; only its right-hand side changes.
+// In exact arithmetic this is the paper's step; in finite precision it keeps
+// O(1) fields out of the transforms and the SAV algebra, so nothing of size
+// (1/dt) phi or (F, phi) has to cancel.
+//
+//   k_stencil     phi*, phi_bar, psi*, psi_bar and the unnormalised fields
+//                   f0', g0' (above),
 //                   S  = phi*(phi*^2 - 1 - beta)/eps
 //                   H  = 3 sqrt2/4 [(phi*^3 - phi*)/eps - eps Lap phi*]
 //                   Q  = 6[phi*|grad phi*|^2 - div(phi*^2 grad phi*)]
 //                        + (phi*^3 - phi*)(3 phi*^2 - 1)/eps^2
 //                   K  = p'(phi*)(f_in - f_out)/2
 //                   P  = [g_in(1+p)(psi*-psi_in) + g_out(1-p)(psi*-psi_out)]/2
-//                   g0 = (t1 psi^n + t2 psi^{n-1})/dt - lam Lap psi*
 //                   LP = div(M_psi(A phi*) grad P)           (eq. mobility_flux)
-//                 and per-block partial sums of the SAV radicands and of the
-//                 explicit inner products (F, w) with w = w1 phi^n + w2 phi^{n-1}
-//                 (Appendix B Step 1);
+//                 plus per-block partial sums of the SAV radicands, the minimum
+//                 face mobility and the sums of psi^n, psi^{n-1};
 //   k_rowdct_T    forward DCT-II along x of the 8 fields, written transposed;
 //   k_coldct_gram forward DCT-II along y (now contiguous), spectral Gram sums
 //                 (Parseval: (u, chi^{-1} v)_h = h^2 sum_k u^ v^ / sigma_k) and
-//                 the 7 spectra needed for recovery;
+//                 the spectra needed for recovery;
 //   k_solve       FP64 reduction of the partials, the 5x5 system (Appendix B
 //                 Step 4), the SAV update and the recovery coefficients;
 //   k_comb_icolT  recovery in spectral space
-//                   phi^ = (f0^ - aS S^ - aH H^ - aQ Q^ - aK K^) / sigma,
-//                   psi^ = (g0^ + aL LP^) / tau,
+//                   d_phi^ = (f0'^ - aS S^ - aH H^ - aQ Q^ - aK K^) / sigma,
+//                   d_psi^ = (g0'^ + aL LP^) / tau,
 //                 inverse DCT along y, written transposed;
-//   k_irow        inverse DCT along x -> phi^{n+1}, psi^{n+1}.
+//   k_irow        inverse DCT along x and phi^{n+1} = phi_bar + d_phi,
+//                 psi^{n+1} = psi_bar + d_psi.
 #pragma once
 #include "dct_device.cuh"
 
 namespace ccm {
 
-enum { NRED1 = 10 };   // k_stencil partials: IV IW IZ rS rH rQ rK rP minM (pad)
-enum { NRED2 = 17 };   // gram partials: 15 chi pairs (a <= b over f0 S H Q K), PG, PL
-enum { NF = 8 };       // fields out of k_stencil: f0 S H Q K P g0 LP
-enum { NSPEC = 7 };    // stored spectra: f0 S H Q K g0 LP
+enum { NRED1 = 10 };   // k_stencil partials: IV IW IZ sum(psi^n) sum(psi^{n-1}) (3 unused) minM (pad)
+enum { NRED2 = 17 };   // gram partials: 15 chi pairs (a <= b over f0' S H Q K), PG, PL
+enum { NF = 8 };       // fields out of k_stencil: f0' S H Q K P g0' LP
 
 struct StencilCoef {
-    double e1, e2;        // phi* = e1 phi^n + e2 phi^{n-1}
-    double t1, t2;        // time part of f0/g0: (t1 u^n + t2 u^{n-1}) / dt  (t1, t2 already / dt)
-    double w1, w2;        // weight of the explicit inner products
+    int bdf1;             // 1: start step (phi* = phi_bar = phi^n)
     double inv_h, inv_h2;
     double eps, inv_eps, inv_eps2, beta;
     double Mth;           // M_phi * theta~
+    double C2, C3, betap; // chi coefficients; betap = M_phi gamma_surf 3 sqrt2 beta / (4 eps)
     double lam;
     double gin, gout, psin, psout, bin, bout;
     double M0;
@@ -61,16 +73,21 @@ struct DevScalars {
     double A;                     // target arc length
     double lamsum;                // sum_{j>=2} dt/2 ||d^j||^2
     double steps;                 // steps taken
-    double mass_mode;             // conserved mean of psi (FP64), added back per point by the FP32 path
+    double mass_mode;             // conserved mean of psi (FP64) that the FP32 path keeps
     double alpha[5];              // recovery coefficients aS aH aQ aK aL
-    double last[8];               // IV IW IZ and diagnostics of the last step
+    double anchor;                // FP32 path: mean correction added to psi^{n+1}
+    double dc_col;                // FP32 path: sum over y of the inverse column pass of the
+                                  // zero-mean psi increment at kx = 0 (its DC leakage)
+    double last[6];               // IV IW IZ minM and diagnostics of the last step
     int status;                   // 0 or a CCMSAV_E* code set on the device
     int pad;
 };
 
 struct SolveCoef {
     double h2, cgs, cga, cgb, cgo;
+    double NN;                    // points per field
     int bdf1;
+    int anchor;                   // FP32 path: compute the psi mean correction
     int nb1, nb2;                 // number of partial rows
 };
 
@@ -112,10 +129,89 @@ __device__ void block_sum_store(T (&v)[NV], double* out, double* sm) {
     __syncthreads();
 }
 
+// Warp sum carried as an unevaluated pair hi + lo (error-free transformation
+// TwoSum of Knuth / Dekker double-length arithmetic), so that a warp of FP32
+// values sums to ~2^-44 relative accuracy without FP64 per element.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = a + b;
+    const float bb = s - a;
+    e = (a - (s - bb)) + (b - bb);
+}
+__device__ __forceinline__ double warp_sum_exact(float x) {
+    float hi = x, lo = 0.f;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, ohi, s, e);
+        e += lo + olo;
+        hi = s + e;                       // renormalise (Fast2Sum, |s| >= |e|)
+        lo = e - (hi - s);
+    }
+    return (double)hi + (double)lo;
+}
+__device__ __forceinline__ double warp_sum_exact(double x) { return warp_sum(x); }
+
+// Neumann ghost cells by even reflection about the boundary face:
+// index -1 -> 0, -2 -> 1, N -> N-1, N+1 -> N-2 (for halo 1 this is the
+// mirror phi_0 = phi_1 of Appendix D; for halo 2 it makes Lap phi at a ghost
+// cell equal the mirror of Lap phi, i.e. Lap^2 = Lap o Lap with mirrored ghosts).
+__device__ __forceinline__ int reflect(int i, int N) {
+    return i < 0 ? -1 - i : (i >= N ? 2 * N - 1 - i : i);
+}
+
+// Counter-based 32-bit hash (the "lowbias32" integer mixer: xor-shifts and
+// odd multipliers) of a point index and a step key.
+__device__ __forceinline__ uint32_t mix32(uint32_t x) {
+    x ^= x >> 16; x *= 0x7feb352du;
+    x ^= x >> 15; x *= 0x846ca68bu;
+    x ^= x >> 16;
+    return x;
+}
+__device__ __forceinline__ uint32_t dither_key(uint32_t step, uint32_t idx) {
+    return mix32(idx * 0x9e3779b9u ^ mix32(step + 0x632be5abu));
+}
+
+// Round s + r (|r| below about one ulp of s, r the exact residual) to a
+// neighbouring float with probability proportional to closeness: adds a
+// uniform dither of one ulp before rounding to nearest.  The stored FP32
+// value is then unbiased and its rounding error uncorrelated between points,
+// even where a whole region holds the same value, so a sub-ulp mean
+// correction shifts the stored mass as intended.
+__device__ __forceinline__ float dither_round(float s, float r, uint32_t key) {
+    const int ex = (__float_as_int(s) >> 23) & 0xff;
+    const float ulp = ex > 24 ? __int_as_float((ex - 23) << 23) : 1.17549435e-38f * 2.0f;
+    // u in (-1/2, 1/2), never +-1/2: a float input with r = 0 is returned unchanged
+    const float u = ((float)(key >> 8) + 0.5f) * (1.0f / 16777216.0f) - 0.5f;
+    return s + fmaf(u, ulp, r);
+}
+
+// u^{n+1} = u_bar + du (+ anchor) with u_bar = u^n + (u^n - u^{n-1})/3
+// (BDF1: u^n).  FP32: the two roundings are compensated (FMA residual and
+// TwoSum), so the stored value is the correctly rounded u_bar + du + anchor
+// and a sub-ulp anchor shifts the stored mean without bias.
+// dither: 0 = round to nearest, else the key of dither_round.
+__device__ __forceinline__ float bar_add(float a, float b, float du, float anc, bool bdf1, uint32_t dither = 0) {
+    float t1 = a, e1 = 0.f;
+    if (!bdf1) {
+        const float d = a - b;
+        t1 = fmaf(d, 1.0f / 3.0f, a);
+        e1 = fmaf(d, 1.0f / 3.0f, a - t1);
+    }
+    float s, e2;
+    two_sum(t1, du, s, e2);
+    const float r = (e1 + e2) + anc;
+    return dither ? dither_round(s, r, dither) : s + r;
+}
+__device__ __forceinline__ double bar_add(double a, double b, double du, double anc, bool bdf1, uint32_t = 0) {
+    return (bdf1 ? a : a + (a - b) / 3.0) + du + anc;
+}
+
 // ------------------------------------------------------------------ k_stencil
-// Tile of TX x TY cells per block (one thread per cell) with a one-cell
-// halo of phi*, psi* and of the P numerator in shared memory.  Neumann ghost
-// cells are the mirrored boundary cells (index clamping).
+// Tile of TX x TY cells per block (one thread per cell).  Shared-memory tiles:
+// phi_bar with a two-cell halo (for Lap^2 phi_bar), and phi*, psi*, the P
+// numerator, psi_bar - psi* and Lap phi_bar with a one-cell halo.
 constexpr int TX = 32, TY = 8;
 
 template <typename T>
@@ -123,37 +219,63 @@ __global__ void __launch_bounds__(TX * TY)
 k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
           const T* __restrict__ psn, const T* __restrict__ pso,
           T* __restrict__ out, double* __restrict__ part, int N, StencilCoef c) {
+    __shared__ T sbar[TY + 4][TX + 4];
     __shared__ T sph[TY + 2][TX + 2];
     __shared__ T sps[TY + 2][TX + 2];
     __shared__ T sP[TY + 2][TX + 2];
+    __shared__ T sdq[TY + 2][TX + 2];
+    __shared__ T slb[TY + 2][TX + 2];
     __shared__ double sred[(TX * TY / 32) * NRED1];
+    __shared__ double smean[2][TX * TY / 32];
     const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
     const int tid = threadIdx.y * TX + threadIdx.x;
-    const T e1 = (T)c.e1, e2 = (T)c.e2;
-    const T hgin = (T)(0.5 * c.gin), hgout = (T)(0.5 * c.gout);
-    for (int q = tid; q < (TX + 2) * (TY + 2); q += TX * TY) {
-        const int lj = q / (TX + 2), li = q % (TX + 2);
-        int gi = i0 + li - 1, gj = j0 + lj - 1;
-        gi = gi < 0 ? 0 : (gi >= N ? N - 1 : gi);
-        gj = gj < 0 ? 0 : (gj >= N ? N - 1 : gj);
+    // with d = u^n - u^{n-1} (exact for nearby values): u* = u^n + d,
+    // u_bar = u^n + d/3, u_bar - u* = -2d/3 (BDF1: u* = u_bar = u^n)
+    const T kst = c.bdf1 ? (T)0 : (T)1, kbar = c.bdf1 ? (T)0 : (T)(1.0 / 3.0), kq = c.bdf1 ? (T)0 : (T)(-2.0 / 3.0);
+    const T ih = (T)c.inv_h, ih2 = (T)c.inv_h2;
+    for (int q = tid; q < (TX + 4) * (TY + 4); q += TX * TY) {
+        const int lj = q / (TX + 4), li = q % (TX + 4);
+        const int gi = reflect(i0 + li - 2, N), gj = reflect(j0 + lj - 2, N);
         const size_t g = (size_t)gj * N + gi;
-        const T ph = e1 * phn[g] + e2 * pho[g];
-        const T ps = e1 * psn[g] + e2 * pso[g];
-        sph[lj][li] = ph;
-        sps[lj][li] = ps;
-        T sp, cp;
-        sincospi_<T>((T)0.5 * ph, &sp, &cp);
-        sP[lj][li] = (T)0.5 * ((T)c.gin * ((T)1 + sp) * (ps - (T)c.psin) + (T)c.gout * ((T)1 - sp) * (ps - (T)c.psout));
+        const T a = phn[g], da = a - pho[g];
+        sbar[lj][li] = a + kbar * da;
+        if (lj >= 1 && lj <= TY + 2 && li >= 1 && li <= TX + 2) {
+            const T ph = a + kst * da;
+            const T u = psn[g], du = u - pso[g];
+            const T ps = u + kst * du;
+            sph[lj - 1][li - 1] = ph;
+            sps[lj - 1][li - 1] = ps;
+            sdq[lj - 1][li - 1] = kq * du;
+            T sp, cp;
+            sincospi_<T>((T)0.5 * ph, &sp, &cp);
+            sP[lj - 1][li - 1] = (T)0.5 * ((T)c.gin * ((T)1 + sp) * (ps - (T)c.psin)
+                                           + (T)c.gout * ((T)1 - sp) * (ps - (T)c.psout));
+        }
+    }
+    __syncthreads();
+    // Lap phi_bar on the one-cell-halo region (sums of neighbour differences:
+    // each difference of nearby values is exact, so the rounding is relative
+    // to the Laplacian, not to the field)
+    for (int q = tid; q < (TX + 2) * (TY + 2); q += TX * TY) {
+        const int lj = q / (TX + 2) + 1, li = q % (TX + 2) + 1;
+        const T C = sbar[lj][li];
+        slb[lj - 1][li - 1] = (((sbar[lj][li + 1] - C) + (sbar[lj][li - 1] - C))
+                               + ((sbar[lj + 1][li] - C) + (sbar[lj - 1][li] - C))) * ih2;
     }
     __syncthreads();
     const int li = threadIdx.x + 1, lj = threadIdx.y + 1;
     const int gi = i0 + threadIdx.x, gj = j0 + threadIdx.y;
-    const size_t g = (size_t)gj * N + gi;
-    const T ih = (T)c.inv_h, ih2 = (T)c.inv_h2;
+    const bool inside = gi < N && gj < N;     // tiles overhang grids smaller than TX x TY
+    const size_t g = inside ? (size_t)gj * N + gi : 0;
     const T pC = sph[lj][li], pE = sph[lj][li + 1], pW = sph[lj][li - 1], pN = sph[lj + 1][li], pS = sph[lj - 1][li];
-    const T qC = sps[lj][li], qE = sps[lj][li + 1], qW = sps[lj][li - 1], qN = sps[lj + 1][li], qS = sps[lj - 1][li];
-    const T lapp = (pE + pW + pN + pS - (T)4 * pC) * ih2;
-    const T lapq = (qE + qW + qN + qS - (T)4 * qC) * ih2;
+    const T qC = sps[lj][li];
+    const T lapp = (((pE - pC) + (pW - pC)) + ((pN - pC) + (pS - pC))) * ih2;
+    const T dC = sdq[lj][li];
+    const T lapd = (((sdq[lj][li + 1] - dC) + (sdq[lj][li - 1] - dC))
+                    + ((sdq[lj + 1][li] - dC) + (sdq[lj - 1][li] - dC))) * ih2;
+    const T lbC = slb[lj][li];
+    const T lap2b = (((slb[lj][li + 1] - lbC) + (slb[lj][li - 1] - lbC))
+                     + ((slb[lj + 1][li] - lbC) + (slb[lj - 1][li] - lbC))) * ih2;
     const T p2 = pC * pC, p3m = pC * (p2 - (T)1);
     const T eps = (T)c.eps, ieps = (T)c.inv_eps, ieps2 = (T)c.inv_eps2;
     // face gradients (zero on boundary faces through the mirrored ghosts)
@@ -167,6 +289,7 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
     T sp, cp;
     sincospi_<T>((T)0.5 * pC, &sp, &cp);
     const T dp = (T)1.5707963267948966192 * cp;
+    const T hgin = (T)(0.5 * c.gin), hgout = (T)(0.5 * c.gout);
     const T fin = hgin * (qC - (T)c.psin) * (qC - (T)c.psin) + (T)c.bin;
     const T fout = hgout * (qC - (T)c.psout) * (qC - (T)c.psout) + (T)c.bout;
     const T Knum = (T)0.5 * dp * (fin - fout);
@@ -178,11 +301,9 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
     const T mN = mob((T)0.5 * (pC + pN)), mS = mob((T)0.5 * (pC + pS));
     const T LP = (mE * (sP[lj][li + 1] - PC) - mW * (PC - sP[lj][li - 1])
                   + mN * (sP[lj + 1][li] - PC) - mS * (PC - sP[lj - 1][li])) * ih2;
-    const bool inside = gi < N && gj < N;     // tiles overhang grids smaller than TX x TY
-    const size_t gc = inside ? g : 0;
-    const T phn_c = phn[gc], pho_c = pho[gc], psn_c = psn[gc], pso_c = pso[gc];
-    const T f0 = (T)c.t1 * phn_c + (T)c.t2 * pho_c - (T)c.Mth * lapp;
-    const T g0 = (T)c.t1 * psn_c + (T)c.t2 * pso_c - (T)c.lam * lapq;
+    const T bC = sbar[lj + 1][li + 1];
+    const T f0 = (T)c.C2 * slb[lj][li] - (T)c.C3 * lap2b - (T)c.Mth * lapp - (T)c.betap * bC;
+    const T g0 = (T)c.lam * lapd;
     const size_t NN = (size_t)N * N;
     if (inside) {
         out[0 * NN + g] = f0;
@@ -195,23 +316,14 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
         out[7 * NN + g] = LP;
     }
     // partial sums
-    const T wphi = (T)c.w1 * phn_c + (T)c.w2 * pho_c;
-    const T wpsi = (T)c.w1 * psn_c + (T)c.w2 * pso_c;
     const T vv = p2 - (T)1 - (T)c.beta;
     T red[NRED1];
-    red[0] = vv * vv * (T)(0.25 * c.inv_eps);
-    red[1] = (T)6 * p2 * gbar + p3m * p3m * ieps2;
-    red[2] = ((T)1 + sp) * fin + ((T)1 - sp) * fout;
-    red[3] = Snum * wphi;
-    red[4] = Hv * wphi;
-    red[5] = Qnum * wphi;
-    red[6] = Knum * wphi;
-    red[7] = PC * wpsi;
-    red[8] = 0;
-    red[9] = 0;
-    if (!inside) {
 #pragma unroll
-        for (int i = 0; i < NRED1; ++i) red[i] = 0;
+    for (int i = 0; i < NRED1; ++i) red[i] = 0;
+    if (inside) {
+        red[0] = vv * vv * (T)(0.25 * c.inv_eps);
+        red[1] = (T)6 * p2 * gbar + p3m * p3m * ieps2;
+        red[2] = ((T)1 + sp) * fin + ((T)1 - sp) * fout;
     }
     // minimum face mobility over interior faces (boundary faces carry no flux)
     T mm = (T)1e30;
@@ -223,13 +335,20 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
     }
     double* prow = part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * NRED1;
     block_sum_store<NRED1, T>(red, prow, sred);
+    // sums of psi^n and psi^{n-1} to ~1e-13 (mass bookkeeping of the FP32 path)
+    const T un = inside ? psn[g] : (T)0, uo = inside ? pso[g] : (T)0;
+    const double sn = warp_sum_exact(un), so = warp_sum_exact(uo);
+    if ((tid & 31) == 0) { smean[0][tid >> 5] = sn; smean[1][tid >> 5] = so; }
     mm = warp_min(mm);
     __shared__ T smin[TX * TY / 32];
     if ((tid & 31) == 0) smin[tid >> 5] = mm;
     __syncthreads();
     if (tid == 0) {
         T m = smin[0];
-        for (int w = 1; w < TX * TY / 32; ++w) m = min(m, smin[w]);
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < TX * TY / 32; ++w) { m = min(m, smin[w]); a += smean[0][w]; b += smean[1][w]; }
+        prow[3] = a;
+        prow[4] = b;
         prow[8] = (double)m;
     }
 }
@@ -436,31 +555,26 @@ k_solve(const double* __restrict__ p1, const double* __restrict__ p2, DevScalars
     if (t != 0) return;
     if (sc->status != 0) return;
     const double* r = fin_;
-    const double IV = r[0], IW = r[1], IZ = r[2];
-    const double rS = r[3], rH = r[4], rQ = r[5], rK = r[6], rP = r[7], minM = r[8];
+    const double IV = r[0], IW = r[1], IZ = r[2], sum_n = r[3], sum_o = r[4], minM = r[8];
     const double* Gm = r + NRED1;
     bool ok = true;
-    for (int i = 0; i < NRED1 + NRED2; ++i) ok = ok && finite_(r[i]);
+    for (int i = 0; i < NR; ++i) ok = ok && finite_(r[i]);
     ok = ok && IV > 0 && IW > 0 && IZ > 0 && minM > 0;
     if (!ok) { sc->status = -5; return; }
     const double h2 = co.h2;
     const double nS = 0.5 / sqrt(h2 * IV), nQ = 1.0 / sqrt(h2 * IW), nK = 1.0 / sqrt(h2 * IZ);
     const double nrm[4] = {nS, 1.0, nQ, nK};
-    double aV, aU, aW, aZ;
-    if (co.bdf1) {
-        aV = sc->V + h2 * nS * rS;
-        aU = sc->U + h2 * rH;
-        aW = sc->W + h2 * nQ * rQ;
-        aZ = sc->Z + h2 * nK * (rK + rP);
-    } else {
-        aV = (4.0 * sc->V - sc->Vo + h2 * nS * rS) / 3.0;
-        aU = (4.0 * sc->U - sc->Uo + h2 * rH) / 3.0;
-        aW = (4.0 * sc->W - sc->Wo + h2 * nQ * rQ) / 3.0;
-        aZ = (4.0 * sc->Z - sc->Zo + h2 * nK * (rK + rP)) / 3.0;
+    // reference SAVs X_bar (Step 1 with the increments taken about phi_bar)
+    double xb[4];
+    if (co.bdf1) { xb[0] = sc->V; xb[1] = sc->U; xb[2] = sc->W; xb[3] = sc->Z; }
+    else {
+        xb[0] = (4.0 * sc->V - sc->Vo) / 3.0;
+        xb[1] = (4.0 * sc->U - sc->Uo) / 3.0;
+        xb[2] = (4.0 * sc->W - sc->Wo) / 3.0;
+        xb[3] = (4.0 * sc->Z - sc->Zo) / 3.0;
     }
-    const double av[4] = {aV, aU, aW, aZ};
     const double cc[4] = {co.cgs, co.cga, co.cgb, co.cgo};
-    // Gram index for a <= b over (f0, S, H, Q, K)
+    // Gram index for a <= b over (f0', S, H, Q, K)
     auto G = [&](int a, int b) {
         if (a > b) { int x = a; a = b; b = x; }
         int idx = 0;
@@ -473,7 +587,7 @@ k_solve(const double* __restrict__ p1, const double* __restrict__ p2, DevScalars
         for (int j = 0; j < 4; ++j) {
             const double gij = h2 * nrm[i] * nrm[j] * G(i + 1, j + 1);
             A[i][j] = (i == j ? 1.0 : 0.0) + cc[j] * gij;
-            bi -= cc[j] * av[j] * nrm[j] * G(i + 1, j + 1);
+            bi -= cc[j] * xb[j] * nrm[j] * G(i + 1, j + 1);
         }
         A[i][4] = co.cgo * h2 * nrm[i] * nK * G(i + 1, 4);
         A[i][5] = h2 * nrm[i] * bi;
@@ -482,7 +596,7 @@ k_solve(const double* __restrict__ p1, const double* __restrict__ p2, DevScalars
     A[4][0] = A[4][1] = A[4][2] = 0.0;
     A[4][3] = -PL;
     A[4][4] = 1.0 - PL;
-    A[4][5] = h2 * nK * Gm[15] + aZ * PL;
+    A[4][5] = h2 * nK * Gm[15] + xb[3] * PL;
     // Gaussian elimination with partial pivoting
     for (int k = 0; k < 5; ++k) {
         int piv = k;
@@ -501,7 +615,7 @@ k_solve(const double* __restrict__ p1, const double* __restrict__ p2, DevScalars
         for (int j = i + 1; j < 5; ++j) s -= A[i][j] * x[j];
         x[i] = s / A[i][i];
     }
-    const double Vn = aV + x[0], Un = aU + x[1], Wn = aW + x[2], Zn = aZ + x[3] + x[4];
+    const double Vn = xb[0] + x[0], Un = xb[1] + x[1], Wn = xb[2] + x[2], Zn = xb[3] + x[3] + x[4];
     bool ok2 = finite_(Vn) && finite_(Un) && finite_(Wn) && finite_(Zn);
     if (!ok2) { sc->status = -5; return; }
     sc->Vo = sc->V; sc->Uo = sc->U; sc->Wo = sc->W; sc->Zo = sc->Z;
@@ -511,6 +625,15 @@ k_solve(const double* __restrict__ p1, const double* __restrict__ p2, DevScalars
     sc->alpha[2] = co.cgb * Wn * nQ;
     sc->alpha[3] = co.cgo * Zn * nK;
     sc->alpha[4] = Zn * nK;
+    // FP32 path: psi^{n+1} = psi_bar + d_psi + anchor keeps the stored mean at
+    // the conserved value (means of the stored levels summed to ~1e-13)
+    if (co.anchor) {
+        const double mn = sum_n / co.NN, mo = sum_o / co.NN;
+        const double mbar = co.bdf1 ? mn : mn + (mn - mo) / 3.0;
+        sc->anchor = sc->mass_mode - mbar;
+    } else {
+        sc->anchor = 0.0;
+    }
     sc->last[0] = IV; sc->last[1] = IW; sc->last[2] = IZ; sc->last[3] = minM;
     sc->steps += 1.0;
 }
@@ -556,8 +679,8 @@ k_comb_icolT(const T* __restrict__ spec, T* __restrict__ out, int N, int RT, int
                 } else {
                     const T itau = (T)(1.0 / (sc.Ct + sc.lam * s));
                     vals[u] = (spec[6 * NN + o] + aL * spec[7 * NN + o]) * itau;
-                    // FP32 path: the mean of psi (the zero mode) is not carried through the
-                    // FP32 transforms; k_irow adds the conserved FP64 mean back per point.
+                    // d_psi has zero mean (mass conservation); the FP32 path sets the zero
+                    // mode exactly and keeps the stored mean with the anchor in k_irow
                     if (anchor_mass && kx == 0 && ky == 0) vals[u] = (T)0;
                 }
             }
@@ -593,7 +716,8 @@ template <typename T>
 __global__ void __launch_bounds__(512)
 k_irow(const T* __restrict__ in, T* __restrict__ phi_new, T* __restrict__ psi_new, int N, int PR,
        const cplx<T>* __restrict__ twM, const PostTw<T>* __restrict__ twP,
-       const DevScalars* __restrict__ dsc, int anchor_mass) {
+       const T* __restrict__ phn, const T* __restrict__ pho, const T* __restrict__ psn, const T* __restrict__ pso,
+       int bdf1, const DevScalars* __restrict__ dsc, int anchor_mass, uint32_t step) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int M = N / 2, ldc = padded_len(M);
     const int E = M < 8 ? M : 8, G = M / E, P = blockDim.x / G;
@@ -602,7 +726,7 @@ k_irow(const T* __restrict__ in, T* __restrict__ phi_new, T* __restrict__ psi_ne
     const int y0 = blockIdx.x * PR;
     const T inv0 = (T)(1.0 / (M * sqrt(1.0 / N))), inv = (T)(1.0 / (M * sqrt(2.0 / N)));
     const int nlines = 2 * PR;
-    const double mean = anchor_mass ? dsc->mass_mode : 0.0;
+    const T anc = anchor_mass ? (T)dsc->anchor : (T)0;
     for (int l0 = 0; l0 < nlines; l0 += P) {
         const int nl = min(P, nlines - l0);
         for (int q = threadIdx.x; q < nl * (M / 2 + 1); q += blockDim.x) {
@@ -621,13 +745,17 @@ k_irow(const T* __restrict__ in, T* __restrict__ phi_new, T* __restrict__ psi_ne
         for (int q = threadIdx.x; q < nl * (M / 2); q += blockDim.x) {
             const int l = l0 + q / (M / 2), m = q % (M / 2);
             const int r = l >> 1, f = l & 1;
-            T* dst = (f == 0 ? phi_new : psi_new) + (size_t)(y0 + r) * N + 4 * m;
+            const size_t off = (size_t)(y0 + r) * N + 4 * m;
             vec4<T> v = unpack4(fb + (size_t)(l - l0) * ldc, M, m);
-            if (f == 1 && anchor_mass) {
-                v.a = (T)((double)v.a + mean); v.b = (T)((double)v.b + mean);
-                v.c = (T)((double)v.c + mean); v.d = (T)((double)v.d + mean);
-            }
-            st4(dst, v);
+            const vec4<T> a = ld4((f == 0 ? phn : psn) + off), b = ld4((f == 0 ? pho : pso) + off);
+            const T an = (f == 1) ? anc : (T)0;
+            const bool dth = (f == 1) && anchor_mass;
+            const uint32_t i0 = (uint32_t)off;
+            v.a = bar_add(a.a, b.a, v.a, an, bdf1 != 0, dth ? dither_key(step, i0) | 1u : 0u);
+            v.b = bar_add(a.b, b.b, v.b, an, bdf1 != 0, dth ? dither_key(step, i0 + 1) | 1u : 0u);
+            v.c = bar_add(a.c, b.c, v.c, an, bdf1 != 0, dth ? dither_key(step, i0 + 2) | 1u : 0u);
+            v.d = bar_add(a.d, b.d, v.d, an, bdf1 != 0, dth ? dither_key(step, i0 + 3) | 1u : 0u);
+            st4((f == 0 ? phi_new : psi_new) + off, v);
         }
         __syncthreads();
     }

@@ -1,0 +1,184 @@
+// warp_fft.cuh -- warp-level four-step FFT of whole grid lines (FP32 path).
+//
+// A line of M = E * G complex values is held by a group of G lanes, E values
+// per lane (lane n2 holds z[G n1 + n2], n1 = 0..E-1):
+//   1. E-point DFT over n1 in registers (radix-2 decimation in frequency,
+//      exact compile-time twiddles; output in bit-reversed register order);
+//   2. twiddle by W_M^{n2 k1} (table tw2[k1][n2], coalesced across lanes);
+//   3. transpose through the line's shared-memory buffer (rows padded to
+//      G + 1 complex values, conflict-free);
+//   4. E/G G-point DFTs over n2 in registers; the result Z[k1 + E k2] is
+//      written to the buffer in natural order.
+// One smem round trip per stage pair instead of one per radix-8 stage, no
+// block barriers (only __syncwarp), and 32 independent values per lane.
+// Supported lines: M in {64, 128, 256, 512, 1024} (N = 2M in 128 .. 2048);
+// G = 2^floor(log2(M)/2) <= E = M / G <= 32.
+#pragma once
+#include "dct_device.cuh"
+
+namespace ccm {
+namespace wf {
+
+__device__ __forceinline__ void w32(int j, double& c, double& s) {
+    switch (j & 31) {
+        case 0: c = 1.0; s = 0.0; break;
+        case 1: c = 0.9807852804032304; s = 0.19509032201612825; break;
+        case 2: c = 0.9238795325112867; s = 0.3826834323650898; break;
+        case 3: c = 0.8314696123025452; s = 0.5555702330196022; break;
+        case 4: c = 0.7071067811865476; s = 0.7071067811865475; break;
+        case 5: c = 0.5555702330196023; s = 0.8314696123025452; break;
+        case 6: c = 0.38268343236508984; s = 0.9238795325112867; break;
+        case 7: c = 0.19509032201612833; s = 0.9807852804032304; break;
+        case 8: c = 0.0; s = 1.0; break;
+        case 9: c = -0.1950903220161282; s = 0.9807852804032304; break;
+        case 10: c = -0.3826834323650897; s = 0.9238795325112867; break;
+        case 11: c = -0.555570233019602; s = 0.8314696123025455; break;
+        case 12: c = -0.7071067811865475; s = 0.7071067811865476; break;
+        case 13: c = -0.8314696123025453; s = 0.5555702330196022; break;
+        case 14: c = -0.9238795325112867; s = 0.3826834323650899; break;
+        case 15: c = -0.9807852804032304; s = 0.1950903220161286; break;
+        case 16: c = -1.0; s = 0.0; break;
+        case 17: c = -0.9807852804032304; s = -0.19509032201612836; break;
+        case 18: c = -0.9238795325112868; s = -0.38268343236508967; break;
+        case 19: c = -0.8314696123025455; s = -0.555570233019602; break;
+        case 20: c = -0.7071067811865477; s = -0.7071067811865475; break;
+        case 21: c = -0.5555702330196022; s = -0.8314696123025452; break;
+        case 22: c = -0.38268343236509034; s = -0.9238795325112865; break;
+        case 23: c = -0.19509032201612866; s = -0.9807852804032303; break;
+        case 24: c = 0.0; s = -1.0; break;
+        case 25: c = 0.1950903220161283; s = -0.9807852804032304; break;
+        case 26: c = 0.38268343236509; s = -0.9238795325112866; break;
+        case 27: c = 0.5555702330196018; s = -0.8314696123025455; break;
+        case 28: c = 0.7071067811865474; s = -0.7071067811865477; break;
+        case 29: c = 0.8314696123025452; s = -0.5555702330196022; break;
+        case 30: c = 0.9238795325112865; s = -0.3826834323650904; break;
+        case 31: c = 0.9807852804032303; s = -0.19509032201612872; break;
+        default: c = 1.0; s = 0.0; break;
+    }
+}
+
+// x * W_R^i (forward: exp(-2 pi i I / R); INV: conjugate)
+template <typename T, int R, bool INV>
+__device__ __forceinline__ cplx<T> twid(cplx<T> x, int i) {
+    const int j = (i * (32 / R)) & 31;
+    if (j == 0) return x;
+    if (j == 8) return INV ? mk(-x.y, x.x) : mk(x.y, -x.x);
+    if (j == 16) return mk(-x.x, -x.y);
+    if (j == 24) return INV ? mk(x.y, -x.x) : mk(-x.y, x.x);
+    double c, s;
+    w32(j, c, s);
+    const T cc = (T)c, ss = INV ? (T)s : (T)(-s);     // W = c + i ss
+    return mk(x.x * cc - x.y * ss, x.x * ss + x.y * cc);
+}
+
+// In-register radix-2 DIF on v[OFF .. OFF + R): natural input, output
+// v[OFF + r] = X[bitrev_R(r)].
+template <typename T, int R, bool INV, int OFF>
+struct DIF {
+    static __device__ __forceinline__ void run(cplx<T>* v) {
+#pragma unroll
+        for (int i = 0; i < R / 2; ++i) {
+            const cplx<T> a = v[OFF + i], b = v[OFF + i + R / 2];
+            v[OFF + i] = a + b;
+            v[OFF + i + R / 2] = twid<T, R, INV>(a - b, i);
+        }
+        DIF<T, R / 2, INV, OFF>::run(v);
+        DIF<T, R / 2, INV, OFF + R / 2>::run(v);
+    }
+};
+template <typename T, bool INV, int OFF>
+struct DIF<T, 1, INV, OFF> {
+    static __device__ __forceinline__ void run(cplx<T>*) {}
+};
+
+template <int R> __host__ __device__ constexpr int bitrev(int r) {
+    int o = 0;
+    for (int b = 1, q = R >> 1; b < R; b <<= 1, q >>= 1)
+        if (r & b) o |= q;
+    return o;
+}
+
+template <int M> struct Shape;
+template <> struct Shape<64>   { static constexpr int E = 8,  G = 8;  };
+template <> struct Shape<128>  { static constexpr int E = 16, G = 8;  };
+template <> struct Shape<256>  { static constexpr int E = 16, G = 16; };
+template <> struct Shape<512>  { static constexpr int E = 32, G = 16; };
+template <> struct Shape<1024> { static constexpr int E = 32, G = 32; };
+
+// Per-line buffer length (complex values) for the transpose and the
+// natural-order result.
+template <int M> __host__ __device__ constexpr int buf_len() {
+    return Shape<M>::E * (Shape<M>::G + 1);
+}
+
+// Steps 1-4.  v: this lane's E values in four-step order.  buf: this line's
+// buffer.  On return buf[k] = Z[k], k = 0..M-1 (visible to the warp).
+template <typename T, int M, bool INV>
+__device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>* __restrict__ tw2, int n2) {
+    constexpr int E = Shape<M>::E, G = Shape<M>::G, J = E / G;
+    DIF<T, E, INV, 0>::run(v);
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int k1 = bitrev<E>(r);
+        const cplx<T> w = tw2[k1 * G + n2];
+        buf[k1 * (G + 1) + n2] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+        for (int m = 0; m < G; ++m) v[j * G + m] = buf[(n2 * J + j) * (G + 1) + m];
+    __syncwarp();
+#pragma unroll
+    for (int j = 0; j < J; ++j) {
+        if (j == 0) DIF<T, G, INV, 0>::run(v);
+        else DIF<T, G, INV, G>::run(v);
+    }
+#pragma unroll
+    for (int j = 0; j < J; ++j)
+#pragma unroll
+        for (int r = 0; r < G; ++r) buf[(n2 * J + j) + E * bitrev<G>(r)] = v[j * G + r];
+    __syncwarp();
+}
+
+// Forward pack from a real line x in global memory (16-byte aligned):
+// z[m] = (x[4m], x[4m+2]), z[M-1-m] = (x[4m+3], x[4m+1]); lane n2 needs
+// z[G n1 + n2]; the mirrored half comes from lane n2 ^ (G-1).
+template <int M>
+__device__ __forceinline__ void pack_fwd_global(const float* __restrict__ x, cplx<float>* v, int n2) {
+    constexpr int E = Shape<M>::E, G = Shape<M>::G;
+#pragma unroll
+    for (int n1 = 0; n1 < E / 2; ++n1) {
+        const float4 q = __ldg(reinterpret_cast<const float4*>(x) + (G * n1 + n2));
+        v[n1] = mk(q.x, q.z);
+        const float ox = __shfl_xor_sync(0xffffffffu, q.w, G - 1);
+        const float oy = __shfl_xor_sync(0xffffffffu, q.y, G - 1);
+        v[E - 1 - n1] = mk(ox, oy);
+    }
+}
+
+// Forward post-process of the pair (k, M-k) from natural-order Z values.
+template <typename T>
+__device__ __forceinline__ Quad<T> post_pair(cplx<T> A, cplx<T> B, int k, PostTw<T> tw, T cn0, T cn) {
+    const T h = (T)0.70710678118654752440;
+    cplx<T> WN = mk(tw.cN, -tw.sN), W4 = mk(tw.c4, -tw.s4);
+    cplx<T> E = scale(A + conj_(B), (T)0.5);
+    cplx<T> D = scale(A - conj_(B), (T)0.5);
+    cplx<T> O = mk(D.y, -D.x);
+    cplx<T> W = cmul(W4, E + cmul(WN, O));
+    cplx<T> Dc = conj_(D);
+    cplx<T> O2 = mk(-Dc.y, Dc.x);
+    cplx<T> WN2 = mk(-WN.x, WN.y);
+    cplx<T> W4c = conj_(W4);
+    cplx<T> W42 = mk(h * (W4c.x + W4c.y), h * (W4c.y - W4c.x));
+    cplx<T> W2 = cmul(W42, conj_(E) + cmul(WN2, O2));
+    Quad<T> q;
+    q.xk = (k == 0 ? cn0 : cn) * W.x;
+    q.xNk = -cn * W.y;
+    q.xMk = cn * W2.x;
+    q.xMpk = -cn * W2.y;
+    return q;
+}
+
+}  // namespace wf
+}  // namespace ccm
