@@ -75,6 +75,10 @@ public:
     int PR = 1; size_t sm_irow = 0;
     dim3 g_dg;
     int nbd = 0;
+    // CUDA graphs of three BDF2 steps, one per phase of the three-level rotation
+    cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
+    bool own_stream = false;
+    bool graphs_failed = false;
     // tracing: event marks between the kernels of traced steps
     bool prof = false;
     std::vector<cudaEvent_t> ev_pool;
@@ -86,7 +90,27 @@ public:
     ~SimImpl() override {
         if (st) cudaStreamSynchronize(st); else cudaDeviceSynchronize();
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        for (int i = 0; i < 3; ++i) if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
         release();
+        if (own_stream && st) cudaStreamDestroy(st);
+    }
+
+    // Captures three consecutive BDF2 steps starting at the current rotation
+    // phase (nothing executes during capture; host counters are restored).
+    int capture_phase() {
+        const int ph = cur;
+        const long long s0 = steps_taken, l0 = nlaunch;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CCMSAV_ECUDA;
+        int r = CCMSAV_OK;
+        for (int i = 0; i < 3 && r == CCMSAV_OK; ++i) r = queue_one_step();
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        steps_taken = s0; nlaunch = l0;
+        if (r != CCMSAV_OK || e != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); return CCMSAV_ECUDA; }
+        const cudaError_t e2 = cudaGraphInstantiate(&gexec[ph], g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) { gexec[ph] = nullptr; return CCMSAV_ECUDA; }
+        return CCMSAV_OK;
     }
 
     int mark(int kind) {
@@ -156,6 +180,12 @@ public:
 
     int init(const ccmsav_params& pp, int N_, int flags_, cudaStream_t s) {
         p = pp; N = N_; flags = flags_; st = s;
+        if (!st) {
+            // NULL: a stream owned by the handle; it is a blocking stream, so it
+            // stays ordered with work on the legacy default stream
+            if (cudaStreamCreate(&st) != cudaSuccess) return CCMSAV_ECUDA;
+            own_stream = true;
+        }
         M = N / 2; NN = (size_t)N * N;
         const size_t fb = NN * sizeof(T);
         for (int i = 0; i < 3; ++i) {
@@ -165,7 +195,7 @@ public:
         if (cudaMalloc(&bufA, 8 * fb) != cudaSuccess) return CCMSAV_ENOMEM;
         if (cudaMalloc(&bufB, 8 * fb) != cudaSuccess) return CCMSAV_ENOMEM;
         b_st = dim3(TX, TY);
-        g_st = dim3((N + TX - 1) / TX, (N + TY - 1) / TY);
+        g_st = dim3((N + TX - 1) / TX, (N + TYB - 1) / TYB);
         nb1 = g_st.x * g_st.y;
         g_dg = dim3((N + 31) / 32, (N + 7) / 8);
         nbd = g_dg.x * g_dg.y;
@@ -220,6 +250,7 @@ public:
         // opt in to the largest dynamic shared memory each kernel can take (the
         // per-block opt-in limit minus the kernel's static shared memory); the
         // attribute is per kernel, so it must not depend on this simulation's N
+        if (set_smem_limit((const void*)k_stencil<T>, stencil_smem_bytes<T>())) return CCMSAV_ECUDA;
         if (set_smem_limit((const void*)k_rowdct_T<T>, sm_rt) || set_smem_limit((const void*)k_coldct_gram<T>, sm_col) ||
             set_smem_limit((const void*)k_comb_icolT<T>, sm_comb) || set_smem_limit((const void*)k_irow<T>, sm_irow))
             return CCMSAV_ECUDA;
@@ -245,16 +276,10 @@ public:
         if (cudaMalloc(&tw2, MM * sizeof(cplx<float>)) != cudaSuccess) return CCMSAV_ENOMEM;
         CCM_CUDA(cudaMemcpyAsync(tw2, h2.data(), MM * sizeof(cplx<float>), cudaMemcpyHostToDevice, st));
         const size_t bb = Gm::buf_bytes();
-        wRT = (N >= 2048) ? 8 : 16;
-        wlds = N + 32 / wRT;
-        wsm_rt = bb + (size_t)wRT * wlds * sizeof(float);
-        wKC = Gm::SLOTS / NF;
-        wsm_col = bb;
-        wRT4 = 4;
-        wlds4 = N + 8;
-        wsm_comb = bb + (size_t)2 * wRT4 * wlds4 * sizeof(float);
-        wRI = Gm::SLOTS / 2;
-        wsm_irow = bb;
+        wRT = Gm::SLOTS; wsm_rt = bb;
+        wKC = Gm::SLOTS / NF; wsm_col = bb;
+        wRT4 = Gm::SLOTS / 2; wsm_comb = bb;
+        wRI = Gm::SLOTS / 2; wsm_irow = bb;
         if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col) ||
             set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
             return CCMSAV_ECUDA;
@@ -288,7 +313,7 @@ public:
         float* fB = reinterpret_cast<float*>(bufB);
         const cplx<float>* t2 = tw2;
         const PostTw<float>* tp = reinterpret_cast<const PostTw<float>*>(twP);
-        kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, wRT, wlds, t2, tp);
+        kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, t2, tp);
         mark(1);
         kw_coldct_gram<MM><<<N / wKC, kWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2, t2, tp, evf, sf);
         mark(2);
@@ -299,13 +324,13 @@ public:
         SpecCoefF sf{(float)s.C1, (float)s.C2, (float)s.C3, (float)s.Ct, (float)s.lam};
         const PostTw<float>* tp = reinterpret_cast<const PostTw<float>*>(twP);
         kw_comb_icolT<MM><<<N / wRT4, kWarps * 32, wsm_comb, st>>>(reinterpret_cast<const float*>(bufA),
-            reinterpret_cast<float*>(bufB), wRT4, wlds4, tw2, tp, evf, sf, sc, anchor);
+            reinterpret_cast<float*>(bufB), tw2, tp, evf, sf, sc, anchor);
         mark(4);
         kw_irow<MM><<<N / wRI, kWarps * 32, wsm_irow, st>>>(reinterpret_cast<const float*>(bufB),
-            reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), wRI, tw2, tp,
+            reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), tw2, tp,
             reinterpret_cast<const float*>(phi[cur]), reinterpret_cast<const float*>(phi[prev]),
             reinterpret_cast<const float*>(psi[cur]), reinterpret_cast<const float*>(psi[prev]),
-            bdf1_launch, sc, anchor, (uint32_t)steps_taken);
+            bdf1_launch, sc, anchor);
         mark(5);
     }
     void warp_forward(const SpecCoef& s, int anchor) {
@@ -431,16 +456,18 @@ public:
     int queue_one_step() {
         const bool bdf1 = (steps_taken == 0);
         const double dt = p.dt;
-        StencilCoef c;
+        StencilCoef<T> c;
         c.bdf1 = bdf1 ? 1 : 0;
-        c.inv_h = 1.0 / h(); c.inv_h2 = 1.0 / (h() * h());
-        c.eps = p.eps; c.inv_eps = 1.0 / p.eps; c.inv_eps2 = 1.0 / (p.eps * p.eps); c.beta = p.beta;
-        c.Mth = p.M_phi * theta_tilde(); c.lam = p.lam;
-        c.C2 = p.M_phi * (p.gamma_surf * 3.0 * M_SQRT2 * p.eps / 4.0 + p.theta);
-        c.C3 = p.M_phi * p.gamma_bend * 3.0 * M_SQRT2 * p.eps / 8.0;
-        c.betap = p.M_phi * p.gamma_surf * 3.0 * M_SQRT2 * p.beta / (4.0 * p.eps);
-        c.gin = p.gamma_in; c.gout = p.gamma_out; c.psin = p.psi_in; c.psout = p.psi_out;
-        c.bin = p.beta_in; c.bout = p.beta_out; c.M0 = p.M0;
+        c.inv_h = (T)(1.0 / h()); c.inv_h2 = (T)(1.0 / (h() * h()));
+        c.eps = (T)p.eps; c.inv_eps = (T)(1.0 / p.eps); c.inv_eps2 = (T)(1.0 / (p.eps * p.eps));
+        c.beta = (T)p.beta; c.quarter_inv_eps = (T)(0.25 / p.eps);
+        c.Mth = (T)(p.M_phi * theta_tilde()); c.lam = (T)p.lam;
+        c.C2 = (T)(p.M_phi * (p.gamma_surf * 3.0 * M_SQRT2 * p.eps / 4.0 + p.theta));
+        c.C3 = (T)(p.M_phi * p.gamma_bend * 3.0 * M_SQRT2 * p.eps / 8.0);
+        c.betap = (T)(p.M_phi * p.gamma_surf * 3.0 * M_SQRT2 * p.beta / (4.0 * p.eps));
+        c.gin = (T)p.gamma_in; c.gout = (T)p.gamma_out; c.hgin = (T)(0.5 * p.gamma_in); c.hgout = (T)(0.5 * p.gamma_out);
+        c.psin = (T)p.psi_in; c.psout = (T)p.psi_out;
+        c.bin = (T)p.beta_in; c.bout = (T)p.beta_out; c.M0 = (T)p.M0;
         SpecCoef s;
         const double a = bdf1 ? 1.0 / dt : 1.5 / dt;
         s.C1 = a + p.M_phi * p.gamma_surf * 3.0 * M_SQRT2 * p.beta / (4.0 * p.eps);
@@ -461,7 +488,7 @@ public:
 
         if (prof && ev_used + 16 > 4096) { int r = profile_flush(); if (r) return r; }
         mark(-1);
-        k_stencil<T><<<g_st, b_st, 0, st>>>(phi[cur], phi[prev], psi[cur], psi[prev], bufA, part1, N, c);
+        k_stencil<T><<<g_st, b_st, stencil_smem_bytes<T>(), st>>>(phi[cur], phi[prev], psi[cur], psi[prev], bufA, part1, N, c);
         mark(0);
         if (warp_path) {
             warp_forward(s, anchor);
@@ -472,7 +499,7 @@ public:
             k_coldct_gram<T><<<N, 512, sm_col, st>>>(bufB, bufA, part2, N, FG, twM, twP, ev, s);
             mark(2);
         }
-        k_solve<<<1, 512, 0, st>>>(part1, part2, sc, so);
+        k_solve<<<1, 256, 0, st>>>(part1, so.nb1, part2, so.nb2, sc, so);
         mark(3);
         if (warp_path) {
             bdf1_launch = so.bdf1;
@@ -481,8 +508,7 @@ public:
             k_comb_icolT<T><<<N / RT4, 512, sm_comb, st>>>(bufA, bufB, N, RT4, lds_c, twM, twP, ev, s, sc, anchor);
             mark(4);
             k_irow<T><<<N / PR, 512, sm_irow, st>>>(bufB, phi[spare], psi[spare], N, PR, twM, twP,
-                                                    phi[cur], phi[prev], psi[cur], psi[prev], so.bdf1, sc, anchor,
-                                                    (uint32_t)steps_taken);
+                                                    phi[cur], phi[prev], psi[cur], psi[prev], so.bdf1, sc, anchor);
             mark(5);
         }
         nlaunch += 6;
@@ -503,10 +529,25 @@ public:
     int queue_steps(int nsteps) override {
         if (!have_state) return CCMSAV_ESTATE;
         if (poisoned) return CCMSAV_ENONFINITE;
-        for (int i = 0; i < nsteps; ++i) {
-            int r = queue_one_step();
-            if (r) return r;
+        int r;
+        // the BDF1 start step and traced steps are launched directly
+        while (nsteps > 0 && (steps_taken == 0 || prof || graphs_failed)) {
+            if ((r = queue_one_step())) return r;
+            --nsteps;
         }
+        // BDF2 steps in groups of three from CUDA graphs (the rotation of the
+        // three levels has period three, so one graph per phase)
+        const long long per_step = 6 + ((flags & CCMSAV_TRACK_ENERGY) ? 2 : 0);
+        while (nsteps >= 3 && !graphs_failed) {
+            const int ph = cur;
+            if (!gexec[ph] && capture_phase() != CCMSAV_OK) { graphs_failed = true; break; }
+            CCM_CUDA(cudaGraphLaunch(gexec[ph], st));
+            steps_taken += 3;
+            nlaunch += 3 * per_step;
+            nsteps -= 3;
+        }
+        while (nsteps-- > 0)
+            if ((r = queue_one_step())) return r;
         return CCMSAV_OK;
     }
 

@@ -51,15 +51,18 @@ enum { NRED1 = 10 };   // k_stencil partials: IV IW IZ sum(psi^n) sum(psi^{n-1})
 enum { NRED2 = 17 };   // gram partials: 15 chi pairs (a <= b over f0' S H Q K), PG, PL
 enum { NF = 8 };       // fields out of k_stencil: f0' S H Q K P g0' LP
 
+// Coefficients of k_stencil in the field precision T (converted once on the
+// host: per-thread FP64 conversions would run on GB300's narrow FP64 pipe).
+template <typename T>
 struct StencilCoef {
     int bdf1;             // 1: start step (phi* = phi_bar = phi^n)
-    double inv_h, inv_h2;
-    double eps, inv_eps, inv_eps2, beta;
-    double Mth;           // M_phi * theta~
-    double C2, C3, betap; // chi coefficients; betap = M_phi gamma_surf 3 sqrt2 beta / (4 eps)
-    double lam;
-    double gin, gout, psin, psout, bin, bout;
-    double M0;
+    T inv_h, inv_h2;
+    T eps, inv_eps, inv_eps2, beta, quarter_inv_eps;
+    T Mth;                // M_phi * theta~
+    T C2, C3, betap;      // chi coefficients; betap = M_phi gamma_surf 3 sqrt2 beta / (4 eps)
+    T lam;
+    T gin, gout, hgin, hgout, psin, psout, bin, bout;
+    T M0;
 };
 
 struct SpecCoef {          // sigma = C1 + C2 s + C3 s^2, tau = Ct + lam s, s = ev[kx] + ev[ky]
@@ -153,6 +156,43 @@ __device__ __forceinline__ double warp_sum_exact(float x) {
 }
 __device__ __forceinline__ double warp_sum_exact(double x) { return warp_sum(x); }
 
+// Double-float (TwoSum) accumulation of FP32 values, then a sum over the G
+// lanes of one lane group (xor offsets below G stay inside the group).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
+    float s, e;
+    two_sum(hi, x, s, e);
+    hi = s;
+    lo += e;
+}
+template <int G>
+__device__ __forceinline__ double group_sum_exact(float hi, float lo) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+        const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
+        const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
+        float s, e;
+        two_sum(hi, ohi, s, e);
+        e += lo + olo;
+        hi = s + e;
+        lo = e - (hi - s);
+    }
+    return (double)hi + (double)lo;
+}
+
+// Per-thread accumulator of a field sum: double-float for FP32 fields, plain
+// FP64 for FP64 fields.
+template <typename T> struct ExactSum;
+template <> struct ExactSum<float> {
+    float hi = 0.f, lo = 0.f;
+    __device__ __forceinline__ void add(float x) { df_add(hi, lo, x); }
+    __device__ __forceinline__ double warp_total() { return group_sum_exact<32>(hi, lo); }
+};
+template <> struct ExactSum<double> {
+    double s = 0.0;
+    __device__ __forceinline__ void add(double x) { s += x; }
+    __device__ __forceinline__ double warp_total() { return warp_sum(s); }
+};
+
 // Neumann ghost cells by even reflection about the boundary face:
 // index -1 -> 0, -2 -> 1, N -> N-1, N+1 -> N-2 (for halo 1 this is the
 // mirror phi_0 = phi_1 of Appendix D; for halo 2 it makes Lap phi at a ghost
@@ -209,148 +249,157 @@ __device__ __forceinline__ double bar_add(double a, double b, double du, double 
 }
 
 // ------------------------------------------------------------------ k_stencil
-// Tile of TX x TY cells per block (one thread per cell).  Shared-memory tiles:
-// phi_bar with a two-cell halo (for Lap^2 phi_bar), and phi*, psi*, the P
-// numerator, psi_bar - psi* and Lap phi_bar with a one-cell halo.
-constexpr int TX = 32, TY = 8;
+// Tile of TX x TYB cells per block of TX x TY threads (each thread handles
+// TYB / TY cells of one column).  Shared-memory tiles: phi_bar with a
+// two-cell halo (for Lap^2 phi_bar), and phi*, psi*, the P numerator,
+// psi_bar - psi* and Lap phi_bar with a one-cell halo.  Partial sums are
+// accumulated per thread over its cells, then reduced once per block.
+constexpr int TX = 32, TY = 8, TYB = 64;
 
 template <typename T>
 __global__ void __launch_bounds__(TX * TY)
 k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
           const T* __restrict__ psn, const T* __restrict__ pso,
-          T* __restrict__ out, double* __restrict__ part, int N, StencilCoef c) {
-    __shared__ T sbar[TY + 4][TX + 4];
-    __shared__ T sph[TY + 2][TX + 2];
-    __shared__ T sps[TY + 2][TX + 2];
-    __shared__ T sP[TY + 2][TX + 2];
-    __shared__ T sdq[TY + 2][TX + 2];
-    __shared__ T slb[TY + 2][TX + 2];
-    __shared__ double sred[(TX * TY / 32) * NRED1];
+          T* __restrict__ out, double* __restrict__ part, int N, StencilCoef<T> c) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    constexpr int W2 = TX + 4, W1 = TX + 2, H1 = TYB + 2;
+    T* sbar = reinterpret_cast<T*>(smraw);              // [TYB+4][W2]
+    T* sph = sbar + (TYB + 4) * W2;                     // [H1][W1] each below
+    T* sps = sph + H1 * W1;
+    T* sP = sps + H1 * W1;
+    T* sdq = sP + H1 * W1;
+    T* slb = sdq + H1 * W1;
+    __shared__ double sred[(TX * TY / 32) * 4];
     __shared__ double smean[2][TX * TY / 32];
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+    __shared__ T smin[TX * TY / 32];
+    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TYB;
     const int tid = threadIdx.y * TX + threadIdx.x;
     // with d = u^n - u^{n-1} (exact for nearby values): u* = u^n + d,
     // u_bar = u^n + d/3, u_bar - u* = -2d/3 (BDF1: u* = u_bar = u^n)
     const T kst = c.bdf1 ? (T)0 : (T)1, kbar = c.bdf1 ? (T)0 : (T)(1.0 / 3.0), kq = c.bdf1 ? (T)0 : (T)(-2.0 / 3.0);
-    const T ih = (T)c.inv_h, ih2 = (T)c.inv_h2;
-    for (int q = tid; q < (TX + 4) * (TY + 4); q += TX * TY) {
-        const int lj = q / (TX + 4), li = q % (TX + 4);
+    const T ih = c.inv_h, ih2 = c.inv_h2;
+    for (int q = tid; q < (TX + 4) * (TYB + 4); q += TX * TY) {
+        const int lj = q / W2, li = q % W2;
         const int gi = reflect(i0 + li - 2, N), gj = reflect(j0 + lj - 2, N);
         const size_t g = (size_t)gj * N + gi;
         const T a = phn[g], da = a - pho[g];
-        sbar[lj][li] = a + kbar * da;
-        if (lj >= 1 && lj <= TY + 2 && li >= 1 && li <= TX + 2) {
+        sbar[lj * W2 + li] = a + kbar * da;
+        if (lj >= 1 && lj <= TYB + 2 && li >= 1 && li <= TX + 2) {
+            const int o = (lj - 1) * W1 + (li - 1);
             const T ph = a + kst * da;
             const T u = psn[g], du = u - pso[g];
             const T ps = u + kst * du;
-            sph[lj - 1][li - 1] = ph;
-            sps[lj - 1][li - 1] = ps;
-            sdq[lj - 1][li - 1] = kq * du;
+            sph[o] = ph;
+            sps[o] = ps;
+            sdq[o] = kq * du;
             T sp, cp;
             sincospi_<T>((T)0.5 * ph, &sp, &cp);
-            sP[lj - 1][li - 1] = (T)0.5 * ((T)c.gin * ((T)1 + sp) * (ps - (T)c.psin)
-                                           + (T)c.gout * ((T)1 - sp) * (ps - (T)c.psout));
+            sP[o] = (T)0.5 * (c.gin * ((T)1 + sp) * (ps - c.psin) + c.gout * ((T)1 - sp) * (ps - c.psout));
         }
     }
     __syncthreads();
     // Lap phi_bar on the one-cell-halo region (sums of neighbour differences:
     // each difference of nearby values is exact, so the rounding is relative
     // to the Laplacian, not to the field)
-    for (int q = tid; q < (TX + 2) * (TY + 2); q += TX * TY) {
-        const int lj = q / (TX + 2) + 1, li = q % (TX + 2) + 1;
-        const T C = sbar[lj][li];
-        slb[lj - 1][li - 1] = (((sbar[lj][li + 1] - C) + (sbar[lj][li - 1] - C))
-                               + ((sbar[lj + 1][li] - C) + (sbar[lj - 1][li] - C))) * ih2;
+    for (int q = tid; q < W1 * H1; q += TX * TY) {
+        const int lj = q / W1 + 1, li = q % W1 + 1;
+        const T* b = sbar + lj * W2 + li;
+        const T C = b[0];
+        slb[q] = (((b[1] - C) + (b[-1] - C)) + ((b[W2] - C) + (b[-W2] - C))) * ih2;
     }
     __syncthreads();
-    const int li = threadIdx.x + 1, lj = threadIdx.y + 1;
-    const int gi = i0 + threadIdx.x, gj = j0 + threadIdx.y;
-    const bool inside = gi < N && gj < N;     // tiles overhang grids smaller than TX x TY
-    const size_t g = inside ? (size_t)gj * N + gi : 0;
-    const T pC = sph[lj][li], pE = sph[lj][li + 1], pW = sph[lj][li - 1], pN = sph[lj + 1][li], pS = sph[lj - 1][li];
-    const T qC = sps[lj][li];
-    const T lapp = (((pE - pC) + (pW - pC)) + ((pN - pC) + (pS - pC))) * ih2;
-    const T dC = sdq[lj][li];
-    const T lapd = (((sdq[lj][li + 1] - dC) + (sdq[lj][li - 1] - dC))
-                    + ((sdq[lj + 1][li] - dC) + (sdq[lj - 1][li] - dC))) * ih2;
-    const T lbC = slb[lj][li];
-    const T lap2b = (((slb[lj][li + 1] - lbC) + (slb[lj][li - 1] - lbC))
-                     + ((slb[lj + 1][li] - lbC) + (slb[lj - 1][li] - lbC))) * ih2;
-    const T p2 = pC * pC, p3m = pC * (p2 - (T)1);
-    const T eps = (T)c.eps, ieps = (T)c.inv_eps, ieps2 = (T)c.inv_eps2;
-    // face gradients (zero on boundary faces through the mirrored ghosts)
-    const T gE = (pE - pC) * ih, gW = (pC - pW) * ih, gN = (pN - pC) * ih, gS = (pC - pS) * ih;
-    const T gbar = (T)0.5 * (gE * gE + gW * gW) + (T)0.5 * (gN * gN + gS * gS);
-    const T divp2g = (((T)0.5 * (p2 + pE * pE)) * gE - ((T)0.5 * (p2 + pW * pW)) * gW
-                      + ((T)0.5 * (p2 + pN * pN)) * gN - ((T)0.5 * (p2 + pS * pS)) * gS) * ih;
-    const T Snum = pC * (p2 - (T)1 - (T)c.beta) * ieps;
-    const T Hv = (T)1.0606601717798212866 * (p3m * ieps - eps * lapp);   // 3 sqrt2 / 4
-    const T Qnum = (T)6 * (pC * gbar - divp2g) + p3m * ((T)3 * p2 - (T)1) * ieps2;
-    T sp, cp;
-    sincospi_<T>((T)0.5 * pC, &sp, &cp);
-    const T dp = (T)1.5707963267948966192 * cp;
-    const T hgin = (T)(0.5 * c.gin), hgout = (T)(0.5 * c.gout);
-    const T fin = hgin * (qC - (T)c.psin) * (qC - (T)c.psin) + (T)c.bin;
-    const T fout = hgout * (qC - (T)c.psout) * (qC - (T)c.psout) + (T)c.bout;
-    const T Knum = (T)0.5 * dp * (fin - fout);
-    const T PC = sP[lj][li];
-    // face mobilities M(A phi*) and the flux divergence of P
-    const T M0 = (T)c.M0;
-    auto mob = [&](T a) { T s = a * a - (T)1; return (T)1 - M0 * s * s; };
-    const T mE = mob((T)0.5 * (pC + pE)), mW = mob((T)0.5 * (pC + pW));
-    const T mN = mob((T)0.5 * (pC + pN)), mS = mob((T)0.5 * (pC + pS));
-    const T LP = (mE * (sP[lj][li + 1] - PC) - mW * (PC - sP[lj][li - 1])
-                  + mN * (sP[lj + 1][li] - PC) - mS * (PC - sP[lj - 1][li])) * ih2;
-    const T bC = sbar[lj + 1][li + 1];
-    const T f0 = (T)c.C2 * slb[lj][li] - (T)c.C3 * lap2b - (T)c.Mth * lapp - (T)c.betap * bC;
-    const T g0 = (T)c.lam * lapd;
-    const size_t NN = (size_t)N * N;
-    if (inside) {
-        out[0 * NN + g] = f0;
-        out[1 * NN + g] = Snum;
-        out[2 * NN + g] = Hv;
-        out[3 * NN + g] = Qnum;
-        out[4 * NN + g] = Knum;
-        out[5 * NN + g] = PC;
-        out[6 * NN + g] = g0;
-        out[7 * NN + g] = LP;
-    }
-    // partial sums
-    const T vv = p2 - (T)1 - (T)c.beta;
-    T red[NRED1];
-#pragma unroll
-    for (int i = 0; i < NRED1; ++i) red[i] = 0;
-    if (inside) {
-        red[0] = vv * vv * (T)(0.25 * c.inv_eps);
-        red[1] = (T)6 * p2 * gbar + p3m * p3m * ieps2;
-        red[2] = ((T)1 + sp) * fin + ((T)1 - sp) * fout;
-    }
-    // minimum face mobility over interior faces (boundary faces carry no flux)
+    T acc0 = 0, acc1 = 0, acc2 = 0;
     T mm = (T)1e30;
-    if (inside) {
-        if (gi + 1 < N) mm = min(mm, mE);
-        if (gi > 0) mm = min(mm, mW);
-        if (gj + 1 < N) mm = min(mm, mN);
-        if (gj > 0) mm = min(mm, mS);
+    ExactSum<T> sum_n, sum_o;
+    const size_t NN = (size_t)N * N;
+    const int gi = i0 + threadIdx.x;
+    const int li = threadIdx.x + 1;
+    for (int jj = threadIdx.y; jj < TYB; jj += TY) {
+        const int lj = jj + 1, gj = j0 + jj;
+        const bool inside = gi < N && gj < N;   // tiles overhang grids smaller than the tile
+        const size_t g = inside ? (size_t)gj * N + gi : 0;
+        const int o = lj * W1 + li;
+        const T pC = sph[o], pE = sph[o + 1], pW = sph[o - 1], pN = sph[o + W1], pS = sph[o - W1];
+        const T qC = sps[o];
+        const T lapp = (((pE - pC) + (pW - pC)) + ((pN - pC) + (pS - pC))) * ih2;
+        const T dC = sdq[o];
+        const T lapd = (((sdq[o + 1] - dC) + (sdq[o - 1] - dC)) + ((sdq[o + W1] - dC) + (sdq[o - W1] - dC))) * ih2;
+        const T lbC = slb[o];
+        const T lap2b = (((slb[o + 1] - lbC) + (slb[o - 1] - lbC)) + ((slb[o + W1] - lbC) + (slb[o - W1] - lbC))) * ih2;
+        const T p2 = pC * pC, p3m = pC * (p2 - (T)1);
+        // face gradients (zero on boundary faces through the mirrored ghosts)
+        const T gE = (pE - pC) * ih, gW = (pC - pW) * ih, gN = (pN - pC) * ih, gS = (pC - pS) * ih;
+        const T gbar = (T)0.5 * (gE * gE + gW * gW) + (T)0.5 * (gN * gN + gS * gS);
+        const T divp2g = (((T)0.5 * (p2 + pE * pE)) * gE - ((T)0.5 * (p2 + pW * pW)) * gW
+                          + ((T)0.5 * (p2 + pN * pN)) * gN - ((T)0.5 * (p2 + pS * pS)) * gS) * ih;
+        const T Snum = pC * (p2 - (T)1 - c.beta) * c.inv_eps;
+        const T Hv = (T)1.0606601717798212866 * (p3m * c.inv_eps - c.eps * lapp);   // 3 sqrt2 / 4
+        const T Qnum = (T)6 * (pC * gbar - divp2g) + p3m * ((T)3 * p2 - (T)1) * c.inv_eps2;
+        T sp, cp;
+        sincospi_<T>((T)0.5 * pC, &sp, &cp);
+        const T dp = (T)1.5707963267948966192 * cp;
+        const T fin = c.hgin * (qC - c.psin) * (qC - c.psin) + c.bin;
+        const T fout = c.hgout * (qC - c.psout) * (qC - c.psout) + c.bout;
+        const T Knum = (T)0.5 * dp * (fin - fout);
+        const T PC = sP[o];
+        // face mobilities M(A phi*) and the flux divergence of P
+        auto mob = [&](T a) { T s = a * a - (T)1; return (T)1 - c.M0 * s * s; };
+        const T mE = mob((T)0.5 * (pC + pE)), mW = mob((T)0.5 * (pC + pW));
+        const T mN = mob((T)0.5 * (pC + pN)), mS = mob((T)0.5 * (pC + pS));
+        const T LP = (mE * (sP[o + 1] - PC) - mW * (PC - sP[o - 1])
+                      + mN * (sP[o + W1] - PC) - mS * (PC - sP[o - W1])) * ih2;
+        const T bC = sbar[(lj + 1) * W2 + li + 1];
+        const T f0 = c.C2 * lbC - c.C3 * lap2b - c.Mth * lapp - c.betap * bC;
+        const T g0 = c.lam * lapd;
+        if (inside) {
+            out[0 * NN + g] = f0;
+            out[1 * NN + g] = Snum;
+            out[2 * NN + g] = Hv;
+            out[3 * NN + g] = Qnum;
+            out[4 * NN + g] = Knum;
+            out[5 * NN + g] = PC;
+            out[6 * NN + g] = g0;
+            out[7 * NN + g] = LP;
+            const T vv = p2 - (T)1 - c.beta;
+            acc0 += vv * vv * c.quarter_inv_eps;
+            acc1 += (T)6 * p2 * gbar + p3m * p3m * c.inv_eps2;
+            acc2 += ((T)1 + sp) * fin + ((T)1 - sp) * fout;
+            // minimum face mobility over interior faces (boundary faces carry no flux)
+            if (gi + 1 < N) mm = min(mm, mE);
+            if (gi > 0) mm = min(mm, mW);
+            if (gj + 1 < N) mm = min(mm, mN);
+            if (gj > 0) mm = min(mm, mS);
+            // sums of psi^n and psi^{n-1} to ~1e-13 (mass bookkeeping of the FP32 path)
+            sum_n.add(psn[g]);
+            sum_o.add(pso[g]);
+        }
     }
     double* prow = part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * NRED1;
-    block_sum_store<NRED1, T>(red, prow, sred);
-    // sums of psi^n and psi^{n-1} to ~1e-13 (mass bookkeeping of the FP32 path)
-    const T un = inside ? psn[g] : (T)0, uo = inside ? pso[g] : (T)0;
-    const double sn = warp_sum_exact(un), so = warp_sum_exact(uo);
-    if ((tid & 31) == 0) { smean[0][tid >> 5] = sn; smean[1][tid >> 5] = so; }
+    const int lane = tid & 31, wp = tid >> 5;
+    const T w0 = warp_sum(acc0), w1 = warp_sum(acc1), w2 = warp_sum(acc2);
+    const double sn = sum_n.warp_total(), so = sum_o.warp_total();
     mm = warp_min(mm);
-    __shared__ T smin[TX * TY / 32];
-    if ((tid & 31) == 0) smin[tid >> 5] = mm;
+    if (lane == 0) {
+        sred[wp * 4 + 0] = (double)w0; sred[wp * 4 + 1] = (double)w1; sred[wp * 4 + 2] = (double)w2;
+        smean[0][wp] = sn; smean[1][wp] = so; smin[wp] = mm;
+    }
     __syncthreads();
     if (tid == 0) {
+        double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
         T m = smin[0];
-        double a = 0.0, b = 0.0;
-        for (int w = 0; w < TX * TY / 32; ++w) { m = min(m, smin[w]); a += smean[0][w]; b += smean[1][w]; }
-        prow[3] = a;
-        prow[4] = b;
-        prow[8] = (double)m;
+        for (int w = 0; w < TX * TY / 32; ++w) {
+            a0 += sred[w * 4]; a1 += sred[w * 4 + 1]; a2 += sred[w * 4 + 2];
+            a3 += smean[0][w]; a4 += smean[1][w];
+            m = min(m, smin[w]);
+        }
+        prow[0] = a0; prow[1] = a1; prow[2] = a2; prow[3] = a3; prow[4] = a4;
+        prow[5] = 0; prow[6] = 0; prow[7] = 0;
+        prow[8] = (double)m; prow[9] = 0;
     }
+}
+
+template <typename T> __host__ __device__ constexpr size_t stencil_smem_bytes() {
+    return ((size_t)(TYB + 4) * (TX + 4) + 5 * (size_t)(TYB + 2) * (TX + 2)) * sizeof(T);
 }
 
 // The pair k (0 <= k <= M/2) of the line transforms touches the modes
@@ -513,46 +562,44 @@ k_coldct_gram(const T* __restrict__ in, T* __restrict__ spec, double* __restrict
 // (thread 0) the scalar algebra of Appendix B Steps 1 and 4.
 __device__ inline bool finite_(double x) { return isfinite(x); }
 
-static __global__ void __launch_bounds__(512)
-k_solve(const double* __restrict__ p1, const double* __restrict__ p2, DevScalars* sc, SolveCoef co) {
-    constexpr int NR = NRED1 + NRED2;
-    __shared__ double red[16][NR];
+// One block of 8 warps.  Warp w reduces columns w, w+8, ... of the partial-sum rows
+// (stencil rows: IV IW IZ sum psi^n sum psi^{n-1} . . . minM; Gram rows:
+// the 17 Gram sums) in a fixed order (four strided accumulators per lane,
+// then a shuffle tree), so the result is deterministic.  Thread 0 then does
+// the scalar algebra with every loop unrolled (registers only; a dynamic row
+// index would put the 5x5 matrix in local memory) and one reciprocal per
+// pivot: FP64 latency dominates this kernel on GB300.
+enum { NRQ = NRED1 + NRED2 };
+__device__ __forceinline__ double red_op(bool is_min, double a, double b) { return is_min ? fmin(a, b) : a + b; }
+
+static __global__ void __launch_bounds__(256)
+k_solve(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, int nb2,
+        DevScalars* sc, SolveCoef co) {
+    constexpr int NR = NRQ;
     __shared__ double fin_[NR];
-    const int t = threadIdx.x, lane = t & 31, wp = t >> 5;
-    double acc[NR];
-#pragma unroll
-    for (int i = 0; i < NR; ++i) acc[i] = 0.0;
-    double mmin = 1e300;
-    for (int b = t; b < co.nb1; b += blockDim.x) {
-        const double* q = p1 + (size_t)b * NRED1;
-#pragma unroll
-        for (int i = 0; i < 8; ++i) acc[i] += q[i];
-        mmin = fmin(mmin, q[8]);
-    }
-    for (int b = t; b < co.nb2; b += blockDim.x) {
-        const double* q = p2 + (size_t)b * NRED2;
-#pragma unroll
-        for (int i = 0; i < NRED2; ++i) acc[NRED1 + i] += q[i];
-    }
-    acc[8] = mmin;
-    // fixed-order tree: warp shuffles, then the 16 warp results in order
-#pragma unroll
-    for (int i = 0; i < NR; ++i) {
-        double v = acc[i];
-        for (int o = 16; o > 0; o >>= 1) {
-            const double w = __shfl_xor_sync(0xffffffffu, v, o);
-            v = (i == 8) ? fmin(v, w) : v + w;
+    const int lane = threadIdx.x & 31;
+    for (int wp = threadIdx.x >> 5; wp < NR; wp += blockDim.x >> 5) {
+        const bool is_min = (wp == 8);
+        const double* base = wp < NRED1 ? p1 + wp : p2 + (wp - NRED1);
+        const int stride = wp < NRED1 ? NRED1 : NRED2;
+        const int nb = wp < NRED1 ? nb1 : nb2;
+        const double id = is_min ? 1e300 : 0.0;
+        double a0 = id, a1 = id, a2 = id, a3 = id;
+        int b = lane;
+        for (; b + 96 < nb; b += 128) {
+            a0 = red_op(is_min, a0, base[(size_t)b * stride]);
+            a1 = red_op(is_min, a1, base[(size_t)(b + 32) * stride]);
+            a2 = red_op(is_min, a2, base[(size_t)(b + 64) * stride]);
+            a3 = red_op(is_min, a3, base[(size_t)(b + 96) * stride]);
         }
-        if (lane == 0) red[wp][i] = v;
+        for (; b < nb; b += 32) a0 = red_op(is_min, a0, base[(size_t)b * stride]);
+        double v = red_op(is_min, red_op(is_min, a0, a1), red_op(is_min, a2, a3));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v = red_op(is_min, v, __shfl_xor_sync(0xffffffffu, v, o));
+        if (lane == 0) fin_[wp] = v;
     }
     __syncthreads();
-    if (t < NR) {
-        double v = red[0][t];
-        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) v = (t == 8) ? fmin(v, red[w][t]) : v + red[w][t];
-        fin_[t] = v;
-    }
-    __syncthreads();
-    if (t != 0) return;
+    if (threadIdx.x != 0) return;
     if (sc->status != 0) return;
     const double* r = fin_;
     const double IV = r[0], IW = r[1], IZ = r[2], sum_n = r[3], sum_o = r[4], minM = r[8];
@@ -562,28 +609,29 @@ k_solve(const double* __restrict__ p1, const double* __restrict__ p2, DevScalars
     ok = ok && IV > 0 && IW > 0 && IZ > 0 && minM > 0;
     if (!ok) { sc->status = -5; return; }
     const double h2 = co.h2;
-    const double nS = 0.5 / sqrt(h2 * IV), nQ = 1.0 / sqrt(h2 * IW), nK = 1.0 / sqrt(h2 * IZ);
+    const double nS = 0.5 * rsqrt(h2 * IV), nQ = rsqrt(h2 * IW), nK = rsqrt(h2 * IZ);
     const double nrm[4] = {nS, 1.0, nQ, nK};
     // reference SAVs X_bar (Step 1 with the increments taken about phi_bar)
+    constexpr double third = 1.0 / 3.0;
     double xb[4];
     if (co.bdf1) { xb[0] = sc->V; xb[1] = sc->U; xb[2] = sc->W; xb[3] = sc->Z; }
     else {
-        xb[0] = (4.0 * sc->V - sc->Vo) / 3.0;
-        xb[1] = (4.0 * sc->U - sc->Uo) / 3.0;
-        xb[2] = (4.0 * sc->W - sc->Wo) / 3.0;
-        xb[3] = (4.0 * sc->Z - sc->Zo) / 3.0;
+        xb[0] = (4.0 * sc->V - sc->Vo) * third;
+        xb[1] = (4.0 * sc->U - sc->Uo) * third;
+        xb[2] = (4.0 * sc->W - sc->Wo) * third;
+        xb[3] = (4.0 * sc->Z - sc->Zo) * third;
     }
     const double cc[4] = {co.cgs, co.cga, co.cgb, co.cgo};
-    // Gram index for a <= b over (f0', S, H, Q, K)
-    auto G = [&](int a, int b) {
-        if (a > b) { int x = a; a = b; b = x; }
-        int idx = 0;
-        for (int i = 0; i < a; ++i) idx += 5 - i;
-        return Gm[idx + (b - a)];
+    // Gram entry (a, b) over (f0', S, H, Q, K), stored for a <= b row by row
+    auto G = [&](int a, int b) -> double {
+        const int lo = a < b ? a : b, hi = a < b ? b : a;
+        return Gm[lo * 5 - lo * (lo - 1) / 2 + (hi - lo)];
     };
     double A[5][6];
+#pragma unroll
     for (int i = 0; i < 4; ++i) {
         double bi = G(0, i + 1);
+#pragma unroll
         for (int j = 0; j < 4; ++j) {
             const double gij = h2 * nrm[i] * nrm[j] * G(i + 1, j + 1);
             A[i][j] = (i == j ? 1.0 : 0.0) + cc[j] * gij;
@@ -597,21 +645,39 @@ k_solve(const double* __restrict__ p1, const double* __restrict__ p2, DevScalars
     A[4][3] = -PL;
     A[4][4] = 1.0 - PL;
     A[4][5] = h2 * nK * Gm[15] + xb[3] * PL;
-    // Gaussian elimination with partial pivoting
+    // Gaussian elimination with partial pivoting (all indices compile-time)
+#pragma unroll
     for (int k = 0; k < 5; ++k) {
         int piv = k;
-        for (int i = k + 1; i < 5; ++i) if (fabs(A[i][k]) > fabs(A[piv][k])) piv = i;
-        if (piv != k) for (int j = 0; j < 6; ++j) { double x = A[k][j]; A[k][j] = A[piv][j]; A[piv][j] = x; }
-        const double d = A[k][k];
-        if (!(fabs(d) > 0)) { sc->status = -5; return; }
+        double pmax = fabs(A[k][k]);
+#pragma unroll
         for (int i = k + 1; i < 5; ++i) {
-            const double f = A[i][k] / d;
-            for (int j = k; j < 6; ++j) A[i][j] -= f * A[k][j];
+            const bool g = fabs(A[i][k]) > pmax;
+            pmax = g ? fabs(A[i][k]) : pmax;
+            piv = g ? i : piv;
+        }
+#pragma unroll
+        for (int i = k + 1; i < 5; ++i) {
+            const bool sw = (i == piv);
+#pragma unroll
+            for (int j = 0; j < 6; ++j) { const double a = A[k][j], b = A[i][j]; A[k][j] = sw ? b : a; A[i][j] = sw ? a : b; }
+        }
+        if (!(pmax > 0)) { sc->status = -5; return; }
+        const double rinv = 1.0 / A[k][k];
+#pragma unroll
+        for (int i = k + 1; i < 5; ++i) {
+            const double f = A[i][k] * rinv;
+            // full rows (columns < k are eliminated already and unused): a
+            // loop start depending on k would leave the matrix in local memory
+#pragma unroll
+            for (int j = 0; j < 6; ++j) A[i][j] -= f * A[k][j];
         }
     }
     double x[5];
+#pragma unroll
     for (int i = 4; i >= 0; --i) {
         double s = A[i][5];
+#pragma unroll
         for (int j = i + 1; j < 5; ++j) s -= A[i][j] * x[j];
         x[i] = s / A[i][i];
     }
@@ -629,7 +695,7 @@ k_solve(const double* __restrict__ p1, const double* __restrict__ p2, DevScalars
     // the conserved value (means of the stored levels summed to ~1e-13)
     if (co.anchor) {
         const double mn = sum_n / co.NN, mo = sum_o / co.NN;
-        const double mbar = co.bdf1 ? mn : mn + (mn - mo) / 3.0;
+        const double mbar = co.bdf1 ? mn : mn + (mn - mo) * third;
         sc->anchor = sc->mass_mode - mbar;
     } else {
         sc->anchor = 0.0;
@@ -717,7 +783,7 @@ __global__ void __launch_bounds__(512)
 k_irow(const T* __restrict__ in, T* __restrict__ phi_new, T* __restrict__ psi_new, int N, int PR,
        const cplx<T>* __restrict__ twM, const PostTw<T>* __restrict__ twP,
        const T* __restrict__ phn, const T* __restrict__ pho, const T* __restrict__ psn, const T* __restrict__ pso,
-       int bdf1, const DevScalars* __restrict__ dsc, int anchor_mass, uint32_t step) {
+       int bdf1, const DevScalars* __restrict__ dsc, int anchor_mass) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const int M = N / 2, ldc = padded_len(M);
     const int E = M < 8 ? M : 8, G = M / E, P = blockDim.x / G;
@@ -727,6 +793,7 @@ k_irow(const T* __restrict__ in, T* __restrict__ phi_new, T* __restrict__ psi_ne
     const T inv0 = (T)(1.0 / (M * sqrt(1.0 / N))), inv = (T)(1.0 / (M * sqrt(2.0 / N)));
     const int nlines = 2 * PR;
     const T anc = anchor_mass ? (T)dsc->anchor : (T)0;
+    const uint32_t step = (uint32_t)dsc->steps;         // dither key
     for (int l0 = 0; l0 < nlines; l0 += P) {
         const int nl = min(P, nlines - l0);
         for (int q = threadIdx.x; q < nl * (M / 2 + 1); q += blockDim.x) {

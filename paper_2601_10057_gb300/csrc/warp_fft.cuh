@@ -108,7 +108,9 @@ template <> struct Shape<1024> { static constexpr int E = 32, G = 32; };
 // Per-line buffer length (complex values) for the transpose and the
 // natural-order result.
 template <int M> __host__ __device__ constexpr int buf_len() {
-    return Shape<M>::E * (Shape<M>::G + 1);
+    // + 2 complex: as a float row the buffer stride is then 4 mod 32 words,
+    // which keeps the strided reads of the transposed writes conflict-free
+    return Shape<M>::E * (Shape<M>::G + 1) + 2;
 }
 
 // Steps 1-4.  v: this lane's E values in four-step order.  buf: this line's

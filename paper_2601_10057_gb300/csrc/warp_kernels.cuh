@@ -21,28 +21,7 @@ struct SpecCoefF {        // FP32 copy of SpecCoef for the FP32 spectral kernels
 
 constexpr int kWarps = 8;
 
-// Double-float (TwoSum) accumulation of FP32 values, then a sum over the G
-// lanes of one line group (xor offsets below G stay inside the group).
-__device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
-    float s, e;
-    two_sum(hi, x, s, e);
-    hi = s;
-    lo += e;
-}
-template <int G>
-__device__ __forceinline__ double group_sum_exact(float hi, float lo) {
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-        const float ohi = __shfl_xor_sync(0xffffffffu, hi, o);
-        const float olo = __shfl_xor_sync(0xffffffffu, lo, o);
-        float s, e;
-        two_sum(hi, ohi, s, e);
-        e += lo + olo;
-        hi = s + e;
-        lo = e - (hi - s);
-    }
-    return (double)hi + (double)lo;
-}
+
 
 template <int M> struct WGeo {
     static constexpr int E = wf::Shape<M>::E, G = wf::Shape<M>::G;
@@ -53,15 +32,19 @@ template <int M> struct WGeo {
 };
 
 // ------------------------------------------------------------------ kw_rowdct_T
+// SLOTS rows of field blockIdx.y per CTA (one line per lane group).  The
+// post-processed DCT row replaces the line's complex buffer in place (each
+// lane first holds all its pairs in registers), so the buffers double as the
+// staging area of the transposed write.
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32)
-kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out, int RT, int lds,
+kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
             const cplx<float>* __restrict__ tw2, const PostTw<float>* __restrict__ twP) {
     using Gm = WGeo<M>;
-    constexpr int N = 2 * M, G = Gm::G, E = Gm::E;
+    constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS, NP = (M / 2 + G) / G;
+    constexpr int LDS = 2 * Gm::BUF;                 // floats per line buffer
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
-    float* stage = reinterpret_cast<float*>(smraw + Gm::buf_bytes());
     const size_t NN = (size_t)N * N;
     const int f = blockIdx.y, y0 = blockIdx.x * RT;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -69,33 +52,38 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out, int RT, int l
     const int slot = warp * Gm::LPW + grp;
     cplx<float>* buf = bufs + (size_t)slot * Gm::BUF;
     const float cn0 = sqrtf(1.0f / N), cn = sqrtf(2.0f / N);
-    for (int l0 = 0; l0 < RT; l0 += Gm::SLOTS) {
-        const int l = l0 + slot;
-        const bool act = l < RT;
-        const float* x = in + f * NN + (size_t)(y0 + (act ? l : 0)) * N;
+    {
         cplx<float> v[E];
-        wf::pack_fwd_global<M>(x, v, n2);
+        wf::pack_fwd_global<M>(in + f * NN + (size_t)(y0 + slot) * N, v, n2);
         wf::fourstep<float, M, false>(v, buf, tw2, n2);
-        if (act) {
-            float* srow = stage + (size_t)l * lds;
-            for (int k = n2; k <= M / 2; k += G) {
-                const Quad<float> X = wf::post_pair(buf[k], buf[(M - k) & (M - 1)], k, twP[k], cn0, cn);
-                srow[k] = X.xk;
-                if (pair_mode_valid(1, k, M)) srow[N - k] = X.xNk;
-                if (pair_mode_valid(2, k, M)) srow[M - k] = X.xMk;
-                if (pair_mode_valid(3, k, M)) srow[M + k] = X.xMpk;
-            }
+    }
+    Quad<float> X[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        const int k = n2 + G * i;
+        if (k <= M / 2) X[i] = wf::post_pair(buf[k], buf[(M - k) & (M - 1)], k, twP[k], cn0, cn);
+    }
+    __syncwarp();
+    float* srow = reinterpret_cast<float*>(buf);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        const int k = n2 + G * i;
+        if (k <= M / 2) {
+            srow[k] = X[i].xk;
+            if (pair_mode_valid(1, k, M)) srow[N - k] = X[i].xNk;
+            if (pair_mode_valid(2, k, M)) srow[M - k] = X[i].xMk;
+            if (pair_mode_valid(3, k, M)) srow[M + k] = X[i].xMpk;
         }
-        __syncwarp();
     }
     __syncthreads();
+    const float* stage = reinterpret_cast<const float*>(bufs);
     float* dst = out + f * NN;
-    const int R4 = RT / 4;
+    constexpr int R4 = RT / 4;
     for (int q = threadIdx.x; q < R4 * N; q += blockDim.x) {
         const int r4 = q % R4, kx = q / R4;
-        const float* s = stage + (size_t)(4 * r4) * lds + kx;
+        const float* s = stage + (size_t)(4 * r4) * LDS + kx;
         *reinterpret_cast<float4*>(dst + (size_t)kx * N + y0 + 4 * r4) =
-            make_float4(s[0], s[lds], s[2 * lds], s[3 * lds]);
+            make_float4(s[0], s[LDS], s[2 * LDS], s[3 * LDS]);
     }
 }
 
@@ -159,163 +147,185 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
 }
 
 // ------------------------------------------------------------------ kw_comb_icolT
-// RT spectral rows per CTA, two lines (phi^, psi^) per row.
+// RT = SLOTS/2 spectral rows per CTA, two lines (d_phi^, d_psi^) per row.
+// Phase 1 (all threads): gather the spectra, combine, divide, pre-process
+// into the line buffers.  Phase 2 (per line): inverse four-step FFT and
+// unpack in place.  Phase 3: transposed write from the buffers.
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32)
-kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out, int RT, int lds,
+kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
               const cplx<float>* __restrict__ tw2, const PostTw<float>* __restrict__ twP,
               const float* __restrict__ evf, SpecCoefF sc, DevScalars* __restrict__ dsc,
               int anchor_mass) {
     using Gm = WGeo<M>;
-    constexpr int N = 2 * M, G = Gm::G, E = Gm::E;
+    constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS / 2, NU = (M / 2 + G - 1) / G;
+    constexpr int LDS = 2 * Gm::BUF;
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
-    float* stage = reinterpret_cast<float*>(smraw + Gm::buf_bytes());     // [2][RT][lds]
     const size_t NN = (size_t)N * N;
     const int kx0 = blockIdx.x * RT;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = lane / G, n2 = lane % G;
-    const int slot = warp * Gm::LPW + grp;
-    cplx<float>* buf = bufs + (size_t)slot * Gm::BUF;
     const float inv0 = 1.0f / (M * sqrtf(1.0f / N)), inv = 1.0f / (M * sqrtf(2.0f / N));
     const float aS = (float)dsc->alpha[0], aH = (float)dsc->alpha[1], aQ = (float)dsc->alpha[2];
     const float aK = (float)dsc->alpha[3], aL = (float)dsc->alpha[4];
-    const int nlines = 2 * RT;
-    for (int l0 = 0; l0 < nlines; l0 += Gm::SLOTS) {
-        const int l = l0 + slot;
-        const bool act = l < nlines;
-        const int r = (act ? l : 0) >> 1, fld = (act ? l : 0) & 1;
+    constexpr int PAIRS = M / 2 + 1;
+#pragma unroll 2
+    for (int q = threadIdx.x; q < 2 * RT * PAIRS; q += blockDim.x) {
+        const int l = q / PAIRS, k = q % PAIRS;
+        const int r = l >> 1, fld = l & 1;
         const int kx = kx0 + r;
         const float evx = evf[kx];
-        for (int k = n2; k <= M / 2; k += G) {
-            const int kys[4] = {k, N - k, M - k, M + k};
-            float vals[4];
+        const int kys[4] = {k, N - k, M - k, M + k};
+        float vals[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                if (u == 1 && k == 0) { vals[u] = 0.f; continue; }
-                const int ky = kys[u];
-                const float s = evx + evf[ky];
-                const size_t o = (size_t)kx * N + ky;
-                if (fld == 0) {
-                    const float isig = 1.0f / (sc.C1 + s * (sc.C2 + sc.C3 * s));
-                    vals[u] = (spec[o] - aS * spec[NN + o] - aH * spec[2 * NN + o]
-                               - aQ * spec[3 * NN + o] - aK * spec[4 * NN + o]) * isig;
-                } else {
-                    const float itau = 1.0f / (sc.Ct + sc.lam * s);
-                    vals[u] = (spec[6 * NN + o] + aL * spec[7 * NN + o]) * itau;
-                    if (anchor_mass && kx == 0 && ky == 0) vals[u] = 0.f;
-                }
+        for (int u = 0; u < 4; ++u) {
+            if (u == 1 && k == 0) { vals[u] = 0.f; continue; }
+            const int ky = kys[u];
+            const float s = evx + evf[ky];
+            const size_t o = (size_t)kx * N + ky;
+            if (fld == 0) {
+                const float isig = 1.0f / (sc.C1 + s * (sc.C2 + sc.C3 * s));
+                vals[u] = (__ldg(spec + o) - aS * __ldg(spec + NN + o) - aH * __ldg(spec + 2 * NN + o)
+                           - aQ * __ldg(spec + 3 * NN + o) - aK * __ldg(spec + 4 * NN + o)) * isig;
+            } else {
+                const float itau = 1.0f / (sc.Ct + sc.lam * s);
+                vals[u] = (__ldg(spec + 6 * NN + o) + aL * __ldg(spec + 7 * NN + o)) * itau;
+                // d_psi has zero mean (mass conservation); the FP32 path sets the
+                // zero mode exactly and keeps the stored mean with the anchor
+                if (anchor_mass && kx == 0 && ky == 0) vals[u] = 0.f;
             }
-            cplx<float> zk, zMk;
-            pre_inverse(Quad<float>{vals[0], vals[1], vals[2], vals[3]}, k, twP[k], inv0, inv, zk, zMk);
-            buf[k] = zk;
-            if (k > 0) buf[M - k] = zMk;
         }
-        __syncwarp();
+        cplx<float> zk, zMk;
+        pre_inverse(Quad<float>{vals[0], vals[1], vals[2], vals[3]}, k, twP[k], inv0, inv, zk, zMk);
+        cplx<float>* b = bufs + (size_t)l * Gm::BUF;
+        b[k] = zk;
+        if (k > 0) b[M - k] = zMk;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int grp = lane / G, n2 = lane % G;
+    const int slot = warp * Gm::LPW + grp;              // line = slot: row slot/2, field slot%2
+    cplx<float>* buf = bufs + (size_t)slot * Gm::BUF;
+    {
         cplx<float> v[E];
 #pragma unroll
         for (int n1 = 0; n1 < E; ++n1) v[n1] = buf[G * n1 + n2];
         __syncwarp();
         wf::fourstep<float, M, true>(v, buf, tw2, n2);
-        float dhi = 0.f, dlo = 0.f;
-        if (act) {
-            float* srow = stage + (size_t)(fld * RT + r) * lds;
-            for (int m = n2; m < M / 2; m += G) {
-                const cplx<float> a = buf[m], b = buf[M - 1 - m];
-                *reinterpret_cast<float4*>(srow + 4 * m) = make_float4(a.x, b.y, a.y, b.x);
-                df_add(dhi, dlo, a.x); df_add(dhi, dlo, b.y); df_add(dhi, dlo, a.y); df_add(dhi, dlo, b.x);
-            }
-        }
-        // FP32 path: the zero-mean psi increment's kx = 0 column should sum to 0
-        // over y; record what the FP32 transform left (removed in kw_irow)
-        const double dsum = group_sum_exact<G>(dhi, dlo);
-        if (anchor_mass && act && fld == 1 && kx == 0 && n2 == 0) dsc->dc_col = dsum;
-        __syncwarp();
     }
+    float4 xo[NU];
+    float dhi = 0.f, dlo = 0.f;
+#pragma unroll
+    for (int i = 0; i < NU; ++i) {
+        const int m = n2 + G * i;
+        const cplx<float> a = buf[m], b = buf[M - 1 - m];
+        xo[i] = make_float4(a.x, b.y, a.y, b.x);
+        df_add(dhi, dlo, a.x); df_add(dhi, dlo, b.y); df_add(dhi, dlo, a.y); df_add(dhi, dlo, b.x);
+    }
+    // FP32 path: the zero-mean psi increment's kx = 0 column should sum to 0
+    // over y; record what the FP32 transform left (removed in kw_irow)
+    const double dsum = group_sum_exact<G>(dhi, dlo);
+    if (anchor_mass && (slot & 1) == 1 && kx0 + (slot >> 1) == 0 && n2 == 0) dsc->dc_col = dsum;
+    __syncwarp();
+    float* srow = reinterpret_cast<float*>(buf);
+#pragma unroll
+    for (int i = 0; i < NU; ++i) *reinterpret_cast<float4*>(srow + 4 * (n2 + G * i)) = xo[i];
     __syncthreads();
-    const int R4 = RT / 4;
+    const float* stage = reinterpret_cast<const float*>(bufs);
+    constexpr int R4 = RT / 4;
     for (int q = threadIdx.x; q < 2 * R4 * N; q += blockDim.x) {
         const int r4 = q % R4, rest = q / R4;
         const int y = rest % N, fld = rest / N;
-        const float* s = stage + (size_t)(fld * RT + 4 * r4) * lds + y;
+        // line of row 4 r4 + i and field fld is buffer 2 (4 r4 + i) + fld
+        const float* s = stage + (size_t)(8 * r4 + fld) * LDS + y;
         *reinterpret_cast<float4*>(out + fld * NN + (size_t)y * N + kx0 + 4 * r4) =
-            make_float4(s[0], s[lds], s[2 * lds], s[3 * lds]);
+            make_float4(s[0], s[2 * LDS], s[4 * LDS], s[6 * LDS]);
     }
 }
 
 // ------------------------------------------------------------------ kw_irow
-// RI rows per CTA, two lines (phi, psi) per row.
+// SLOTS/2 rows per CTA, two lines (phi, psi) per row.  Phase 1 (all
+// threads): pre-process the transposed rows into the line buffers; phase 2
+// (per line): inverse four-step FFT, then u^{n+1} = u_bar + du with the
+// compensated (and, for psi on the FP32 path, dithered and mass-anchored)
+// final rounding.
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32)
-kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __restrict__ psi_new, int RI,
+kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __restrict__ psi_new,
         const cplx<float>* __restrict__ tw2, const PostTw<float>* __restrict__ twP,
         const float* __restrict__ phn, const float* __restrict__ pho,
         const float* __restrict__ psn, const float* __restrict__ pso, int bdf1,
-        const DevScalars* __restrict__ dsc, int anchor_mass, uint32_t step) {
+        const DevScalars* __restrict__ dsc, int anchor_mass) {
     using Gm = WGeo<M>;
-    constexpr int N = 2 * M, G = Gm::G, E = Gm::E;
+    constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RI = Gm::SLOTS / 2, NU = (M / 2 + G - 1) / G;
+    const uint32_t step = (uint32_t)dsc->steps;         // dither key (graph replays read it here)
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
     const int y0 = blockIdx.x * RI;
+    const float inv0 = 1.0f / (M * sqrtf(1.0f / N)), inv = 1.0f / (M * sqrtf(2.0f / N));
+    constexpr int PAIRS = M / 2 + 1;
+#pragma unroll 4
+    for (int q = threadIdx.x; q < 2 * RI * PAIRS; q += blockDim.x) {
+        const int l = q / PAIRS, k = q % PAIRS;
+        const int r = l >> 1, fld = l & 1;
+        const float* row = in + fld * NN + (size_t)(y0 + r) * N;
+        const Quad<float> X{__ldg(row + k), k > 0 ? __ldg(row + N - k) : 0.f, __ldg(row + M - k), __ldg(row + M + k)};
+        cplx<float> zk, zMk;
+        pre_inverse(X, k, twP[k], inv0, inv, zk, zMk);
+        cplx<float>* b = bufs + (size_t)l * Gm::BUF;
+        b[k] = zk;
+        if (k > 0) b[M - k] = zMk;
+    }
+    __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / G, n2 = lane % G;
     const int slot = warp * Gm::LPW + grp;
+    const int r = slot >> 1, fld = slot & 1;
     cplx<float>* buf = bufs + (size_t)slot * Gm::BUF;
-    const float inv0 = 1.0f / (M * sqrtf(1.0f / N)), inv = 1.0f / (M * sqrtf(2.0f / N));
-    const double anc_d = anchor_mass ? dsc->anchor - sqrt((double)N) * dsc->dc_col / ((double)N * N) : 0.0;
-    const int nlines = 2 * RI;
-    for (int l0 = 0; l0 < nlines; l0 += Gm::SLOTS) {
-        const int l = l0 + slot;
-        const bool act = l < nlines;
-        const int r = (act ? l : 0) >> 1, fld = (act ? l : 0) & 1;
-        const float* row = in + fld * NN + (size_t)(y0 + r) * N;
-        const float x0 = row[0];                  // the line's DC coefficient
-        for (int k = n2; k <= M / 2; k += G) {
-            const Quad<float> X{row[k], k > 0 ? row[N - k] : 0.f, row[M - k], row[M + k]};
-            cplx<float> zk, zMk;
-            pre_inverse(X, k, twP[k], inv0, inv, zk, zMk);
-            buf[k] = zk;
-            if (k > 0) buf[M - k] = zMk;
-        }
-        __syncwarp();
+    {
         cplx<float> v[E];
 #pragma unroll
         for (int n1 = 0; n1 < E; ++n1) v[n1] = buf[G * n1 + n2];
         __syncwarp();
         wf::fourstep<float, M, true>(v, buf, tw2, n2);
-        // FP32 path, psi: the row's increments should sum to sqrt(N) x0; the
-        // residual of the FP32 transform is removed (with the anchor) in the
-        // compensated final rounding, so the stored mass stays conserved
-        float rhi = 0.f, rlo = 0.f;
-        if (anchor_mass && fld == 1)
-            for (int m = n2; m < M / 2; m += G) {
-                const cplx<float> a = buf[m], b = buf[M - 1 - m];
-                df_add(rhi, rlo, a.x); df_add(rhi, rlo, b.y); df_add(rhi, rlo, a.y); df_add(rhi, rlo, b.x);
-            }
-        const double rsum = group_sum_exact<G>(rhi, rlo);
-        if (act) {
-            const size_t roff = (size_t)(y0 + r) * N;
-            float* dst = (fld == 0 ? phi_new : psi_new) + roff;
-            const float4* un = reinterpret_cast<const float4*>((fld == 0 ? phn : psn) + roff);
-            const float4* uo = reinterpret_cast<const float4*>((fld == 0 ? pho : pso) + roff);
-            const float an = (fld == 1 && anchor_mass)
-                                 ? (float)(anc_d + (sqrt((double)N) * (double)x0 - rsum) / (double)N) : 0.f;
-            const bool b1 = bdf1 != 0;
-            const bool dth = (fld == 1) && anchor_mass;
-            for (int m = n2; m < M / 2; m += G) {
-                const cplx<float> a = buf[m], b = buf[M - 1 - m];
-                const float4 p = __ldg(un + m), q = __ldg(uo + m);
-                const uint32_t i0 = (uint32_t)(roff + 4 * m);
-                float4 o;
-                o.x = bar_add(p.x, q.x, a.x, an, b1, dth ? dither_key(step, i0) | 1u : 0u);
-                o.y = bar_add(p.y, q.y, b.y, an, b1, dth ? dither_key(step, i0 + 1) | 1u : 0u);
-                o.z = bar_add(p.z, q.z, a.y, an, b1, dth ? dither_key(step, i0 + 2) | 1u : 0u);
-                o.w = bar_add(p.w, q.w, b.x, an, b1, dth ? dither_key(step, i0 + 3) | 1u : 0u);
-                *reinterpret_cast<float4*>(dst + 4 * m) = o;
-            }
+    }
+    const size_t roff = (size_t)(y0 + r) * N;
+    // FP32 path, psi: the row's increments should sum to sqrt(N) x0 (x0 the
+    // row's DC coefficient); the residual of the FP32 transform and the
+    // column residual dc_col are removed, with the mean anchor, in the final
+    // rounding, so the stored mass stays conserved
+    const bool psi_line = fld == 1 && anchor_mass;
+    float rhi = 0.f, rlo = 0.f;
+    if (psi_line)
+#pragma unroll
+        for (int i = 0; i < NU; ++i) {
+            const int m = n2 + G * i;
+            const cplx<float> a = buf[m], b = buf[M - 1 - m];
+            df_add(rhi, rlo, a.x); df_add(rhi, rlo, b.y); df_add(rhi, rlo, a.y); df_add(rhi, rlo, b.x);
         }
-        __syncwarp();
+    const double rsum = group_sum_exact<G>(rhi, rlo);
+    float an = 0.f;
+    if (psi_line) {
+        const double x0 = (double)__ldg(in + fld * NN + roff);
+        const double sN = sqrt((double)N);
+        an = (float)(dsc->anchor - sN * dsc->dc_col / ((double)N * N) + (sN * x0 - rsum) / (double)N);
+    }
+    float* dst = (fld == 0 ? phi_new : psi_new) + roff;
+    const float4* un = reinterpret_cast<const float4*>((fld == 0 ? phn : psn) + roff);
+    const float4* uo = reinterpret_cast<const float4*>((fld == 0 ? pho : pso) + roff);
+    const bool b1 = bdf1 != 0;
+#pragma unroll
+    for (int i = 0; i < NU; ++i) {
+        const int m = n2 + G * i;
+        const cplx<float> a = buf[m], b = buf[M - 1 - m];
+        const float4 p = __ldg(un + m), q = __ldg(uo + m);
+        const uint32_t i0 = (uint32_t)(roff + 4 * m);
+        float4 o;
+        o.x = bar_add(p.x, q.x, a.x, an, b1, psi_line ? dither_key(step, i0) | 1u : 0u);
+        o.y = bar_add(p.y, q.y, b.y, an, b1, psi_line ? dither_key(step, i0 + 1) | 1u : 0u);
+        o.z = bar_add(p.z, q.z, a.y, an, b1, psi_line ? dither_key(step, i0 + 2) | 1u : 0u);
+        o.w = bar_add(p.w, q.w, b.x, an, b1, psi_line ? dither_key(step, i0 + 3) | 1u : 0u);
+        *reinterpret_cast<float4*>(dst + 4 * m) = o;
     }
 }
 
