@@ -50,6 +50,7 @@ public:
     double* part1 = nullptr;
     double* part2 = nullptr;
     double* partd = nullptr;
+    double* part3 = nullptr;         // k_solve slices (kSolveBlocks x NRQ)
     cplx<T>* twM = nullptr;
     PostTw<T>* twP = nullptr;
     double* ev = nullptr;
@@ -156,12 +157,12 @@ public:
 
     void release() {
         for (int i = 0; i < 3; ++i) { cudaFree(phi[i]); cudaFree(psi[i]); phi[i] = psi[i] = nullptr; }
-        cudaFree(bufA); cudaFree(bufB); cudaFree(part1); cudaFree(part2); cudaFree(partd);
+        cudaFree(bufA); cudaFree(bufB); cudaFree(part1); cudaFree(part2); cudaFree(partd); cudaFree(part3);
         cudaFree(twM); cudaFree(twP); cudaFree(ev); cudaFree(sc); cudaFree(tmp64);
         cudaFree(tw2); cudaFree(evf); tw2 = nullptr; evf = nullptr;
         if (sc_host) cudaFreeHost(sc_host);
         if (h_part) cudaFreeHost(h_part);
-        bufA = bufB = nullptr; part1 = part2 = partd = nullptr; twM = nullptr; twP = nullptr;
+        bufA = bufB = nullptr; part1 = part2 = partd = part3 = nullptr; twM = nullptr; twP = nullptr;
         ev = nullptr; sc = nullptr; tmp64 = nullptr; sc_host = nullptr; h_part = nullptr;
     }
 
@@ -173,6 +174,10 @@ public:
         if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 1;
         const int lim = optin - (int)fa.sharedSizeBytes;
         if ((size_t)lim < needed) return 1;
+        // the whole unified L1 as shared memory: otherwise the driver may pick a
+        // smaller carveout and fit fewer CTAs of these large-tile kernels per SM
+        if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) return 1;
         return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess;
     }
 
@@ -202,6 +207,7 @@ public:
         if (cudaMalloc(&part1, (size_t)nb1 * NRED1 * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
         if (cudaMalloc(&part2, (size_t)N * NRED2 * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
         if (cudaMalloc(&partd, (size_t)nbd * NDIAG * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaMalloc(&part3, (size_t)kSolveBlocks * NRQ * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
         if (cudaMalloc(&tmp64, 2 * NN * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
         if (cudaMalloc(&sc, sizeof(DevScalars)) != cudaSuccess) return CCMSAV_ENOMEM;
         if (cudaHostAlloc(&sc_host, sizeof(DevScalars), cudaHostAllocDefault) != cudaSuccess) return CCMSAV_ENOMEM;
@@ -482,7 +488,7 @@ public:
         so.cgo = p.M_phi;
         so.bdf1 = bdf1 ? 1 : 0;
         so.nb1 = nb1; so.nb2 = N;
-        so.NN = (double)NN;
+        so.inv_NN = 1.0 / (double)NN;
         const int anchor = (sizeof(T) == sizeof(float)) ? 1 : 0;
         so.anchor = anchor;
 
@@ -499,7 +505,7 @@ public:
             k_coldct_gram<T><<<N, 512, sm_col, st>>>(bufB, bufA, part2, N, FG, twM, twP, ev, s);
             mark(2);
         }
-        k_solve<<<1, 256, 0, st>>>(part1, so.nb1, part2, so.nb2, sc, so);
+        k_solve<<<kSolveBlocks, kSolveThreads, 0, st>>>(part1, so.nb1, part2, so.nb2, part3, sc, so);
         mark(3);
         if (warp_path) {
             bdf1_launch = so.bdf1;

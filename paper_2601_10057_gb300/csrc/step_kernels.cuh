@@ -83,12 +83,12 @@ struct DevScalars {
                                   // zero-mean psi increment at kx = 0 (its DC leakage)
     double last[6];               // IV IW IZ minM and diagnostics of the last step
     int status;                   // 0 or a CCMSAV_E* code set on the device
-    int pad;
+    unsigned int solve_arrivals;  // blocks of k_solve done with their slice (reset by the last)
 };
 
 struct SolveCoef {
     double h2, cgs, cga, cgb, cgo;
-    double NN;                    // points per field
+    double inv_NN;                // 1 / points per field (exact: a power of two)
     int bdf1;
     int anchor;                   // FP32 path: compute the psi mean correction
     int nb1, nb2;                 // number of partial rows
@@ -562,45 +562,131 @@ k_coldct_gram(const T* __restrict__ in, T* __restrict__ spec, double* __restrict
 // (thread 0) the scalar algebra of Appendix B Steps 1 and 4.
 __device__ inline bool finite_(double x) { return isfinite(x); }
 
-// One block of 8 warps.  Warp w reduces columns w, w+8, ... of the partial-sum rows
-// (stencil rows: IV IW IZ sum psi^n sum psi^{n-1} . . . minM; Gram rows:
-// the 17 Gram sums) in a fixed order (four strided accumulators per lane,
-// then a shuffle tree), so the result is deterministic.  Thread 0 then does
-// the scalar algebra with every loop unrolled (registers only; a dynamic row
-// index would put the 5x5 matrix in local memory) and one reciprocal per
-// pivot: FP64 latency dominates this kernel on GB300.
-enum { NRQ = NRED1 + NRED2 };
+// kSolveBlocks blocks.  Block b adds its slice of the partial-sum rows of
+// both arrays for every column: the slice is read as one flat, coalesced
+// stream (thread t < RS*NC, RS = threads / NC, keeps column t % NC), and the
+// RS partials of a column are added by one warp in a fixed order.  FP64
+// additions run at a small fraction of the FP32 rate on GB300, so they are
+// spread over many SMs.  The block that finishes last (an atomic arrival
+// count; nothing waits) adds the slices in block order, which keeps the
+// result deterministic, and its thread 0 does the scalar algebra with every
+// loop unrolled (registers only; a dynamic row index would put the 5x5
+// matrix in local memory) and one reciprocal per pivot, reused in the back
+// substitution.
+enum { NRQ = NRED1 + NRED2, kSolveThreads = 256, kSolveBlocks = 128 };
 __device__ __forceinline__ double red_op(bool is_min, double a, double b) { return is_min ? fmin(a, b) : a + b; }
 
-static __global__ void __launch_bounds__(256)
+template <int NC>
+__device__ __forceinline__ void solve_stream_partials(const double* __restrict__ p, int nrows, int min_col,
+                                                      double* __restrict__ scratch) {
+    constexpr int RS = kSolveThreads / NC, ACT = RS * NC;
+    const int t = threadIdx.x;
+    if (t >= ACT) return;
+    const bool is_min = (t % NC) == min_col;
+    double a0 = is_min ? 1e300 : 0.0, a1 = a0;
+    const int total = nrows * NC;
+    int i = t;
+    for (; i + ACT < total; i += 2 * ACT) {
+        const double v0 = p[i], v1 = p[i + ACT];
+        a0 = red_op(is_min, a0, v0);
+        a1 = red_op(is_min, a1, v1);
+    }
+    if (i < total) a0 = red_op(is_min, a0, p[i]);
+    scratch[t] = red_op(is_min, a0, a1);
+}
+
+// rows [b * per, min(n, (b + 1) * per)) of an n-row array belong to block b
+__device__ __forceinline__ void solve_slice(int n, int b, int& r0, int& cnt) {
+    const int per = (n + kSolveBlocks - 1) / kSolveBlocks;
+    r0 = min(n, b * per);
+    cnt = min(n, r0 + per) - r0;
+}
+
+static __global__ void __launch_bounds__(kSolveThreads)
 k_solve(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, int nb2,
-        DevScalars* sc, SolveCoef co) {
-    constexpr int NR = NRQ;
+        double* __restrict__ slices, DevScalars* sc, SolveCoef co) {
+    constexpr int NR = NRQ, NW = kSolveThreads / 32, CPW = (NR + NW - 1) / NW;
+    constexpr int RS1 = kSolveThreads / NRED1, RS2 = kSolveThreads / NRED2;
+    static_assert(RS1 <= 32 && RS2 <= 32, "one partial per lane and column");
+    static_assert(kSolveBlocks % 32 == 0, "whole slices per lane");
+    __shared__ double s1[RS1 * NRED1];
+    __shared__ double s2[RS2 * NRED2];
     __shared__ double fin_[NR];
-    const int lane = threadIdx.x & 31;
-    for (int wp = threadIdx.x >> 5; wp < NR; wp += blockDim.x >> 5) {
-        const bool is_min = (wp == 8);
-        const double* base = wp < NRED1 ? p1 + wp : p2 + (wp - NRED1);
-        const int stride = wp < NRED1 ? NRED1 : NRED2;
-        const int nb = wp < NRED1 ? nb1 : nb2;
-        const double id = is_min ? 1e300 : 0.0;
-        double a0 = id, a1 = id, a2 = id, a3 = id;
-        int b = lane;
-        for (; b + 96 < nb; b += 128) {
-            a0 = red_op(is_min, a0, base[(size_t)b * stride]);
-            a1 = red_op(is_min, a1, base[(size_t)(b + 32) * stride]);
-            a2 = red_op(is_min, a2, base[(size_t)(b + 64) * stride]);
-            a3 = red_op(is_min, a3, base[(size_t)(b + 96) * stride]);
-        }
-        for (; b < nb; b += 32) a0 = red_op(is_min, a0, base[(size_t)b * stride]);
-        double v = red_op(is_min, red_op(is_min, a0, a1), red_op(is_min, a2, a3));
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) v = red_op(is_min, v, __shfl_xor_sync(0xffffffffu, v, o));
-        if (lane == 0) fin_[wp] = v;
+    __shared__ int is_last;
+    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // the scalar state, read early so that its latency overlaps the reductions
+    double V0 = 0, U0 = 0, W0 = 0, Z0 = 0, Vp = 0, Up = 0, Wp = 0, Zp = 0, mass_mode = 0, nsteps = 0;
+    int status0 = 0;
+    if (threadIdx.x == 0) {
+        V0 = sc->V; U0 = sc->U; W0 = sc->W; Z0 = sc->Z;
+        Vp = sc->Vo; Up = sc->Uo; Wp = sc->Wo; Zp = sc->Zo;
+        mass_mode = sc->mass_mode; nsteps = sc->steps; status0 = sc->status;
+    }
+    {
+        int r0, cnt;
+        solve_slice(nb1, blockIdx.x, r0, cnt);
+        solve_stream_partials<NRED1>(p1 + (size_t)r0 * NRED1, cnt, 8, s1);
+        solve_slice(nb2, blockIdx.x, r0, cnt);
+        solve_stream_partials<NRED2>(p2 + (size_t)r0 * NRED2, cnt, -1, s2);
     }
     __syncthreads();
+    // warp wp totals columns wp, wp + NW, ... together (one partial per lane,
+    // then interleaved shuffle trees); column 8 is a minimum
+    double v[CPW];
+#pragma unroll
+    for (int j = 0; j < CPW; ++j) {
+        const int c = wp + NW * j;
+        double x = (c == 8) ? 1e300 : 0.0;
+        if (c < NRED1) { if (lane < RS1) x = s1[lane * NRED1 + c]; }
+        else if (c < NR) { if (lane < RS2) x = s2[lane * NRED2 + (c - NRED1)]; }
+        v[j] = x;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) v[j] = red_op(wp + NW * j == 8, v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
+    if (lane == 0)
+#pragma unroll
+        for (int j = 0; j < CPW; ++j)
+            if (wp + NW * j < NR) slices[(size_t)blockIdx.x * NR + wp + NW * j] = v[j];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) is_last = atomicAdd(&sc->solve_arrivals, 1u) == gridDim.x - 1;
+    __syncthreads();
+    if (!is_last) return;
+    __threadfence();
+    // last block: the slices of every block in block order (all loads issued first)
+    {
+        constexpr int BPL = kSolveBlocks / 32;
+        double x[CPW][BPL];
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+            const int c = wp + NW * j;
+#pragma unroll
+            for (int q = 0; q < BPL; ++q)
+                x[j][q] = c < NR ? __ldcg(slices + (size_t)(lane + 32 * q) * NR + c) : 0.0;
+        }
+#pragma unroll
+        for (int j = 0; j < CPW; ++j) {
+            const bool mn = (wp + NW * j == 8);
+            double t = x[j][0];
+#pragma unroll
+            for (int q = 1; q < BPL; ++q) t = red_op(mn, t, x[j][q]);
+            v[j] = t;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int j = 0; j < CPW; ++j) v[j] = red_op(wp + NW * j == 8, v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
+        if (lane == 0)
+#pragma unroll
+            for (int j = 0; j < CPW; ++j)
+                if (wp + NW * j < NR) fin_[wp + NW * j] = v[j];
+    }
+    if (threadIdx.x == 0) sc->solve_arrivals = 0u;
+    __syncthreads();
     if (threadIdx.x != 0) return;
-    if (sc->status != 0) return;
+    if (status0 != 0) return;
     const double* r = fin_;
     const double IV = r[0], IW = r[1], IZ = r[2], sum_n = r[3], sum_o = r[4], minM = r[8];
     const double* Gm = r + NRED1;
@@ -614,12 +700,12 @@ k_solve(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, i
     // reference SAVs X_bar (Step 1 with the increments taken about phi_bar)
     constexpr double third = 1.0 / 3.0;
     double xb[4];
-    if (co.bdf1) { xb[0] = sc->V; xb[1] = sc->U; xb[2] = sc->W; xb[3] = sc->Z; }
+    if (co.bdf1) { xb[0] = V0; xb[1] = U0; xb[2] = W0; xb[3] = Z0; }
     else {
-        xb[0] = (4.0 * sc->V - sc->Vo) * third;
-        xb[1] = (4.0 * sc->U - sc->Uo) * third;
-        xb[2] = (4.0 * sc->W - sc->Wo) * third;
-        xb[3] = (4.0 * sc->Z - sc->Zo) * third;
+        xb[0] = (4.0 * V0 - Vp) * third;
+        xb[1] = (4.0 * U0 - Up) * third;
+        xb[2] = (4.0 * W0 - Wp) * third;
+        xb[3] = (4.0 * Z0 - Zp) * third;
     }
     const double cc[4] = {co.cgs, co.cga, co.cgb, co.cgo};
     // Gram entry (a, b) over (f0', S, H, Q, K), stored for a <= b row by row
@@ -645,15 +731,22 @@ k_solve(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, i
     A[4][3] = -PL;
     A[4][4] = 1.0 - PL;
     A[4][5] = h2 * nK * Gm[15] + xb[3] * PL;
-    // Gaussian elimination with partial pivoting (all indices compile-time)
+    // Gaussian elimination with partial pivoting (all indices compile-time);
+    // the reciprocals of all pivot candidates are formed while the pivot is
+    // searched, so the search is off the dependent chain
+    double rpiv[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
+        double rc[5];
+#pragma unroll
+        for (int i = k; i < 5; ++i) rc[i] = 1.0 / A[i][k];
         int piv = k;
-        double pmax = fabs(A[k][k]);
+        double pmax = fabs(A[k][k]), rinv = rc[k];
 #pragma unroll
         for (int i = k + 1; i < 5; ++i) {
             const bool g = fabs(A[i][k]) > pmax;
             pmax = g ? fabs(A[i][k]) : pmax;
+            rinv = g ? rc[i] : rinv;
             piv = g ? i : piv;
         }
 #pragma unroll
@@ -663,7 +756,7 @@ k_solve(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, i
             for (int j = 0; j < 6; ++j) { const double a = A[k][j], b = A[i][j]; A[k][j] = sw ? b : a; A[i][j] = sw ? a : b; }
         }
         if (!(pmax > 0)) { sc->status = -5; return; }
-        const double rinv = 1.0 / A[k][k];
+        rpiv[k] = rinv;
 #pragma unroll
         for (int i = k + 1; i < 5; ++i) {
             const double f = A[i][k] * rinv;
@@ -679,12 +772,12 @@ k_solve(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, i
         double s = A[i][5];
 #pragma unroll
         for (int j = i + 1; j < 5; ++j) s -= A[i][j] * x[j];
-        x[i] = s / A[i][i];
+        x[i] = s * rpiv[i];
     }
     const double Vn = xb[0] + x[0], Un = xb[1] + x[1], Wn = xb[2] + x[2], Zn = xb[3] + x[3] + x[4];
     bool ok2 = finite_(Vn) && finite_(Un) && finite_(Wn) && finite_(Zn);
     if (!ok2) { sc->status = -5; return; }
-    sc->Vo = sc->V; sc->Uo = sc->U; sc->Wo = sc->W; sc->Zo = sc->Z;
+    sc->Vo = V0; sc->Uo = U0; sc->Wo = W0; sc->Zo = Z0;
     sc->V = Vn; sc->U = Un; sc->W = Wn; sc->Z = Zn;
     sc->alpha[0] = co.cgs * Vn * nS;
     sc->alpha[1] = co.cga * Un;
@@ -694,14 +787,14 @@ k_solve(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, i
     // FP32 path: psi^{n+1} = psi_bar + d_psi + anchor keeps the stored mean at
     // the conserved value (means of the stored levels summed to ~1e-13)
     if (co.anchor) {
-        const double mn = sum_n / co.NN, mo = sum_o / co.NN;
+        const double mn = sum_n * co.inv_NN, mo = sum_o * co.inv_NN;
         const double mbar = co.bdf1 ? mn : mn + (mn - mo) * third;
-        sc->anchor = sc->mass_mode - mbar;
+        sc->anchor = mass_mode - mbar;
     } else {
         sc->anchor = 0.0;
     }
     sc->last[0] = IV; sc->last[1] = IW; sc->last[2] = IZ; sc->last[3] = minM;
-    sc->steps += 1.0;
+    sc->steps = nsteps + 1.0;
 }
 
 // ------------------------------------------------------------------ k_comb_icolT

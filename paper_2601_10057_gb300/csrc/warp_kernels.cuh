@@ -89,7 +89,7 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
 
 // ------------------------------------------------------------------ kw_coldct_gram
 template <int M>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, 3)
 kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* __restrict__ part,
                const cplx<float>* __restrict__ tw2, const PostTw<float>* __restrict__ twP,
                const float* __restrict__ evf, SpecCoefF sc) {
@@ -168,35 +168,41 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
     const float aS = (float)dsc->alpha[0], aH = (float)dsc->alpha[1], aQ = (float)dsc->alpha[2];
     const float aK = (float)dsc->alpha[3], aL = (float)dsc->alpha[4];
     constexpr int PAIRS = M / 2 + 1;
+    // one item = one spectral row and one pair index k: the four modes
+    // k, N-k, M-k, M+k of both lines (d_phi^ from five spectra, d_psi^ from
+    // two), all 28 loads independent of each other
 #pragma unroll 2
-    for (int q = threadIdx.x; q < 2 * RT * PAIRS; q += blockDim.x) {
-        const int l = q / PAIRS, k = q % PAIRS;
-        const int r = l >> 1, fld = l & 1;
+    for (int q = threadIdx.x; q < RT * PAIRS; q += blockDim.x) {
+        const int r = q / PAIRS, k = q % PAIRS;
         const int kx = kx0 + r;
         const float evx = evf[kx];
         const int kys[4] = {k, N - k, M - k, M + k};
-        float vals[4];
+        float vp[4], vq[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-            if (u == 1 && k == 0) { vals[u] = 0.f; continue; }
-            const int ky = kys[u];
-            const float s = evx + evf[ky];
+            const int ky = (u == 1 && k == 0) ? 0 : kys[u];
             const size_t o = (size_t)kx * N + ky;
-            if (fld == 0) {
-                const float isig = 1.0f / (sc.C1 + s * (sc.C2 + sc.C3 * s));
-                vals[u] = (__ldg(spec + o) - aS * __ldg(spec + NN + o) - aH * __ldg(spec + 2 * NN + o)
-                           - aQ * __ldg(spec + 3 * NN + o) - aK * __ldg(spec + 4 * NN + o)) * isig;
-            } else {
-                const float itau = 1.0f / (sc.Ct + sc.lam * s);
-                vals[u] = (__ldg(spec + 6 * NN + o) + aL * __ldg(spec + 7 * NN + o)) * itau;
-                // d_psi has zero mean (mass conservation); the FP32 path sets the
-                // zero mode exactly and keeps the stored mean with the anchor
-                if (anchor_mass && kx == 0 && ky == 0) vals[u] = 0.f;
-            }
+            const float s0 = __ldg(spec + o), s1 = __ldg(spec + NN + o), s2 = __ldg(spec + 2 * NN + o);
+            const float s3 = __ldg(spec + 3 * NN + o), s4 = __ldg(spec + 4 * NN + o);
+            const float s6 = __ldg(spec + 6 * NN + o), s7 = __ldg(spec + 7 * NN + o);
+            const float s = evx + evf[ky];
+            const float isig = 1.0f / (sc.C1 + s * (sc.C2 + sc.C3 * s));
+            const float itau = 1.0f / (sc.Ct + sc.lam * s);
+            vp[u] = (s0 - aS * s1 - aH * s2 - aQ * s3 - aK * s4) * isig;
+            vq[u] = (s6 + aL * s7) * itau;
         }
+        if (k == 0) { vp[1] = 0.f; vq[1] = 0.f; }
+        // d_psi has zero mean (mass conservation); the FP32 path sets the
+        // zero mode exactly and keeps the stored mean with the anchor
+        if (anchor_mass && kx == 0 && k == 0) vq[0] = 0.f;
+        const PostTw<float> tw = twP[k];
         cplx<float> zk, zMk;
-        pre_inverse(Quad<float>{vals[0], vals[1], vals[2], vals[3]}, k, twP[k], inv0, inv, zk, zMk);
-        cplx<float>* b = bufs + (size_t)l * Gm::BUF;
+        cplx<float>* b = bufs + (size_t)(2 * r) * Gm::BUF;
+        pre_inverse(Quad<float>{vp[0], vp[1], vp[2], vp[3]}, k, tw, inv0, inv, zk, zMk);
+        b[k] = zk;
+        if (k > 0) b[M - k] = zMk;
+        b += Gm::BUF;
+        pre_inverse(Quad<float>{vq[0], vq[1], vq[2], vq[3]}, k, tw, inv0, inv, zk, zMk);
         b[k] = zk;
         if (k > 0) b[M - k] = zMk;
     }
