@@ -244,6 +244,24 @@ __device__ __forceinline__ float bar_add(float a, float b, float du, float anc, 
     const float r = (e1 + e2) + anc;
     return dither ? dither_round(s, r, dither) : s + r;
 }
+// The same sum rounded to nearest with error feedback: carry (the exact
+// rounding error of this thread's earlier values, value minus stored) is
+// added before rounding and replaced by the new error (TwoSum), so the
+// stored values of one thread sum to the exact values within half an ulp.
+__device__ __forceinline__ float bar_add_fb(float a, float b, float du, float anc, bool bdf1, float& carry) {
+    float t1 = a, e1 = 0.f;
+    if (!bdf1) {
+        const float d = a - b;
+        t1 = fmaf(d, 1.0f / 3.0f, a);
+        e1 = fmaf(d, 1.0f / 3.0f, a - t1);
+    }
+    float s, e2;
+    two_sum(t1, du, s, e2);
+    const float r = ((e1 + e2) + anc) + carry;
+    float out;
+    two_sum(s, r, out, carry);
+    return out;
+}
 __device__ __forceinline__ double bar_add(double a, double b, double du, double anc, bool bdf1, uint32_t = 0) {
     return (bdf1 ? a : a + (a - b) / 3.0) + du + anc;
 }

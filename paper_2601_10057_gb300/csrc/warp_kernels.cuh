@@ -320,19 +320,35 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
     const float4* un = reinterpret_cast<const float4*>((fld == 0 ? phn : psn) + roff);
     const float4* uo = reinterpret_cast<const float4*>((fld == 0 ? pho : pso) + roff);
     const bool b1 = bdf1 != 0;
+    // psi on the FP32 path: rounding with error feedback along each lane's
+    // values, then the lanes' remaining errors (summed exactly over the row)
+    // are folded into the row's first value with one dithered rounding, so
+    // the stored row sums to its exact value within about one ulp.  Every
+    // lane takes part in the group sum (the carry stays 0 on other lines).
+    float carry = 0.f;
+    float first = 0.f;
 #pragma unroll
     for (int i = 0; i < NU; ++i) {
         const int m = n2 + G * i;
         const cplx<float> a = buf[m], b = buf[M - 1 - m];
         const float4 p = __ldg(un + m), q = __ldg(uo + m);
-        const uint32_t i0 = (uint32_t)(roff + 4 * m);
         float4 o;
-        o.x = bar_add(p.x, q.x, a.x, an, b1, psi_line ? dither_key(step, i0) | 1u : 0u);
-        o.y = bar_add(p.y, q.y, b.y, an, b1, psi_line ? dither_key(step, i0 + 1) | 1u : 0u);
-        o.z = bar_add(p.z, q.z, a.y, an, b1, psi_line ? dither_key(step, i0 + 2) | 1u : 0u);
-        o.w = bar_add(p.w, q.w, b.x, an, b1, psi_line ? dither_key(step, i0 + 3) | 1u : 0u);
+        if (psi_line) {
+            o.x = bar_add_fb(p.x, q.x, a.x, an, b1, carry);
+            o.y = bar_add_fb(p.y, q.y, b.y, an, b1, carry);
+            o.z = bar_add_fb(p.z, q.z, a.y, an, b1, carry);
+            o.w = bar_add_fb(p.w, q.w, b.x, an, b1, carry);
+        } else {
+            o.x = bar_add(p.x, q.x, a.x, 0.f, b1);
+            o.y = bar_add(p.y, q.y, b.y, 0.f, b1);
+            o.z = bar_add(p.z, q.z, a.y, 0.f, b1);
+            o.w = bar_add(p.w, q.w, b.x, 0.f, b1);
+        }
+        if (i == 0) first = o.x;
         *reinterpret_cast<float4*>(dst + 4 * m) = o;
     }
+    const double rest = group_sum_exact<G>(carry, 0.f);
+    if (psi_line && n2 == 0) dst[0] = dither_round(first, (float)rest, dither_key(step, (uint32_t)roff) | 1u);
 }
 
 }  // namespace ccm
