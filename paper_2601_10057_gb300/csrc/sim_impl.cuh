@@ -166,7 +166,9 @@ public:
         ev = nullptr; sc = nullptr; tmp64 = nullptr; sc_host = nullptr; h_part = nullptr;
     }
 
-    static int set_smem_limit(const void* fn, size_t needed) {
+    // max_carveout: take the whole unified L1 as shared memory (kernels whose
+    // occupancy is set by their tiles; the others keep L1 for cached loads)
+    static int set_smem_limit(const void* fn, size_t needed, bool max_carveout = false) {
         int dev = 0, optin = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 1;
         if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 1;
@@ -174,10 +176,8 @@ public:
         if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 1;
         const int lim = optin - (int)fa.sharedSizeBytes;
         if ((size_t)lim < needed) return 1;
-        // the whole unified L1 as shared memory: otherwise the driver may pick a
-        // smaller carveout and fit fewer CTAs of these large-tile kernels per SM
-        if (cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) return 1;
+        if (max_carveout && cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) return 1;
         return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess;
     }
 
@@ -256,7 +256,7 @@ public:
         // opt in to the largest dynamic shared memory each kernel can take (the
         // per-block opt-in limit minus the kernel's static shared memory); the
         // attribute is per kernel, so it must not depend on this simulation's N
-        if (set_smem_limit((const void*)k_stencil<T>, stencil_smem_bytes<T>())) return CCMSAV_ECUDA;
+        if (set_smem_limit((const void*)k_stencil<T>, stencil_smem_bytes<T>(), true)) return CCMSAV_ECUDA;
         if (set_smem_limit((const void*)k_rowdct_T<T>, sm_rt) || set_smem_limit((const void*)k_coldct_gram<T>, sm_col) ||
             set_smem_limit((const void*)k_comb_icolT<T>, sm_comb) || set_smem_limit((const void*)k_irow<T>, sm_irow))
             return CCMSAV_ECUDA;
@@ -286,7 +286,7 @@ public:
         wKC = Gm::SLOTS / NF; wsm_col = bb;
         wRT4 = Gm::SLOTS / 2; wsm_comb = bb;
         wRI = Gm::SLOTS / 2; wsm_irow = bb;
-        if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col) ||
+        if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col, true) ||
             set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
             return CCMSAV_ECUDA;
         return CCMSAV_OK;

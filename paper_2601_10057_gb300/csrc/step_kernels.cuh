@@ -580,37 +580,30 @@ k_coldct_gram(const T* __restrict__ in, T* __restrict__ spec, double* __restrict
 // (thread 0) the scalar algebra of Appendix B Steps 1 and 4.
 __device__ inline bool finite_(double x) { return isfinite(x); }
 
-// kSolveBlocks blocks.  Block b adds its slice of the partial-sum rows of
-// both arrays for every column: the slice is read as one flat, coalesced
-// stream (thread t < RS*NC, RS = threads / NC, keeps column t % NC), and the
-// RS partials of a column are added by one warp in a fixed order.  FP64
-// additions run at a small fraction of the FP32 rate on GB300, so they are
-// spread over many SMs.  The block that finishes last (an atomic arrival
-// count; nothing waits) adds the slices in block order, which keeps the
-// result deterministic, and its thread 0 does the scalar algebra with every
-// loop unrolled (registers only; a dynamic row index would put the 5x5
-// matrix in local memory) and one reciprocal per pivot, reused in the back
-// substitution.
-enum { NRQ = NRED1 + NRED2, kSolveThreads = 256, kSolveBlocks = 128 };
-__device__ __forceinline__ double red_op(bool is_min, double a, double b) { return is_min ? fmin(a, b) : a + b; }
+// kSolveBlocks blocks of kSolveThreads.  FP64 instructions issue at a small
+// fraction of the FP32 rate on GB300 (about one warp instruction per 64-80
+// cycles per SM sub-partition, dependent or not), so this kernel is laid out
+// to execute few of them:
+//  - the per-column sums run with one column per lane: block b adds its
+//    slice of the partial rows; the block that finishes last (an atomic
+//    arrival count; nothing waits) adds the slices, split over its warps;
+//  - the minimum column (minimum face mobility) is reduced through
+//    order-preserving integer keys;
+//  - one warp solves the 5x5 system of Appendix B Step 4 holding one entry
+//    of the augmented matrix per lane (Gauss-Jordan elimination with partial
+//    pivoting, pivots compared as integer magnitudes).
+// Every sum runs in a fixed order, so the result is deterministic.
+enum { NRQ = NRED1 + NRED2, kSolveThreads = 128, kSolveBlocks = 128, kSolveMinCol = 8 };
+static_assert(NRQ <= 32, "one column per lane");
+static_assert(kSolveBlocks == 32 * (kSolveThreads / 32), "32 slices per warp in the last block");
 
-template <int NC>
-__device__ __forceinline__ void solve_stream_partials(const double* __restrict__ p, int nrows, int min_col,
-                                                      double* __restrict__ scratch) {
-    constexpr int RS = kSolveThreads / NC, ACT = RS * NC;
-    const int t = threadIdx.x;
-    if (t >= ACT) return;
-    const bool is_min = (t % NC) == min_col;
-    double a0 = is_min ? 1e300 : 0.0, a1 = a0;
-    const int total = nrows * NC;
-    int i = t;
-    for (; i + ACT < total; i += 2 * ACT) {
-        const double v0 = p[i], v1 = p[i + ACT];
-        a0 = red_op(is_min, a0, v0);
-        a1 = red_op(is_min, a1, v1);
-    }
-    if (i < total) a0 = red_op(is_min, a0, p[i]);
-    scratch[t] = red_op(is_min, a0, a1);
+// total order of doubles as signed 64-bit integers
+__device__ __forceinline__ long long order_key(double x) {
+    const long long b = __double_as_longlong(x);
+    return b >= 0 ? b : b ^ 0x7fffffffffffffffLL;
+}
+__device__ __forceinline__ double from_order_key(long long k) {
+    return __longlong_as_double(k >= 0 ? k : k ^ 0x7fffffffffffffffLL);
 }
 
 // rows [b * per, min(n, (b + 1) * per)) of an n-row array belong to block b
@@ -623,175 +616,153 @@ __device__ __forceinline__ void solve_slice(int n, int b, int& r0, int& cnt) {
 static __global__ void __launch_bounds__(kSolveThreads)
 k_solve(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, int nb2,
         double* __restrict__ slices, DevScalars* sc, SolveCoef co) {
-    constexpr int NR = NRQ, NW = kSolveThreads / 32, CPW = (NR + NW - 1) / NW;
-    constexpr int RS1 = kSolveThreads / NRED1, RS2 = kSolveThreads / NRED2;
-    static_assert(RS1 <= 32 && RS2 <= 32, "one partial per lane and column");
-    static_assert(kSolveBlocks % 32 == 0, "whole slices per lane");
-    __shared__ double s1[RS1 * NRED1];
-    __shared__ double s2[RS2 * NRED2];
+    constexpr int NR = NRQ;
+    constexpr unsigned FULL = 0xffffffffu;
     __shared__ double fin_[NR];
-    __shared__ int is_last;
-    const int wp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    // the scalar state, read early so that its latency overlaps the reductions
-    double V0 = 0, U0 = 0, W0 = 0, Z0 = 0, Vp = 0, Up = 0, Wp = 0, Zp = 0, mass_mode = 0, nsteps = 0;
-    int status0 = 0;
-    if (threadIdx.x == 0) {
-        V0 = sc->V; U0 = sc->U; W0 = sc->W; Z0 = sc->Z;
-        Vp = sc->Vo; Up = sc->Uo; Wp = sc->Wo; Zp = sc->Zo;
-        mass_mode = sc->mass_mode; nsteps = sc->steps; status0 = sc->status;
+    __shared__ double part[kSolveThreads / 32][NR];
+    __shared__ double s_state[10];       // V U W Z at n and n-1, conserved mean, steps
+    __shared__ int s_status, is_last;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 32) {             // the scalar state, read while warp 0 streams
+        s_state[0] = sc->V; s_state[1] = sc->U; s_state[2] = sc->W; s_state[3] = sc->Z;
+        s_state[4] = sc->Vo; s_state[5] = sc->Uo; s_state[6] = sc->Wo; s_state[7] = sc->Zo;
+        s_state[8] = sc->mass_mode; s_state[9] = sc->steps; s_status = sc->status;
     }
-    {
+    // this block's slice: lane c of warp 0 adds column c
+    if (warp == 0 && lane < NR) {
+        const int c = lane;
+        const bool in1 = c < NRED1;
+        const double* col = in1 ? p1 + c : p2 + (c - NRED1);
+        const int stride = in1 ? NRED1 : NRED2;
         int r0, cnt;
-        solve_slice(nb1, blockIdx.x, r0, cnt);
-        solve_stream_partials<NRED1>(p1 + (size_t)r0 * NRED1, cnt, 8, s1);
-        solve_slice(nb2, blockIdx.x, r0, cnt);
-        solve_stream_partials<NRED2>(p2 + (size_t)r0 * NRED2, cnt, -1, s2);
+        solve_slice(in1 ? nb1 : nb2, blockIdx.x, r0, cnt);
+        double acc = 0.0;
+        long long kmin = 0x7fffffffffffffffLL;
+        for (int r = 0; r < cnt; r += 8) {
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) v[u] = (r + u < cnt) ? col[(size_t)(r0 + r + u) * stride] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (r + u >= cnt) break;
+                if (c == kSolveMinCol) kmin = min(kmin, order_key(v[u]));
+                else acc += v[u];
+            }
+        }
+        slices[(size_t)blockIdx.x * NR + c] = (c == kSolveMinCol) ? __longlong_as_double(kmin) : acc;
     }
-    __syncthreads();
-    // warp wp totals columns wp, wp + NW, ... together (one partial per lane,
-    // then interleaved shuffle trees); column 8 is a minimum
-    double v[CPW];
-#pragma unroll
-    for (int j = 0; j < CPW; ++j) {
-        const int c = wp + NW * j;
-        double x = (c == 8) ? 1e300 : 0.0;
-        if (c < NRED1) { if (lane < RS1) x = s1[lane * NRED1 + c]; }
-        else if (c < NR) { if (lane < RS2) x = s2[lane * NRED2 + (c - NRED1)]; }
-        v[j] = x;
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int j = 0; j < CPW; ++j) v[j] = red_op(wp + NW * j == 8, v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
-    if (lane == 0)
-#pragma unroll
-        for (int j = 0; j < CPW; ++j)
-            if (wp + NW * j < NR) slices[(size_t)blockIdx.x * NR + wp + NW * j] = v[j];
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) is_last = atomicAdd(&sc->solve_arrivals, 1u) == gridDim.x - 1;
     __syncthreads();
     if (!is_last) return;
     __threadfence();
-    // last block: the slices of every block in block order (all loads issued first)
-    {
-        constexpr int BPL = kSolveBlocks / 32;
-        double x[CPW][BPL];
+    // last block: warp w adds slices 32 w .. 32 w + 31 of every column
+    if (lane < NR) {
+        const int c = lane;
+        double v[32];
 #pragma unroll
-        for (int j = 0; j < CPW; ++j) {
-            const int c = wp + NW * j;
+        for (int q = 0; q < 32; ++q) v[q] = __ldcg(slices + (size_t)(32 * warp + q) * NR + c);
+        double acc = 0.0;
+        long long kmin = 0x7fffffffffffffffLL;
 #pragma unroll
-            for (int q = 0; q < BPL; ++q)
-                x[j][q] = c < NR ? __ldcg(slices + (size_t)(lane + 32 * q) * NR + c) : 0.0;
+        for (int q = 0; q < 32; ++q) {
+            if (c == kSolveMinCol) kmin = min(kmin, __double_as_longlong(v[q]));
+            else acc += v[q];
         }
-#pragma unroll
-        for (int j = 0; j < CPW; ++j) {
-            const bool mn = (wp + NW * j == 8);
-            double t = x[j][0];
-#pragma unroll
-            for (int q = 1; q < BPL; ++q) t = red_op(mn, t, x[j][q]);
-            v[j] = t;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-            for (int j = 0; j < CPW; ++j) v[j] = red_op(wp + NW * j == 8, v[j], __shfl_xor_sync(0xffffffffu, v[j], o));
-        if (lane == 0)
-#pragma unroll
-            for (int j = 0; j < CPW; ++j)
-                if (wp + NW * j < NR) fin_[wp + NW * j] = v[j];
+        part[warp][c] = (c == kSolveMinCol) ? __longlong_as_double(kmin) : acc;
     }
     if (threadIdx.x == 0) sc->solve_arrivals = 0u;
     __syncthreads();
-    if (threadIdx.x != 0) return;
-    if (status0 != 0) return;
-    const double* r = fin_;
-    const double IV = r[0], IW = r[1], IZ = r[2], sum_n = r[3], sum_o = r[4], minM = r[8];
-    const double* Gm = r + NRED1;
-    bool ok = true;
-    for (int i = 0; i < NR; ++i) ok = ok && finite_(r[i]);
-    ok = ok && IV > 0 && IW > 0 && IZ > 0 && minM > 0;
-    if (!ok) { sc->status = -5; return; }
-    const double h2 = co.h2;
-    const double nS = 0.5 * rsqrt(h2 * IV), nQ = rsqrt(h2 * IW), nK = rsqrt(h2 * IZ);
-    const double nrm[4] = {nS, 1.0, nQ, nK};
-    // reference SAVs X_bar (Step 1 with the increments taken about phi_bar)
-    constexpr double third = 1.0 / 3.0;
-    double xb[4];
-    if (co.bdf1) { xb[0] = V0; xb[1] = U0; xb[2] = W0; xb[3] = Z0; }
-    else {
-        xb[0] = (4.0 * V0 - Vp) * third;
-        xb[1] = (4.0 * U0 - Up) * third;
-        xb[2] = (4.0 * W0 - Wp) * third;
-        xb[3] = (4.0 * Z0 - Zp) * third;
+    if (warp != 0) return;
+    if (lane < NR) {
+        const int c = lane;
+        if (c == kSolveMinCol) {
+            long long kmin = __double_as_longlong(part[0][c]);
+#pragma unroll
+            for (int w = 1; w < kSolveThreads / 32; ++w) kmin = min(kmin, __double_as_longlong(part[w][c]));
+            fin_[c] = from_order_key(kmin);
+        } else {
+            double acc = part[0][c];
+#pragma unroll
+            for (int w = 1; w < kSolveThreads / 32; ++w) acc += part[w][c];
+            fin_[c] = acc;
+        }
     }
-    const double cc[4] = {co.cgs, co.cga, co.cgb, co.cgo};
+    __syncwarp();
+    if (s_status != 0) return;
+    const double* r = fin_;
+    const double IV = r[0], IW = r[1], IZ = r[2], sum_n = r[3], sum_o = r[4], minM = r[kSolveMinCol];
+    const double* Gm = r + NRED1;
+    const bool fin_ok = __all_sync(FULL, lane >= NR || finite_(r[lane < NR ? lane : 0]));
+    if (!(fin_ok && IV > 0 && IW > 0 && IZ > 0 && minM > 0)) {
+        if (lane == 0) sc->status = -5;
+        return;
+    }
+    const double h2 = co.h2;
+    // normalisations 1/(2 sqrt I_V), 1/sqrt I_W, 1/sqrt I_Z (lanes 0, 1, 2)
+    const double rr = rsqrt(h2 * (lane == 0 ? IV : lane == 1 ? IW : IZ));
+    const double nS = 0.5 * __shfl_sync(FULL, rr, 0), nQ = __shfl_sync(FULL, rr, 1), nK = __shfl_sync(FULL, rr, 2);
+    // reference SAVs X_bar (Step 1 with the increments taken about phi_bar), lane q < 4
+    constexpr double third = 1.0 / 3.0;
+    const int q4 = lane & 3;
+    const double x0q = s_state[q4], xpq = s_state[4 + q4];
+    const double xbq = co.bdf1 ? x0q : (4.0 * x0q - xpq) * third;
+    auto nrm_of = [&](int q) { return q == 0 ? nS : q == 1 ? 1.0 : q == 2 ? nQ : nK; };
+    auto cc_of = [&](int q) { return q == 0 ? co.cgs : q == 1 ? co.cga : q == 2 ? co.cgb : co.cgo; };
+    const double wq = cc_of(q4) * xbq * nrm_of(q4);
+    double xb[4], w[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) { xb[q] = __shfl_sync(FULL, xbq, q); w[q] = __shfl_sync(FULL, wq, q); }
     // Gram entry (a, b) over (f0', S, H, Q, K), stored for a <= b row by row
-    auto G = [&](int a, int b) -> double {
-        const int lo = a < b ? a : b, hi = a < b ? b : a;
+    auto G = [&](int ga, int gb) -> double {
+        const int lo = ga < gb ? ga : gb, hi = ga < gb ? gb : ga;
         return Gm[lo * 5 - lo * (lo - 1) / 2 + (hi - lo)];
     };
-    double A[5][6];
+    // entry (i, j) of the augmented matrix [A | b] on lane 6 i + j
+    const int l = lane < 30 ? lane : 29;
+    const int i = l / 6, j = l % 6;
+    double a;
+    if (i < 4) {
+        const double ni = nrm_of(i);
+        if (j < 5) {
+            const double nj = j < 4 ? nrm_of(j) : nK, cj = j < 4 ? cc_of(j) : co.cgo;
+            a = (i == j ? 1.0 : 0.0) + cj * (h2 * ni * nj * G(i + 1, j < 4 ? j + 1 : 4));
+        } else {
+            double bi = G(0, i + 1);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        double bi = G(0, i + 1);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const double gij = h2 * nrm[i] * nrm[j] * G(i + 1, j + 1);
-            A[i][j] = (i == j ? 1.0 : 0.0) + cc[j] * gij;
-            bi -= cc[j] * xb[j] * nrm[j] * G(i + 1, j + 1);
+            for (int q = 0; q < 4; ++q) bi -= w[q] * G(i + 1, q + 1);
+            a = h2 * ni * bi;
         }
-        A[i][4] = co.cgo * h2 * nrm[i] * nK * G(i + 1, 4);
-        A[i][5] = h2 * nrm[i] * bi;
+    } else {
+        const double PL = h2 * nK * nK * Gm[16];
+        a = j == 3 ? -PL : j == 4 ? 1.0 - PL : j == 5 ? h2 * nK * Gm[15] + xb[3] * PL : 0.0;
     }
-    const double PL = h2 * nK * nK * Gm[16];
-    A[4][0] = A[4][1] = A[4][2] = 0.0;
-    A[4][3] = -PL;
-    A[4][4] = 1.0 - PL;
-    A[4][5] = h2 * nK * Gm[15] + xb[3] * PL;
-    // Gaussian elimination with partial pivoting (all indices compile-time);
-    // the reciprocals of all pivot candidates are formed while the pivot is
-    // searched, so the search is off the dependent chain
-    double rpiv[5];
 #pragma unroll
     for (int k = 0; k < 5; ++k) {
-        double rc[5];
-#pragma unroll
-        for (int i = k; i < 5; ++i) rc[i] = 1.0 / A[i][k];
+        const unsigned long long mag = (unsigned long long)__double_as_longlong(a) & 0x7fffffffffffffffull;
+        unsigned long long best = __shfl_sync(FULL, mag, 6 * k + k);
         int piv = k;
-        double pmax = fabs(A[k][k]), rinv = rc[k];
 #pragma unroll
-        for (int i = k + 1; i < 5; ++i) {
-            const bool g = fabs(A[i][k]) > pmax;
-            pmax = g ? fabs(A[i][k]) : pmax;
-            rinv = g ? rc[i] : rinv;
-            piv = g ? i : piv;
+        for (int rr2 = k + 1; rr2 < 5; ++rr2) {
+            const unsigned long long m = __shfl_sync(FULL, mag, 6 * rr2 + k);
+            if (m > best) { best = m; piv = rr2; }
         }
-#pragma unroll
-        for (int i = k + 1; i < 5; ++i) {
-            const bool sw = (i == piv);
-#pragma unroll
-            for (int j = 0; j < 6; ++j) { const double a = A[k][j], b = A[i][j]; A[k][j] = sw ? b : a; A[i][j] = sw ? a : b; }
+        if (best == 0ull) {
+            if (lane == 0) sc->status = -5;
+            return;
         }
-        if (!(pmax > 0)) { sc->status = -5; return; }
-        rpiv[k] = rinv;
-#pragma unroll
-        for (int i = k + 1; i < 5; ++i) {
-            const double f = A[i][k] * rinv;
-            // full rows (columns < k are eliminated already and unused): a
-            // loop start depending on k would leave the matrix in local memory
-#pragma unroll
-            for (int j = 0; j < 6; ++j) A[i][j] -= f * A[k][j];
-        }
+        a = __shfl_sync(FULL, a, i == k ? 6 * piv + j : i == piv ? 6 * k + j : l);
+        const double rinv = 1.0 / __shfl_sync(FULL, a, 6 * k + k);
+        const double akj = __shfl_sync(FULL, a, 6 * k + j) * rinv;
+        const double aik = __shfl_sync(FULL, a, 6 * i + k);
+        a = (i == k) ? akj : a - aik * akj;
     }
     double x[5];
 #pragma unroll
-    for (int i = 4; i >= 0; --i) {
-        double s = A[i][5];
-#pragma unroll
-        for (int j = i + 1; j < 5; ++j) s -= A[i][j] * x[j];
-        x[i] = s * rpiv[i];
-    }
+    for (int q = 0; q < 5; ++q) x[q] = __shfl_sync(FULL, a, 6 * q + 5);
+    if (lane != 0) return;
+    const double V0 = s_state[0], U0 = s_state[1], W0 = s_state[2], Z0 = s_state[3];
     const double Vn = xb[0] + x[0], Un = xb[1] + x[1], Wn = xb[2] + x[2], Zn = xb[3] + x[3] + x[4];
     bool ok2 = finite_(Vn) && finite_(Un) && finite_(Wn) && finite_(Zn);
     if (!ok2) { sc->status = -5; return; }
@@ -807,12 +778,12 @@ k_solve(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, i
     if (co.anchor) {
         const double mn = sum_n * co.inv_NN, mo = sum_o * co.inv_NN;
         const double mbar = co.bdf1 ? mn : mn + (mn - mo) * third;
-        sc->anchor = mass_mode - mbar;
+        sc->anchor = s_state[8] - mbar;
     } else {
         sc->anchor = 0.0;
     }
     sc->last[0] = IV; sc->last[1] = IW; sc->last[2] = IZ; sc->last[3] = minM;
-    sc->steps = nsteps + 1.0;
+    sc->steps = s_state[9] + 1.0;
 }
 
 // ------------------------------------------------------------------ k_comb_icolT
