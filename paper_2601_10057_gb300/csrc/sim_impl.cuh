@@ -433,9 +433,16 @@ public:
         cur = 0; prev = 1; spare = 2;
         int r = upload_levels(phi0, psi0, phi1, psi1);
         if (r) return r;
-        double ssum = 0.0;
-        for (size_t q = 0; q < NN; ++q) ssum += psi0[q];
-        r = init_scalars_from_fields(ssum);
+        // conserved mass: compensated (Neumaier) summation, accurate to a few
+        // ulps of the sum; a plain running sum of 10^6..10^8 positive values
+        // can be off by 1e-11 relative, which the FP32 path would then conserve
+        double ssum = 0.0, scomp = 0.0;
+        for (size_t q = 0; q < NN; ++q) {
+            const double x = psi0[q], t = ssum + x;
+            scomp += std::fabs(ssum) >= std::fabs(x) ? (ssum - t) + x : (x - t) + ssum;
+            ssum = t;
+        }
+        r = init_scalars_from_fields(ssum + scomp);
         if (r) return r;
         have_state = true; poisoned = false;
         steps_taken = (phi1 && psi1) ? 1 : 0;   // two given levels: continue with BDF2
