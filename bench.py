@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the secondary workloads (batch of 64, N=4096, N=8192)")
     return ap.parse_args()
 
 
@@ -213,6 +215,51 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
+def extra_workloads(sh, stream):
+    """Batching form (64 simulations of N in {128, 256, 512} in one handle:
+    one stream each, BDF2 steps from one graph for the batch) and the larger
+    single grids (N = 4096 three vesicles, N = 8192 sixteen vesicles), FP32,
+    device-timed with events on the caller's stream after 6 warm-up steps."""
+    import torch
+    from paper_2601_10057_gb300 import ccmsav as cc
+    from paper_2601_10057_gb300 import inputs as I
+
+    def run(ws, k):
+        sim = cc.Simulation(None if len(ws) > 1 else ws[0].params, [w.N for w in ws],
+                            per_sim=[w.params for w in ws] if len(ws) > 1 else None,
+                            precision="fp32", stream=sh)
+        for j, w in enumerate(ws):
+            sim.set_state(w.phi0, w.psi0, sim=j)
+        sim.step(6)
+        sim.sync()
+        l0 = sim.launches()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.step(k)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        sim.sync()
+        secs = e0.elapsed_time(e1) / 1e3
+        pts = sum(w.N * w.N for w in ws)
+        out = {"value": pts * k / secs, "unit": "grid-point-steps/s", "ms_per_step": 1e3 * secs / k,
+               "steps": k, "points_per_step": pts, "gpu_launches": sim.launches() - l0}
+        sim.close()
+        return out
+
+    res = {}
+    for name, make, k in (("batch64_N128-512", lambda: I.batch_64(), 60),
+                          ("three_vesicles_N4096", lambda: [I.three_vesicles(N=4096)], 30),
+                          ("lattice16_N8192", lambda: [I.lattice_16(N=8192)], 12)):
+        try:
+            ws = make()
+            res[name] = run(ws, k)
+            if len(ws) > 1:
+                res[name]["sizes"] = {str(n): sum(1 for w in ws if w.N == n) for n in sorted({w.N for w in ws})}
+        except Exception as e:             # reported, not fatal: the headline line still prints
+            res[name] = {"error": str(e)}
+    return res
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -287,6 +334,10 @@ def run_ours(args, world, rank, local):
         s64.close()
         fp64 = {"value": NN * k64 / t64, "ms_per_step": 1e3 * t64 / k64, "steps": k64,
                 "speedup_fp32_over_fp64": (NN * args.steps / secs) / (NN * k64 / t64)}
+    # ---- the method's other workloads, device-timed (secondary lines)
+    extra = None
+    if not args.no_extra and rank == 0 and world == 1 and args.precision == "fp32":
+        extra = extra_workloads(sh, stream)
     # ---- end to end through the C ABI with pinned host buffers
     pin = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float64)).pin_memory().numpy()
     phi_h, psi_h = pin(w.phi0), pin(w.psi0)
@@ -339,6 +390,7 @@ def run_ours(args, world, rank, local):
                           "frac": round(value / world * STEP_PASSES_MIN_SCHEDULE * esize / 1e9 / peak, 4)},
         "kernels": kernels,
         "fp64": fp64,
+        "workloads": extra,
         "e2e": {"value": e2e_value, "unit": "grid-point-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": k_e2e,
                 "what": "set_state from pinned host FP64 arrays, per step ccmsav_step(1) + ccmsav_get_aux "

@@ -4,12 +4,23 @@
 #include <vector>
 #include "sim.h"
 
+// A handle with several simulations gives each its own stream, ordered with
+// the caller's stream by events around every call (fork: the simulations
+// wait for the caller's stream; join: the caller's stream waits for them), so
+// independent simulations run concurrently.  Their BDF2 steps run from one
+// graph per rotation phase holding three steps of every simulation as
+// parallel branches: one launch per three steps for the whole batch.
 struct ccmsav {
     std::vector<ccm::SimBase*> sims;
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;        // the caller's stream
     int precision = 0;
     int flags = 0;
     long long extra_launches = 0;
+    cudaStream_t cap = nullptr;           // capture origin of the batch graphs
+    cudaEvent_t fork_ev = nullptr;
+    std::vector<cudaEvent_t> join_ev;
+    cudaGraphExec_t bexec[3] = {nullptr, nullptr, nullptr};
+    bool batch_failed = false;
 };
 
 namespace {
@@ -25,6 +36,73 @@ bool valid_params(const ccmsav_params& p) {
 }
 
 bool valid_N(int N) { return N >= 8 && N <= 8192 && (N & (N - 1)) == 0; }
+
+bool batched(const ccmsav* h) { return h->sims.size() > 1; }
+
+// the simulations' streams wait for work queued so far on `from`
+int fork_from(ccmsav* h, cudaStream_t from) {
+    if (cudaEventRecord(h->fork_ev, from) != cudaSuccess) return CCMSAV_ECUDA;
+    for (ccm::SimBase* s : h->sims)
+        if (cudaStreamWaitEvent(s->stream(), h->fork_ev, 0) != cudaSuccess) return CCMSAV_ECUDA;
+    return CCMSAV_OK;
+}
+
+// `into` waits for work queued so far on every simulation's stream
+int join_into(ccmsav* h, cudaStream_t into) {
+    for (size_t k = 0; k < h->sims.size(); ++k) {
+        if (cudaEventRecord(h->join_ev[k], h->sims[k]->stream()) != cudaSuccess) return CCMSAV_ECUDA;
+        if (cudaStreamWaitEvent(into, h->join_ev[k], 0) != cudaSuccess) return CCMSAV_ECUDA;
+    }
+    return CCMSAV_OK;
+}
+
+// every simulation takes a BDF2 step next, in the same rotation phase
+bool uniform_phase(const ccmsav* h) {
+    const int ph = h->sims[0]->phase();
+    for (ccm::SimBase* s : h->sims)
+        if (!s->batchable() || s->phase() != ph) return false;
+    return true;
+}
+
+// One graph: three steps of every simulation, each on its own stream.
+int capture_batch(ccmsav* h, int ph) {
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CCMSAV_ECUDA;
+    int r = fork_from(h, h->cap);
+    for (size_t k = 0; k < h->sims.size() && r == CCMSAV_OK; ++k) r = h->sims[k]->queue_steps_captured(3);
+    if (r == CCMSAV_OK) r = join_into(h, h->cap);
+    const cudaError_t e = cudaStreamEndCapture(h->cap, &g);
+    if (r != CCMSAV_OK || e != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); return CCMSAV_ECUDA; }
+    const cudaError_t e2 = cudaGraphInstantiate(&h->bexec[ph], g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) { h->bexec[ph] = nullptr; return CCMSAV_ECUDA; }
+    return CCMSAV_OK;
+}
+
+int step_batched(ccmsav* h, int nsteps) {
+    int r = fork_from(h, h->stream);
+    if (r) return r;
+    // start steps (BDF1) and any simulation out of phase: direct, per simulation
+    while (nsteps > 0 && !uniform_phase(h)) {
+        for (ccm::SimBase* s : h->sims)
+            if ((r = s->queue_steps(1))) return r;
+        --nsteps;
+    }
+    if (nsteps >= 3 && !h->batch_failed) {
+        if ((r = join_into(h, h->stream))) return r;
+        while (nsteps >= 3) {
+            const int ph = h->sims[0]->phase();
+            if (!h->bexec[ph] && capture_batch(h, ph) != CCMSAV_OK) { h->batch_failed = true; break; }
+            if (cudaGraphLaunch(h->bexec[ph], h->stream) != cudaSuccess) return CCMSAV_ECUDA;
+            for (ccm::SimBase* s : h->sims) s->count_steps(3);
+            nsteps -= 3;
+        }
+        if ((r = fork_from(h, h->stream))) return r;
+    }
+    for (ccm::SimBase* s : h->sims)
+        if ((r = s->queue_steps(nsteps))) return r;
+    return join_into(h, h->stream);
+}
 
 ccm::SimBase* get(ccmsav_t* h, int sim) {
     if (!h || sim < 0 || sim >= (int)h->sims.size()) return nullptr;
@@ -51,11 +129,26 @@ int ccmsav_create(ccmsav_t** out, const ccmsav_params* params, int n_sims, const
     h->stream = (cudaStream_t)stream;
     h->precision = precision;
     h->flags = flags;
+    if (n_sims > 1) {
+        if (cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess) {
+            ccmsav_destroy(h);
+            return CCMSAV_ECUDA;
+        }
+        h->join_ev.assign(n_sims, nullptr);
+        for (int s = 0; s < n_sims; ++s)
+            if (cudaEventCreateWithFlags(&h->join_ev[s], cudaEventDisableTiming) != cudaSuccess) {
+                ccmsav_destroy(h);
+                return CCMSAV_ECUDA;
+            }
+    }
     for (int s = 0; s < n_sims; ++s) {
         int err = 0;
         const ccmsav_params& p = per_sim ? per_sim[s] : *params;
-        ccm::SimBase* sim = (precision == CCMSAV_FP64) ? ccm::make_sim_f64(p, N[s], flags, h->stream, &err)
-                                                       : ccm::make_sim_f32(p, N[s], flags, h->stream, &err);
+        // several simulations: each on a stream of its own (see struct ccmsav)
+        cudaStream_t ss = n_sims > 1 ? nullptr : h->stream;
+        ccm::SimBase* sim = (precision == CCMSAV_FP64) ? ccm::make_sim_f64(p, N[s], flags, ss, &err)
+                                                       : ccm::make_sim_f32(p, N[s], flags, ss, &err);
         if (!sim) { ccmsav_destroy(h); return err ? err : CCMSAV_ENOMEM; }
         sim->N = N[s];
         h->sims.push_back(sim);
@@ -89,12 +182,8 @@ int ccmsav_step(ccmsav_t* h, int nsteps) {
         if (!s->has_state()) return CCMSAV_ESTATE;
         if (s->in_error()) return CCMSAV_ESTATE;
     }
-    for (int i = 0; i < nsteps; ++i)
-        for (ccm::SimBase* s : h->sims) {
-            int r = s->queue_steps(1);
-            if (r) return r;
-        }
-    return CCMSAV_OK;
+    if (batched(h)) return step_batched(h, nsteps);
+    return h->sims[0]->queue_steps(nsteps);
 }
 
 int ccmsav_sync(ccmsav_t* h) {
@@ -189,6 +278,10 @@ void ccmsav_destroy(ccmsav_t* h) {
     if (!h) return;
     if (h->stream) cudaStreamSynchronize(h->stream); else cudaDeviceSynchronize();
     for (ccm::SimBase* s : h->sims) delete s;
+    for (cudaGraphExec_t& g : h->bexec) if (g) cudaGraphExecDestroy(g);
+    for (cudaEvent_t e : h->join_ev) if (e) cudaEventDestroy(e);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->cap) cudaStreamDestroy(h->cap);
     delete h;
 }
 

@@ -25,6 +25,13 @@ public:
     virtual long long launches() const = 0;
     virtual int profile(bool enable) = 0;
     virtual int profile_read(double ms[8], long long* nsteps) = 0;
+    // batched stepping of several simulations (one graph for all of them)
+    virtual cudaStream_t stream() const = 0;
+    virtual int phase() const = 0;                 // rotation phase of the three levels
+    virtual bool batchable() const = 0;            // next step is BDF2; no tracing, no error
+    virtual int queue_steps_captured(int n3) = 0;  // three steps as direct launches (for a
+                                                   // stream capture); host counters unchanged
+    virtual void count_steps(int n3) = 0;          // host counters after three batched steps
     int N = 0;
 };
 

@@ -96,17 +96,33 @@ public:
         if (own_stream && st) cudaStreamDestroy(st);
     }
 
-    // Captures three consecutive BDF2 steps starting at the current rotation
-    // phase (nothing executes during capture; host counters are restored).
-    int capture_phase() {
-        const int ph = cur;
+    // Three consecutive steps as direct launches on st while the stream is
+    // being captured: nothing executes, so the host counters are restored
+    // (three steps rotate the three levels back to the same phase).
+    int queue_steps_captured(int n3) override {
+        if (n3 != 3) return CCMSAV_EINVAL;
         const long long s0 = steps_taken, l0 = nlaunch;
-        cudaGraph_t g = nullptr;
-        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CCMSAV_ECUDA;
         int r = CCMSAV_OK;
         for (int i = 0; i < 3 && r == CCMSAV_OK; ++i) r = queue_one_step();
-        const cudaError_t e = cudaStreamEndCapture(st, &g);
         steps_taken = s0; nlaunch = l0;
+        return r;
+    }
+
+    long long launches_per_step() const { return 6 + ((flags & CCMSAV_TRACK_ENERGY) ? 2 : 0); }
+
+    void count_steps(int n3) override { steps_taken += n3; nlaunch += n3 * launches_per_step(); }
+    cudaStream_t stream() const override { return st; }
+    int phase() const override { return cur; }
+    bool batchable() const override { return have_state && !poisoned && steps_taken > 0 && !prof; }
+
+    // Captures three consecutive BDF2 steps starting at the current rotation
+    // phase into this simulation's graph for that phase.
+    int capture_phase() {
+        const int ph = cur;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CCMSAV_ECUDA;
+        const int r = queue_steps_captured(3);
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
         if (r != CCMSAV_OK || e != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); return CCMSAV_ECUDA; }
         const cudaError_t e2 = cudaGraphInstantiate(&gexec[ph], g, 0);
         cudaGraphDestroy(g);
@@ -550,7 +566,7 @@ public:
         }
         // BDF2 steps in groups of three from CUDA graphs (the rotation of the
         // three levels has period three, so one graph per phase)
-        const long long per_step = 6 + ((flags & CCMSAV_TRACK_ENERGY) ? 2 : 0);
+        const long long per_step = launches_per_step();
         while (nsteps >= 3 && !graphs_failed) {
             const int ph = cur;
             if (!gexec[ph] && capture_phase() != CCMSAV_OK) { graphs_failed = true; break; }

@@ -101,6 +101,34 @@ def vesicle_phi(N: int, L: float, eps: float, centre, radius_fn) -> np.ndarray:
     return np.tanh((radius_fn(th) - r) / (math.sqrt(2.0) * eps))
 
 
+def _compose(N: int, L: float, eps: float, vesicles):
+    """phi = max_k phi_k and psi = 0.8 + sum_k (inside_k - 0.8)(1 + phi_k)/2 for
+    vesicles ``(centre, radius_fn, rmax, ratio)``.  Each phi_k is evaluated
+    only where r < rmax + 20 sqrt(2) eps: beyond that the tanh argument is
+    below -20 and phi_k is exactly -1 in double precision, so the result is
+    bitwise that of evaluating every vesicle on the whole grid (same
+    elementwise operations in the same order), without a full-grid array per
+    vesicle."""
+    h = L / N
+    phi = np.full((N, N), -1.0)
+    psi = np.full((N, N), PSI_OUTSIDE)
+    for centre, radius_fn, rmax, ratio in vesicles:
+        reach = rmax + 20.0 * math.sqrt(2.0) * eps
+        i0 = max(0, int(math.floor((centre[0] - reach) / h)) - 1)
+        i1 = min(N, int(math.ceil((centre[0] + reach) / h)) + 1)
+        j0 = max(0, int(math.floor((centre[1] - reach) / h)) - 1)
+        j1 = min(N, int(math.ceil((centre[1] + reach) / h)) + 1)
+        X, Y = np.meshgrid((np.arange(i0, i1, dtype=np.float64) + 0.5) * h,
+                           (np.arange(j0, j1, dtype=np.float64) + 0.5) * h, indexing="xy")
+        dx, dy = X - centre[0], Y - centre[1]
+        pk = np.tanh((radius_fn(np.arctan2(dy, dx)) - np.hypot(dx, dy)) / (math.sqrt(2.0) * eps))
+        win = (slice(j0, j1), slice(i0, i1))
+        phi[win] = np.maximum(phi[win], pk)
+        inside = PSI_INSIDE_GROWTH if ratio >= 1.0 else PSI_INSIDE_SHRINK
+        psi[win] = psi[win] + (inside - PSI_OUTSIDE) * (1.0 + pk) / 2.0
+    return phi, psi
+
+
 PSI_OUTSIDE = 0.8          # outside value of both benchmark profiles
 PSI_INSIDE_GROWTH = 0.1    # -0.35 * 1 + 0.45
 PSI_INSIDE_SHRINK = 0.6    # -0.1 * 1 + 0.7
@@ -146,11 +174,21 @@ class Workload:
         return self.N * self.N
 
 
-def _params_for(ratios, N, L, dt, **kw) -> Params:
+def _params_for(ratios, N, L, dt, eps=None, **kw) -> Params:
     # Growth column when any vesicle grows (ratio >= 1), shrinkage otherwise.
     grows = any(r >= 1.0 for r in ratios)
     mk = growth_params if grows else shrinkage_params
-    return mk(eps=4.0 * L / N, dt=dt, L=L, **kw)
+    return mk(eps=4.0 * L / N if eps is None else eps, dt=dt, L=L, **kw)
+
+
+# Interface width of the multi-vesicle workloads: 4 cells up to N = 2048; the
+# larger grids keep the physical width of the N = 2048 interface (8 and 16
+# cells at N = 4096 and 8192).  With eps = 4 h the explicit nonlinear terms
+# stiffen like 1/eps, and the largest stable step shrinks about as h^4 (a
+# 1/16 of the step per doubling of N), so eps = 4 h at N = 4096 or 8192 is
+# unstable at the workloads' dt = 1e-5 and 5e-6.
+def _multi_vesicle_eps(N: int, L: float) -> float:
+    return 4.0 * L / min(N, 2048)
 
 
 def one_vesicle_circle(N: int = 64, seed: int = 1001, dt: float = 1e-4,
@@ -213,16 +251,15 @@ def three_vesicles(N: int = 2048, seed: int = 1003, dt: float = 1e-5,
     """Three perturbed circles, R ~ U(0.5, 1.0), centres by rejection sampling
     (gap >= 8 eps between perturbed outlines, wall margin >= R + 8 eps)."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    eps = 4.0 * L / N
+    eps = _multi_vesicle_eps(N, L)
     placed = _place(rng, 3, 0.5, 1.0, L, 8 * eps, 8 * eps)
-    phis = []
+    ves = []
     for (cx, cy, R) in placed:
         amps = rng.uniform(0.0, 0.03, 5)
         phases = rng.uniform(0.0, 2 * math.pi, 5)
-        phis.append(vesicle_phi(N, L, eps, (cx, cy), _perturbed(R, amps, phases)))
-    phi = np.maximum.reduce(phis)
-    psi = concentration(phis, [ratio] * 3)
-    p = _params_for([ratio], N, L, dt)
+        ves.append(((cx, cy), _perturbed(R, amps, phases), R * (1.0 + float(np.sum(amps))), ratio))
+    phi, psi = _compose(N, L, eps, ves)
+    p = _params_for([ratio], N, L, dt, eps=eps)
     return Workload(f"three_vesicles_N{N}", N, p, phi, psi, steps, precision)
 
 
@@ -232,9 +269,9 @@ def lattice_16(N: int = 8192, seed: int = 1005, dt: float = 5e-6,
     """16 perturbed circles, R ~ U(0.2, 0.4), on a jittered 4 x 4 lattice with
     concentration ratios alternating 0.8 / 1.25."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    eps = 4.0 * L / N
+    eps = _multi_vesicle_eps(N, L)
     cell = L / 4
-    phis, ratios = [], []
+    ves, ratios = [], []
     for k in range(16):
         gx, gy = k % 4, k // 4
         R = rng.uniform(0.2, 0.4)
@@ -243,11 +280,10 @@ def lattice_16(N: int = 8192, seed: int = 1005, dt: float = 5e-6,
         cx, cy = (gx + 0.5) * cell + jx, (gy + 0.5) * cell + jy
         amps = rng.uniform(0.0, 0.03, 5)
         phases = rng.uniform(0.0, 2 * math.pi, 5)
-        phis.append(vesicle_phi(N, L, eps, (cx, cy), _perturbed(R, amps, phases)))
         ratios.append(0.8 if k % 2 == 0 else 1.25)
-    phi = np.maximum.reduce(phis)
-    psi = concentration(phis, ratios)
-    p = _params_for(ratios, N, L, dt)
+        ves.append(((cx, cy), _perturbed(R, amps, phases), R * (1.0 + float(np.sum(amps))), ratios[-1]))
+    phi, psi = _compose(N, L, eps, ves)
+    p = _params_for(ratios, N, L, dt, eps=eps)
     return Workload(f"lattice16_N{N}", N, p, phi, psi, steps, precision)
 
 

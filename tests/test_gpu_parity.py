@@ -232,3 +232,32 @@ def test_uneven_batch_matches_single_runs():
         phi, psi = sim.state(sim=k)
         _, phi1, psi1, _ = run_gpu(w, 6)
         assert np.array_equal(phi, phi1) and np.array_equal(psi, psi1)
+
+
+@pytest.mark.parametrize("caller_stream", [False, True])
+def test_batched_graph_steps_match_single_runs(caller_stream):
+    """Several simulations in one handle step concurrently (one stream each,
+    BDF2 steps from one graph per rotation phase for the whole batch); over
+    15 steps in uneven chunks every phase's graph runs, and each simulation
+    ends bit-identical to a run of its own."""
+    torch = pytest.importorskip("torch")
+    ws = [I.workload("one_vesicle", N=32, dt=1e-5), I.workload("ellipse_shrink", N=64),
+          I.workload("one_vesicle", N=128, dt=1e-5), I.workload("ellipse_shrink", N=256)]
+    stream = torch.cuda.Stream() if caller_stream else None
+    sim = cc.Simulation(None, [w.N for w in ws], per_sim=[w.params for w in ws], precision="fp32",
+                        stream=None if stream is None else stream.cuda_stream)
+    for k, w in enumerate(ws):
+        sim.set_state(w.phi0, w.psi0, sim=k)
+    for chunk in (1, 10, 4):
+        sim.step(chunk)
+    sim.sync()
+    for k, w in enumerate(ws):
+        phi, psi = sim.state(sim=k)
+        solo = cc.Simulation(w.params, w.N, precision="fp32")
+        solo.set_state(w.phi0, w.psi0)
+        solo.step(15)
+        phi1, psi1 = solo.state()
+        solo.close()
+        assert np.array_equal(phi, phi1) and np.array_equal(psi, psi1), f"simulation {k} (N={w.N})"
+    assert all(sim.aux(sim=k)[10] == 15 for k in range(len(ws)))
+    sim.close()
