@@ -59,6 +59,7 @@ public:
     bool warp_path = false;
     cplx<float>* tw2 = nullptr;
     float* evf = nullptr;
+    float4* evp = nullptr;   // eigenvalues in the pair order of the warp-path spectra
     int wRT = 8, wlds = 0, wRT4 = 4, wlds4 = 0, wKC = 1, wRI = 4;
     size_t wsm_rt = 0, wsm_col = 0, wsm_comb = 0, wsm_irow = 0;
     DevScalars* sc_host = nullptr;   // pinned
@@ -175,7 +176,7 @@ public:
         for (int i = 0; i < 3; ++i) { cudaFree(phi[i]); cudaFree(psi[i]); phi[i] = psi[i] = nullptr; }
         cudaFree(bufA); cudaFree(bufB); cudaFree(part1); cudaFree(part2); cudaFree(partd); cudaFree(part3);
         cudaFree(twM); cudaFree(twP); cudaFree(ev); cudaFree(sc); cudaFree(tmp64);
-        cudaFree(tw2); cudaFree(evf); tw2 = nullptr; evf = nullptr;
+        cudaFree(tw2); cudaFree(evf); cudaFree(evp); tw2 = nullptr; evf = nullptr; evp = nullptr;
         if (sc_host) cudaFreeHost(sc_host);
         if (h_part) cudaFreeHost(h_part);
         bufA = bufB = nullptr; part1 = part2 = partd = part3 = nullptr; twM = nullptr; twP = nullptr;
@@ -309,11 +310,22 @@ public:
     }
 
     int init_warp_path() {
-        std::vector<float> he(N);
+        std::vector<float> he(N), hp;
         const double hh = p.L / N;
         for (int k = 0; k < N; ++k) { const double s = std::sin(M_PI * k / (2.0 * N)); he[k] = (float)(4.0 * s * s / (hh * hh)); }
         if (cudaMalloc(&evf, N * sizeof(float)) != cudaSuccess) return CCMSAV_ENOMEM;
         CCM_CUDA(cudaMemcpyAsync(evf, he.data(), N * sizeof(float), cudaMemcpyHostToDevice, st));
+        // pair k: modes k, N-k (k > 0), M-k, M+k
+        const int Mh = N / 2;
+        hp.assign(4 * (size_t)(Mh / 2 + 1), 0.f);
+        for (int k = 0; k <= Mh / 2; ++k) {
+            hp[4 * k + 0] = he[k];
+            hp[4 * k + 1] = k > 0 ? he[N - k] : 0.f;
+            hp[4 * k + 2] = he[Mh - k];
+            hp[4 * k + 3] = he[Mh + k];
+        }
+        if (cudaMalloc(&evp, hp.size() * sizeof(float)) != cudaSuccess) return CCMSAV_ENOMEM;
+        CCM_CUDA(cudaMemcpyAsync(evp, hp.data(), hp.size() * sizeof(float), cudaMemcpyHostToDevice, st));
         int r = CCMSAV_EINVAL;
         if constexpr (std::is_same<T, float>::value)
         switch (M) {
@@ -337,7 +349,7 @@ public:
         const PostTw<float>* tp = reinterpret_cast<const PostTw<float>*>(twP);
         kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, t2, tp);
         mark(1);
-        kw_coldct_gram<MM><<<N / wKC, kWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2, t2, tp, evf, sf);
+        kw_coldct_gram<MM><<<N / wKC, kWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2, t2, tp, evf, evp, sf);
         mark(2);
     }
     int bdf1_launch = 0;
@@ -346,7 +358,7 @@ public:
         SpecCoefF sf{(float)s.C1, (float)s.C2, (float)s.C3, (float)s.Ct, (float)s.lam};
         const PostTw<float>* tp = reinterpret_cast<const PostTw<float>*>(twP);
         kw_comb_icolT<MM><<<N / wRT4, kWarps * 32, wsm_comb, st>>>(reinterpret_cast<const float*>(bufA),
-            reinterpret_cast<float*>(bufB), tw2, tp, evf, sf, sc, anchor);
+            reinterpret_cast<float*>(bufB), tw2, tp, evf, evp, sf, sc, anchor);
         mark(4);
         kw_irow<MM><<<N / wRI, kWarps * 32, wsm_irow, st>>>(reinterpret_cast<const float*>(bufB),
             reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), tw2, tp,

@@ -23,6 +23,15 @@ constexpr int kWarps = 8;
 
 
 
+// Pair-ordered spectra of the warp path: row kx of a field holds, for each
+// pair k = 0 .. M/2, the float4 of modes (k, N-k, M-k, M+k); rows of
+// RS = 4 (M/2 + 1) = N + 4 floats (16-byte aligned), fields of FS = N RS
+// floats, the 7 stored fields (f0', S, H, Q, K, g0', L_P) packed.
+template <int M> struct SpecRow {
+    static constexpr int RS = 4 * (M / 2 + 1);
+    static constexpr size_t FS = (size_t)(2 * M) * RS;
+};
+
 template <int M> struct WGeo {
     static constexpr int E = wf::Shape<M>::E, G = wf::Shape<M>::G;
     static constexpr int LPW = 32 / G;                  // lines per warp
@@ -92,7 +101,7 @@ template <int M>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* __restrict__ part,
                const cplx<float>* __restrict__ tw2, const PostTw<float>* __restrict__ twP,
-               const float* __restrict__ evf, SpecCoefF sc) {
+               const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc) {
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, KC = Gm::SLOTS / NF;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -124,12 +133,12 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
             X[g] = wf::post_pair(b[k], b[(M - k) & (M - 1)], k, twP[k], cn0, cn);
         }
         const float evx = evf[kx];
-        const int kys[4] = {k, N - k, M - k, M + k};
+        const float4 e4 = evp[k];
+        const float ev_u[4] = {e4.x, e4.y, e4.z, e4.w};
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (!pair_mode_valid(u, k, M)) continue;
-            const int ky = kys[u];
-            const float s = evx + evf[ky];
+            const float s = evx + ev_u[u];
             const float isig = 1.0f / (sc.C1 + s * (sc.C2 + sc.C3 * s));
             const float itau = 1.0f / (sc.Ct + sc.lam * s);
             float v[NF];
@@ -137,10 +146,18 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
             for (int g = 0; g < NF; ++g)
                 v[g] = (u == 0) ? X[g].xk : (u == 1) ? X[g].xNk : (u == 2) ? X[g].xMk : X[g].xMpk;
             gram_accumulate(acc, v, isig, itau);
-            const size_t o = (size_t)kx * N + ky;
+        }
+        // spectra in pair order: slot u of pair k holds mode k, N-k, M-k, M+k
+        // (k = 0: no mode N, slot 3 repeats mode M; k = M/2: slots 2, 3 repeat
+        // modes M/2, 3M/2), one float4 per field
+        float* dst = spec + (size_t)kx * SpecRow<M>::RS + 4 * k;
 #pragma unroll
-            for (int g = 0; g < NF; ++g)
-                if (g != 5) spec[g * NN + o] = v[g];
+        for (int g = 0; g < NF; ++g) {
+            if (g == 5) continue;
+            float4 o = make_float4(X[g].xk, k == 0 ? 0.f : X[g].xNk, X[g].xMk, X[g].xMpk);
+            if (k == 0) o.w = o.z;
+            if (k == M / 2) { o.z = o.x; o.w = o.y; }
+            *reinterpret_cast<float4*>(dst + (size_t)(g < 5 ? g : g - 1) * SpecRow<M>::FS) = o;
         }
     }
     block_sum_store<NRED2, float>(acc, part + (size_t)blockIdx.x * NRED2, sred);
@@ -155,8 +172,8 @@ template <int M>
 __global__ void __launch_bounds__(kWarps * 32)
 kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
               const cplx<float>* __restrict__ tw2, const PostTw<float>* __restrict__ twP,
-              const float* __restrict__ evf, SpecCoefF sc, DevScalars* __restrict__ dsc,
-              int anchor_mass) {
+              const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc,
+              DevScalars* __restrict__ dsc, int anchor_mass) {
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS / 2, NU = (M / 2 + G - 1) / G;
     constexpr int LDS = 2 * Gm::BUF;
@@ -170,28 +187,33 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
     constexpr int PAIRS = M / 2 + 1;
     // one item = one spectral row and one pair index k: the four modes
     // k, N-k, M-k, M+k of both lines (d_phi^ from five spectra, d_psi^ from
-    // two), all 28 loads independent of each other
+    // two), one float4 per spectrum in the pair-ordered layout
 #pragma unroll 2
     for (int q = threadIdx.x; q < RT * PAIRS; q += blockDim.x) {
         const int r = q / PAIRS, k = q % PAIRS;
         const int kx = kx0 + r;
         const float evx = evf[kx];
-        const int kys[4] = {k, N - k, M - k, M + k};
+        const float4 e4 = evp[k];
+        const float* src = spec + (size_t)kx * SpecRow<M>::RS + 4 * k;
+        constexpr size_t FS = SpecRow<M>::FS;
+        const float4 f0 = __ldg(reinterpret_cast<const float4*>(src));
+        const float4 f1 = __ldg(reinterpret_cast<const float4*>(src + FS));
+        const float4 f2 = __ldg(reinterpret_cast<const float4*>(src + 2 * FS));
+        const float4 f3 = __ldg(reinterpret_cast<const float4*>(src + 3 * FS));
+        const float4 f4 = __ldg(reinterpret_cast<const float4*>(src + 4 * FS));
+        const float4 f6 = __ldg(reinterpret_cast<const float4*>(src + 5 * FS));
+        const float4 f7 = __ldg(reinterpret_cast<const float4*>(src + 6 * FS));
+        auto comb = [&](float a0, float a1, float a2, float a3, float a4, float a6, float a7, float ev,
+                        float& vp, float& vq) {
+            const float s = evx + ev;
+            vp = (a0 - aS * a1 - aH * a2 - aQ * a3 - aK * a4) * (1.0f / (sc.C1 + s * (sc.C2 + sc.C3 * s)));
+            vq = (a6 + aL * a7) * (1.0f / (sc.Ct + sc.lam * s));
+        };
         float vp[4], vq[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int ky = (u == 1 && k == 0) ? 0 : kys[u];
-            const size_t o = (size_t)kx * N + ky;
-            const float s0 = __ldg(spec + o), s1 = __ldg(spec + NN + o), s2 = __ldg(spec + 2 * NN + o);
-            const float s3 = __ldg(spec + 3 * NN + o), s4 = __ldg(spec + 4 * NN + o);
-            const float s6 = __ldg(spec + 6 * NN + o), s7 = __ldg(spec + 7 * NN + o);
-            const float s = evx + evf[ky];
-            const float isig = 1.0f / (sc.C1 + s * (sc.C2 + sc.C3 * s));
-            const float itau = 1.0f / (sc.Ct + sc.lam * s);
-            vp[u] = (s0 - aS * s1 - aH * s2 - aQ * s3 - aK * s4) * isig;
-            vq[u] = (s6 + aL * s7) * itau;
-        }
-        if (k == 0) { vp[1] = 0.f; vq[1] = 0.f; }
+        comb(f0.x, f1.x, f2.x, f3.x, f4.x, f6.x, f7.x, e4.x, vp[0], vq[0]);
+        comb(f0.y, f1.y, f2.y, f3.y, f4.y, f6.y, f7.y, e4.y, vp[1], vq[1]);
+        comb(f0.z, f1.z, f2.z, f3.z, f4.z, f6.z, f7.z, e4.z, vp[2], vq[2]);
+        comb(f0.w, f1.w, f2.w, f3.w, f4.w, f6.w, f7.w, e4.w, vp[3], vq[3]);
         // d_psi has zero mean (mass conservation); the FP32 path sets the
         // zero mode exactly and keeps the stored mean with the anchor
         if (anchor_mass && kx == 0 && k == 0) vq[0] = 0.f;
