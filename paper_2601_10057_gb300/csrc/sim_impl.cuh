@@ -61,6 +61,7 @@ public:
     float* evf = nullptr;
     float4* evp = nullptr;   // eigenvalues in the pair order of the warp-path spectra
     int wRT = 8, wlds = 0, wRT4 = 4, wlds4 = 0, wKC = 1, wRI = 4;
+    int ahead_rt = 0;   // L2 prefetch distance of the row kernel (its resident CTAs)
     size_t wsm_rt = 0, wsm_col = 0, wsm_comb = 0, wsm_irow = 0;
     DevScalars* sc_host = nullptr;   // pinned
     double* h_part = nullptr;        // pinned, diag partial rows
@@ -306,7 +307,17 @@ public:
         if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col, true) ||
             set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
             return CCMSAV_ECUDA;
+        ahead_rt = resident_ctas((const void*)kw_rowdct_T<MM>, kWarps * 32, wsm_rt);
         return CCMSAV_OK;
+    }
+
+    // CTAs of a kernel resident on the whole device at once (0 if unknown)
+    static int resident_ctas(const void* fn, int threads, size_t smem) {
+        int dev = 0, nsm = 0, per_sm = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, threads, smem) != cudaSuccess) return 0;
+        return nsm * per_sm;
     }
 
     int init_warp_path() {
@@ -347,7 +358,7 @@ public:
         float* fB = reinterpret_cast<float*>(bufB);
         const cplx<float>* t2 = tw2;
         const PostTw<float>* tp = reinterpret_cast<const PostTw<float>*>(twP);
-        kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, t2, tp);
+        kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, t2, tp, ahead_rt);
         mark(1);
         kw_coldct_gram<MM><<<N / wKC, kWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2, t2, tp, evf, evp, sf);
         mark(2);

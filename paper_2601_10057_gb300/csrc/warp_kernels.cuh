@@ -48,7 +48,7 @@ template <int M> struct WGeo {
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32)
 kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
-            const cplx<float>* __restrict__ tw2, const PostTw<float>* __restrict__ twP) {
+            const cplx<float>* __restrict__ tw2, const PostTw<float>* __restrict__ twP, int ahead) {
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS, NP = (M / 2 + G) / G;
     constexpr int LDS = 2 * Gm::BUF;                 // floats per line buffer
@@ -56,6 +56,11 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
     const int f = blockIdx.y, y0 = blockIdx.x * RT;
+    {   // rows of the CTA one residency ahead
+        const int t = blockIdx.y * gridDim.x + blockIdx.x + ahead;
+        if (ahead > 0 && t < (int)(gridDim.x * gridDim.y) && threadIdx.x < RT)
+            prefetch_l2(in + (t / gridDim.x) * NN + (size_t)((t % gridDim.x) * RT + threadIdx.x) * N, N * sizeof(float));
+    }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / G, n2 = lane % G;
     const int slot = warp * Gm::LPW + grp;
