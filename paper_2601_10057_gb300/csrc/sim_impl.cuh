@@ -303,7 +303,7 @@ public:
         wRT = Gm::SLOTS; wsm_rt = bb;
         wKC = Gm::SLOTS / NF; wsm_col = bb;
         wRT4 = Gm::SLOTS / 2; wsm_comb = bb;
-        wRI = Gm::SLOTS / 2; wsm_irow = bb;
+        wsm_irow = InvGeo<MM>::smem_bytes();
         if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col, true) ||
             set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
             return CCMSAV_ECUDA;
@@ -371,7 +371,8 @@ public:
         kw_comb_icolT<MM><<<N / wRT4, kWarps * 32, wsm_comb, st>>>(reinterpret_cast<const float*>(bufA),
             reinterpret_cast<float*>(bufB), tw2, tp, evf, evp, sf, sc, anchor);
         mark(4);
-        kw_irow<MM><<<N / wRI, kWarps * 32, wsm_irow, st>>>(reinterpret_cast<const float*>(bufB),
+        kw_irow<MM><<<(2 * N + InvGeo<MM>::LINES - 1) / InvGeo<MM>::LINES, kWarpsInv * 32, wsm_irow, st>>>(
+            reinterpret_cast<const float*>(bufB),
             reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), tw2, tp,
             reinterpret_cast<const float*>(phi[cur]), reinterpret_cast<const float*>(phi[prev]),
             reinterpret_cast<const float*>(psi[cur]), reinterpret_cast<const float*>(psi[prev]),

@@ -6,7 +6,7 @@
 //      exact compile-time twiddles; output in bit-reversed register order);
 //   2. twiddle by W_M^{n2 k1} (table tw2[k1][n2], coalesced across lanes);
 //   3. transpose through the line's shared-memory buffer (rows padded to
-//      G + 1 complex values, conflict-free);
+//      G + 1 values, or unpadded and XOR-swizzled; both conflict-free);
 //   4. E/G G-point DFTs over n2 in registers; the result Z[k1 + E k2] is
 //      written to the buffer in natural order.
 // One smem round trip per stage pair instead of one per radix-8 stage, no
@@ -106,16 +106,26 @@ template <> struct Shape<512>  { static constexpr int E = 32, G = 16; };
 template <> struct Shape<1024> { static constexpr int E = 32, G = 32; };
 
 // Per-line buffer length (complex values) for the transpose and the
-// natural-order result.
-template <int M> __host__ __device__ constexpr int buf_len() {
-    // + 2 complex: as a float row the buffer stride is then 4 mod 32 words,
-    // which keeps the strided reads of the transposed writes conflict-free
-    return Shape<M>::E * (Shape<M>::G + 1) + 2;
+// natural-order result.  Padded (SWZ = false): rows of G + 1 values; + 2 so
+// that, as float rows, consecutive line buffers sit 4 banks apart (the
+// strided reads of the transposed writes).  Swizzled (SWZ = true): M values
+// + 2, for kernels that need more lines per SM.
+template <int M, bool SWZ = false> __host__ __device__ constexpr int buf_len() {
+    return SWZ ? M + 2 : Shape<M>::E * (Shape<M>::G + 1) + 2;
+}
+
+// Position of element c of transpose row R (E rows of G values).  Padded:
+// R (G + 1) + c.  Swizzled: R G + (c ^ swz(R)), swz(R) = (R / J) mod G with
+// J = E / G; writes (one row, all lanes of a group) and reads (lane n2 reads
+// rows n2 J + j) both touch distinct banks within each half-warp.
+template <int M, bool SWZ> __device__ __forceinline__ int tpos(int R, int c) {
+    constexpr int G = Shape<M>::G, J = Shape<M>::E / Shape<M>::G;
+    return SWZ ? R * G + (c ^ ((R / J) & (G - 1))) : R * (G + 1) + c;
 }
 
 // Steps 1-4.  v: this lane's E values in four-step order.  buf: this line's
 // buffer.  On return buf[k] = Z[k], k = 0..M-1 (visible to the warp).
-template <typename T, int M, bool INV>
+template <typename T, int M, bool INV, bool SWZ = false>
 __device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>* __restrict__ tw2, int n2) {
     constexpr int E = Shape<M>::E, G = Shape<M>::G, J = E / G;
     DIF<T, E, INV, 0>::run(v);
@@ -123,13 +133,13 @@ __device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>
     for (int r = 0; r < E; ++r) {
         const int k1 = bitrev<E>(r);
         const cplx<T> w = tw2[k1 * G + n2];
-        buf[k1 * (G + 1) + n2] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+        buf[tpos<M, SWZ>(k1, n2)] = INV ? cmulc(v[r], w) : cmul(v[r], w);
     }
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < J; ++j)
 #pragma unroll
-        for (int m = 0; m < G; ++m) v[j * G + m] = buf[(n2 * J + j) * (G + 1) + m];
+        for (int m = 0; m < G; ++m) v[j * G + m] = buf[tpos<M, SWZ>(n2 * J + j, m)];
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < J; ++j) {

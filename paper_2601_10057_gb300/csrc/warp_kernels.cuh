@@ -276,36 +276,46 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
 }
 
 // ------------------------------------------------------------------ kw_irow
-// SLOTS/2 rows per CTA, two lines (phi, psi) per row.  Phase 1 (all
-// threads): pre-process the transposed rows into the line buffers; phase 2
-// (per line): inverse four-step FFT, then u^{n+1} = u_bar + du with the
-// compensated (and, for psi on the FP32 path, dithered and mass-anchored)
-// final rounding.
+// kWarpsInv * LPW lines per CTA, line = 2 y + field (phi, psi of row y), so
+// that 3 CTAs per SM hold every line of an N = 2048 field at once (one round,
+// no tail).  Phase 1 (all threads): pre-process the transposed rows into
+// the line buffers; phase 2 (per line): inverse four-step FFT, then
+// u^{n+1} = u_bar + du with the compensated (and, for psi on the FP32 path,
+// error-feedback and mass-anchored) final rounding.
+constexpr int kWarpsInv = 9;
+
+template <int M> struct InvGeo {
+    static constexpr int LINES = kWarpsInv * WGeo<M>::LPW;     // lines per CTA
+    static constexpr int BUF = wf::buf_len<M, true>();         // unpadded, swizzled transpose
+    static constexpr size_t smem_bytes() { return (size_t)LINES * BUF * sizeof(cplx<float>); }
+};
+
 template <int M>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarpsInv * 32, 3)
 kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __restrict__ psi_new,
         const cplx<float>* __restrict__ tw2, const PostTw<float>* __restrict__ twP,
         const float* __restrict__ phn, const float* __restrict__ pho,
         const float* __restrict__ psn, const float* __restrict__ pso, int bdf1,
         const DevScalars* __restrict__ dsc, int anchor_mass) {
     using Gm = WGeo<M>;
-    constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RI = Gm::SLOTS / 2, NU = (M / 2 + G - 1) / G;
+    constexpr int N = 2 * M, G = Gm::G, E = Gm::E, L = InvGeo<M>::LINES, NU = (M / 2 + G - 1) / G;
     const uint32_t step = (uint32_t)dsc->steps;         // dither key (graph replays read it here)
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
-    const int y0 = blockIdx.x * RI;
+    const int l0 = blockIdx.x * L;                       // first line of this CTA
     const float inv0 = 1.0f / (M * sqrtf(1.0f / N)), inv = 1.0f / (M * sqrtf(2.0f / N));
     constexpr int PAIRS = M / 2 + 1;
 #pragma unroll 4
-    for (int q = threadIdx.x; q < 2 * RI * PAIRS; q += blockDim.x) {
+    for (int q = threadIdx.x; q < L * PAIRS; q += blockDim.x) {
         const int l = q / PAIRS, k = q % PAIRS;
-        const int r = l >> 1, fld = l & 1;
-        const float* row = in + fld * NN + (size_t)(y0 + r) * N;
+        const int gl = l0 + l;
+        if (gl >= 2 * N) continue;
+        const float* row = in + (gl & 1) * NN + (size_t)(gl >> 1) * N;
         const Quad<float> X{__ldg(row + k), k > 0 ? __ldg(row + N - k) : 0.f, __ldg(row + M - k), __ldg(row + M + k)};
         cplx<float> zk, zMk;
         pre_inverse(X, k, twP[k], inv0, inv, zk, zMk);
-        cplx<float>* b = bufs + (size_t)l * Gm::BUF;
+        cplx<float>* b = bufs + (size_t)l * InvGeo<M>::BUF;
         b[k] = zk;
         if (k > 0) b[M - k] = zMk;
     }
@@ -313,21 +323,23 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / G, n2 = lane % G;
     const int slot = warp * Gm::LPW + grp;
-    const int r = slot >> 1, fld = slot & 1;
-    cplx<float>* buf = bufs + (size_t)slot * Gm::BUF;
+    const int gl = l0 + slot;
+    const bool valid = gl < 2 * N;                       // the last CTA has fewer lines
+    const int fld = gl & 1;
+    cplx<float>* buf = bufs + (size_t)slot * InvGeo<M>::BUF;
     {
         cplx<float> v[E];
 #pragma unroll
         for (int n1 = 0; n1 < E; ++n1) v[n1] = buf[G * n1 + n2];
         __syncwarp();
-        wf::fourstep<float, M, true>(v, buf, tw2, n2);
+        wf::fourstep<float, M, true, true>(v, buf, tw2, n2);
     }
-    const size_t roff = (size_t)(y0 + r) * N;
+    const size_t roff = valid ? (size_t)(gl >> 1) * N : 0;
     // FP32 path, psi: the row's increments should sum to sqrt(N) x0 (x0 the
     // row's DC coefficient); the residual of the FP32 transform and the
     // column residual dc_col are removed, with the mean anchor, in the final
     // rounding, so the stored mass stays conserved
-    const bool psi_line = fld == 1 && anchor_mass;
+    const bool psi_line = valid && fld == 1 && anchor_mass;
     float rhi = 0.f, rlo = 0.f;
     if (psi_line)
 #pragma unroll
@@ -358,6 +370,7 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
     for (int i = 0; i < NU; ++i) {
         const int m = n2 + G * i;
         const cplx<float> a = buf[m], b = buf[M - 1 - m];
+        if (!valid) continue;
         const float4 p = __ldg(un + m), q = __ldg(uo + m);
         float4 o;
         if (psi_line) {
