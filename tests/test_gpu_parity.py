@@ -261,3 +261,32 @@ def test_batched_graph_steps_match_single_runs(caller_stream):
         assert np.array_equal(phi, phi1) and np.array_equal(psi, psi1), f"simulation {k} (N={w.N})"
     assert all(sim.aux(sim=k)[10] == 15 for k in range(len(ws)))
     sim.close()
+
+
+@pytest.mark.slow
+def test_fp32_against_fp64_after_1000_steps_N2048():
+    """The precision form at full size: three vesicles, N = 2048, 1000 steps
+    at dt = 1e-5, FP32-bulk against the FP64 GPU path (itself within 1e-12 of
+    the oracle).  Measured: phi max 4.1e-5 / L2 1.9e-6, psi max 6.8e-6 / L2
+    2.6e-7 relative to the max-norm / RMS of the FP64 fields; the bounds
+    below leave about 2x room.  Stored mass of both paths within 5e-11 of the
+    initial mass."""
+    w = I.workload("three_vesicles", N=2048)
+    res = {}
+    for prec in ("fp64", "fp32"):
+        sim = cc.Simulation(w.params, w.N, precision=prec)
+        sim.set_state(w.phi0, w.psi0)
+        sim.step(1000)
+        sim.sync()
+        res[prec] = (*sim.state(), sim.mass())
+        sim.close()
+    (p64, q64, m64), (p32, q32, m32) = res["fp64"], res["fp32"]
+    m0 = float(np.sum(w.psi0)) * (w.params.L / w.N) ** 2
+    e = {"phi_max": rel(p32, p64), "psi_max": rel(q32, q64),
+         "phi_l2": float(np.sqrt(np.mean((p32 - p64) ** 2) / np.mean(p64 ** 2))),
+         "psi_l2": float(np.sqrt(np.mean((q32 - q64) ** 2) / np.mean(q64 ** 2))),
+         "mass32": abs(m32 - m0) / m0, "mass64": abs(m64 - m0) / m0}
+    print("fp32 vs fp64 after 1000 steps", e)
+    assert e["phi_l2"] < 5e-6 and e["psi_l2"] < 1e-6, e
+    assert e["phi_max"] < 1e-4 and e["psi_max"] < 2e-5, e
+    assert e["mass32"] < 5e-11 and e["mass64"] < 5e-11, e
