@@ -60,6 +60,8 @@ public:
     cplx<float>* tw2 = nullptr;
     float* evf = nullptr;
     float4* evp = nullptr;   // eigenvalues in the pair order of the warp-path spectra
+    wf::PairTw* twF = nullptr;   // forward / inverse pair twiddles of the warp path
+    wf::PairTw* twI = nullptr;
     int wRT = 8, wlds = 0, wRT4 = 4, wlds4 = 0, wKC = 1, wRI = 4;
     int ahead_rt = 0;   // L2 prefetch distance of the row kernel (its resident CTAs)
     size_t wsm_rt = 0, wsm_col = 0, wsm_comb = 0, wsm_irow = 0;
@@ -177,7 +179,8 @@ public:
         for (int i = 0; i < 3; ++i) { cudaFree(phi[i]); cudaFree(psi[i]); phi[i] = psi[i] = nullptr; }
         cudaFree(bufA); cudaFree(bufB); cudaFree(part1); cudaFree(part2); cudaFree(partd); cudaFree(part3);
         cudaFree(twM); cudaFree(twP); cudaFree(ev); cudaFree(sc); cudaFree(tmp64);
-        cudaFree(tw2); cudaFree(evf); cudaFree(evp); tw2 = nullptr; evf = nullptr; evp = nullptr;
+        cudaFree(tw2); cudaFree(evf); cudaFree(evp); cudaFree(twF); cudaFree(twI);
+        tw2 = nullptr; evf = nullptr; evp = nullptr; twF = nullptr; twI = nullptr;
         if (sc_host) cudaFreeHost(sc_host);
         if (h_part) cudaFreeHost(h_part);
         bufA = bufB = nullptr; part1 = part2 = partd = part3 = nullptr; twM = nullptr; twP = nullptr;
@@ -322,6 +325,7 @@ public:
 
     int init_warp_path() {
         std::vector<float> he(N), hp;
+        std::vector<wf::PairTw> hf, hi;
         const double hh = p.L / N;
         for (int k = 0; k < N; ++k) { const double s = std::sin(M_PI * k / (2.0 * N)); he[k] = (float)(4.0 * s * s / (hh * hh)); }
         if (cudaMalloc(&evf, N * sizeof(float)) != cudaSuccess) return CCMSAV_ENOMEM;
@@ -337,6 +341,28 @@ public:
         }
         if (cudaMalloc(&evp, hp.size() * sizeof(float)) != cudaSuccess) return CCMSAV_ENOMEM;
         CCM_CUDA(cudaMemcpyAsync(evp, hp.data(), hp.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        // pair twiddles (FP64 closed forms, see wf::PairTw)
+        hf.assign(Mh / 2 + 1, wf::PairTw{});
+        hi.assign(Mh / 2 + 1, wf::PairTw{});
+        const double c0 = std::sqrt(1.0 / N), c1 = std::sqrt(2.0 / N);
+        const double s0 = 1.0 / (Mh * c0), s1 = 1.0 / (Mh * c1);
+        for (int k = 0; k <= Mh / 2; ++k) {
+            const double a = 2.0 * M_PI * k / N, th = M_PI * k / (2.0 * N), q = M_PI / 4.0;
+            const double ck = k == 0 ? c0 : c1, sk = k == 0 ? s0 : s1;
+            wf::PairTw f{}, v{};
+            f.wnx = v.wnx = (float)std::cos(a);
+            f.wny = v.wny = (float)(-std::sin(a));
+            f.ax = (float)(0.5 * ck * std::cos(th)); f.ay = (float)(-0.5 * ck * std::sin(th));
+            f.bx = (float)(0.5 * c1 * std::cos(th - q)); f.by = (float)(0.5 * c1 * std::sin(th - q));
+            v.ax = (float)(0.5 * sk * std::cos(th)); v.ay = (float)(0.5 * sk * std::sin(th));
+            v.bx = (float)(0.5 * s1 * std::cos(q - th)); v.by = (float)(0.5 * s1 * std::sin(q - th));
+            hf[k] = f; hi[k] = v;
+        }
+        if (cudaMalloc(&twF, hf.size() * sizeof(wf::PairTw)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaMalloc(&twI, hi.size() * sizeof(wf::PairTw)) != cudaSuccess) return CCMSAV_ENOMEM;
+        CCM_CUDA(cudaMemcpyAsync(twF, hf.data(), hf.size() * sizeof(wf::PairTw), cudaMemcpyHostToDevice, st));
+        CCM_CUDA(cudaMemcpyAsync(twI, hi.data(), hi.size() * sizeof(wf::PairTw), cudaMemcpyHostToDevice, st));
+        CCM_CUDA(cudaStreamSynchronize(st));
         int r = CCMSAV_EINVAL;
         if constexpr (std::is_same<T, float>::value)
         switch (M) {
@@ -357,23 +383,21 @@ public:
         const float* fin = reinterpret_cast<const float*>(bufA);
         float* fB = reinterpret_cast<float*>(bufB);
         const cplx<float>* t2 = tw2;
-        const PostTw<float>* tp = reinterpret_cast<const PostTw<float>*>(twP);
-        kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, t2, tp, ahead_rt);
+        kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, t2, twF, ahead_rt);
         mark(1);
-        kw_coldct_gram<MM><<<N / wKC, kWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2, t2, tp, evf, evp, sf);
+        kw_coldct_gram<MM><<<N / wKC, kWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2, t2, twF, evf, evp, sf);
         mark(2);
     }
     int bdf1_launch = 0;
     template <int MM>
     void launch_warp_inverse(const SpecCoef& s, int anchor) {
         SpecCoefF sf{(float)s.C1, (float)s.C2, (float)s.C3, (float)s.Ct, (float)s.lam};
-        const PostTw<float>* tp = reinterpret_cast<const PostTw<float>*>(twP);
         kw_comb_icolT<MM><<<N / wRT4, kWarps * 32, wsm_comb, st>>>(reinterpret_cast<const float*>(bufA),
-            reinterpret_cast<float*>(bufB), tw2, tp, evf, evp, sf, sc, anchor);
+            reinterpret_cast<float*>(bufB), tw2, twI, evf, evp, sf, sc, anchor);
         mark(4);
         kw_irow<MM><<<(2 * N + InvGeo<MM>::LINES - 1) / InvGeo<MM>::LINES, kWarpsInv * 32, wsm_irow, st>>>(
             reinterpret_cast<const float*>(bufB),
-            reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), tw2, tp,
+            reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), tw2, twI,
             reinterpret_cast<const float*>(phi[cur]), reinterpret_cast<const float*>(phi[prev]),
             reinterpret_cast<const float*>(psi[cur]), reinterpret_cast<const float*>(psi[prev]),
             bdf1_launch, sc, anchor);

@@ -169,6 +169,53 @@ __device__ __forceinline__ void pack_fwd_global(const float* __restrict__ x, cpl
     }
 }
 
+// Twiddles of the pair (k, M-k) for the lean post-/pre-processing below
+// (host-computed in FP64 from the closed forms; the 1/2 of the even/odd
+// split, the DCT normalisation and the e^{-+i pi/4} rotation are folded in):
+//   wn = e^{-2 pi i k / N};
+//   forward: a = c_k / 2 e^{-i pi k / (2N)} (c_0 = sqrt(1/N), c_k = sqrt(2/N)),
+//            b = sqrt(2/N) / 2 e^{-i pi/4} e^{+i pi k / (2N)};
+//   inverse: a = s_k / 2 e^{+i pi k / (2N)} (s_0 = 1/(M sqrt(1/N)), s_k = 1/(M sqrt(2/N))),
+//            b = s_k' / 2 e^{+i pi/4} e^{-i pi k / (2N)} (s_k' = 1/(M sqrt(2/N))).
+struct alignas(16) PairTw { float wnx, wny, ax, ay, bx, by, pad0, pad1; };
+
+__device__ __forceinline__ PairTw load_pair_tw(const PairTw* __restrict__ t, int k) {
+    const float4 u = __ldg(reinterpret_cast<const float4*>(t + k));
+    const float4 v = __ldg(reinterpret_cast<const float4*>(t + k) + 1);
+    return PairTw{u.x, u.y, u.z, u.w, v.x, v.y, 0.f, 0.f};
+}
+
+// Forward post-process of the pair (k, M-k): A = Z[k], B = Z[M-k].  With
+// P = A + conj B, Q = A - conj B and U = wn Q, the half-length spectrum gives
+// V[k] ~ P - iU and V[M-k] ~ conj(P + iU), so
+//   X[k] = Re(a S), X[N-k] = -Im(a S), S = P - iU;
+//   X[M-k] = Re(b R), X[M+k] = -Im(b R), R = conj(P + iU).
+__device__ __forceinline__ Quad<float> post_pair_lean(cplx<float> A, cplx<float> B, const PairTw& t) {
+    const float Px = A.x + B.x, Py = A.y - B.y, Qx = A.x - B.x, Qy = A.y + B.y;
+    const float Ux = t.wnx * Qx - t.wny * Qy, Uy = t.wnx * Qy + t.wny * Qx;
+    const float Sx = Px + Uy, Sy = Py - Ux;
+    const float Rx = Px - Uy, Ry = -(Py + Ux);
+    Quad<float> q;
+    q.xk = t.ax * Sx - t.ay * Sy;
+    q.xNk = -(t.ax * Sy + t.ay * Sx);
+    q.xMk = t.bx * Rx - t.by * Ry;
+    q.xMpk = -(t.bx * Ry + t.by * Rx);
+    return q;
+}
+
+// Inverse pre-process of the pair (k, M-k) from X[k], X[N-k] (0 for k = 0),
+// X[M-k], X[M+k]: Vk = a (X[k] - i X[N-k]), Vm = b (X[M-k] - i X[M+k]),
+// s = Vk + conj Vm, d = Vk - conj Vm, tt = d conj(wn); then
+// z[k] = s + i tt and z[M-k] = conj(s) + i conj(tt).
+__device__ __forceinline__ void pre_pair_lean(const Quad<float>& X, const PairTw& t, cplx<float>& zk, cplx<float>& zMk) {
+    const float Vkx = t.ax * X.xk + t.ay * X.xNk, Vky = t.ay * X.xk - t.ax * X.xNk;
+    const float Vmx = t.bx * X.xMk + t.by * X.xMpk, Vmy = t.by * X.xMk - t.bx * X.xMpk;
+    const float sx = Vkx + Vmx, sy = Vky - Vmy, dx = Vkx - Vmx, dy = Vky + Vmy;
+    const float tx = dx * t.wnx + dy * t.wny, ty = dy * t.wnx - dx * t.wny;
+    zk = mk(sx - ty, sy + tx);
+    zMk = mk(sx + ty, tx - sy);
+}
+
 // Forward post-process of the pair (k, M-k) from natural-order Z values.
 template <typename T>
 __device__ __forceinline__ Quad<T> post_pair(cplx<T> A, cplx<T> B, int k, PostTw<T> tw, T cn0, T cn) {

@@ -48,7 +48,7 @@ template <int M> struct WGeo {
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32)
 kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
-            const cplx<float>* __restrict__ tw2, const PostTw<float>* __restrict__ twP, int ahead) {
+            const cplx<float>* __restrict__ tw2, const wf::PairTw* __restrict__ twF, int ahead) {
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS, NP = (M / 2 + G) / G;
     constexpr int LDS = 2 * Gm::BUF;                 // floats per line buffer
@@ -65,7 +65,6 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
     const int grp = lane / G, n2 = lane % G;
     const int slot = warp * Gm::LPW + grp;
     cplx<float>* buf = bufs + (size_t)slot * Gm::BUF;
-    const float cn0 = sqrtf(1.0f / N), cn = sqrtf(2.0f / N);
     {
         cplx<float> v[E];
         wf::pack_fwd_global<M>(in + f * NN + (size_t)(y0 + slot) * N, v, n2);
@@ -75,7 +74,7 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         const int k = n2 + G * i;
-        if (k <= M / 2) X[i] = wf::post_pair(buf[k], buf[(M - k) & (M - 1)], k, twP[k], cn0, cn);
+        if (k <= M / 2) X[i] = wf::post_pair_lean(buf[k], buf[(M - k) & (M - 1)], wf::load_pair_tw(twF, k));
     }
     __syncwarp();
     float* srow = reinterpret_cast<float*>(buf);
@@ -105,7 +104,7 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32, 3)
 kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* __restrict__ part,
-               const cplx<float>* __restrict__ tw2, const PostTw<float>* __restrict__ twP,
+               const cplx<float>* __restrict__ tw2, const wf::PairTw* __restrict__ twF,
                const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc) {
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, KC = Gm::SLOTS / NF;
@@ -124,7 +123,6 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
         wf::fourstep<float, M, false>(v, bufs + (size_t)slot * Gm::BUF, tw2, n2);
     }
     __syncthreads();
-    const float cn0 = sqrtf(1.0f / N), cn = sqrtf(2.0f / N);
     float acc[NRED2];
 #pragma unroll
     for (int i = 0; i < NRED2; ++i) acc[i] = 0.f;
@@ -132,10 +130,11 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
         const int c = q / (M / 2 + 1), k = q % (M / 2 + 1);
         const int kx = kx0 + c;
         Quad<float> X[NF];
+        const wf::PairTw tw = wf::load_pair_tw(twF, k);
 #pragma unroll
         for (int g = 0; g < NF; ++g) {
             const cplx<float>* b = bufs + (size_t)(c * NF + g) * Gm::BUF;
-            X[g] = wf::post_pair(b[k], b[(M - k) & (M - 1)], k, twP[k], cn0, cn);
+            X[g] = wf::post_pair_lean(b[k], b[(M - k) & (M - 1)], tw);
         }
         const float evx = evf[kx];
         const float4 e4 = evp[k];
@@ -176,7 +175,7 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32)
 kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
-              const cplx<float>* __restrict__ tw2, const PostTw<float>* __restrict__ twP,
+              const cplx<float>* __restrict__ tw2, const wf::PairTw* __restrict__ twI,
               const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc,
               DevScalars* __restrict__ dsc, int anchor_mass) {
     using Gm = WGeo<M>;
@@ -186,7 +185,6 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
     const int kx0 = blockIdx.x * RT;
-    const float inv0 = 1.0f / (M * sqrtf(1.0f / N)), inv = 1.0f / (M * sqrtf(2.0f / N));
     const float aS = (float)dsc->alpha[0], aH = (float)dsc->alpha[1], aQ = (float)dsc->alpha[2];
     const float aK = (float)dsc->alpha[3], aL = (float)dsc->alpha[4];
     constexpr int PAIRS = M / 2 + 1;
@@ -222,14 +220,14 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
         // d_psi has zero mean (mass conservation); the FP32 path sets the
         // zero mode exactly and keeps the stored mean with the anchor
         if (anchor_mass && kx == 0 && k == 0) vq[0] = 0.f;
-        const PostTw<float> tw = twP[k];
+        const wf::PairTw tw = wf::load_pair_tw(twI, k);
         cplx<float> zk, zMk;
         cplx<float>* b = bufs + (size_t)(2 * r) * Gm::BUF;
-        pre_inverse(Quad<float>{vp[0], vp[1], vp[2], vp[3]}, k, tw, inv0, inv, zk, zMk);
+        wf::pre_pair_lean(Quad<float>{vp[0], vp[1], vp[2], vp[3]}, tw, zk, zMk);
         b[k] = zk;
         if (k > 0) b[M - k] = zMk;
         b += Gm::BUF;
-        pre_inverse(Quad<float>{vq[0], vq[1], vq[2], vq[3]}, k, tw, inv0, inv, zk, zMk);
+        wf::pre_pair_lean(Quad<float>{vq[0], vq[1], vq[2], vq[3]}, tw, zk, zMk);
         b[k] = zk;
         if (k > 0) b[M - k] = zMk;
     }
@@ -293,7 +291,7 @@ template <int M> struct InvGeo {
 template <int M>
 __global__ void __launch_bounds__(kWarpsInv * 32, 3)
 kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __restrict__ psi_new,
-        const cplx<float>* __restrict__ tw2, const PostTw<float>* __restrict__ twP,
+        const cplx<float>* __restrict__ tw2, const wf::PairTw* __restrict__ twI,
         const float* __restrict__ phn, const float* __restrict__ pho,
         const float* __restrict__ psn, const float* __restrict__ pso, int bdf1,
         const DevScalars* __restrict__ dsc, int anchor_mass) {
@@ -304,7 +302,6 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
     const int l0 = blockIdx.x * L;                       // first line of this CTA
-    const float inv0 = 1.0f / (M * sqrtf(1.0f / N)), inv = 1.0f / (M * sqrtf(2.0f / N));
     constexpr int PAIRS = M / 2 + 1;
 #pragma unroll 4
     for (int q = threadIdx.x; q < L * PAIRS; q += blockDim.x) {
@@ -314,7 +311,7 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
         const float* row = in + (gl & 1) * NN + (size_t)(gl >> 1) * N;
         const Quad<float> X{__ldg(row + k), k > 0 ? __ldg(row + N - k) : 0.f, __ldg(row + M - k), __ldg(row + M + k)};
         cplx<float> zk, zMk;
-        pre_inverse(X, k, twP[k], inv0, inv, zk, zMk);
+        wf::pre_pair_lean(X, wf::load_pair_tw(twI, k), zk, zMk);
         cplx<float>* b = bufs + (size_t)l * InvGeo<M>::BUF;
         b[k] = zk;
         if (k > 0) b[M - k] = zMk;
