@@ -282,7 +282,7 @@ public:
             set_smem_limit((const void*)k_comb_icolT<T>, sm_comb) || set_smem_limit((const void*)k_irow<T>, sm_irow))
             return CCMSAV_ECUDA;
         const char* force_block = std::getenv("CCMSAV_FORCE_BLOCK_FFT");   // test switch: block-FFT kernels only
-        if (std::is_same<T, float>::value && M >= 64 && M <= 1024 && !(force_block && force_block[0] == '1')) {
+        if (std::is_same<T, float>::value && M >= 64 && M <= 2048 && !(force_block && force_block[0] == '1')) {
             int r = init_warp_path();
             if (r) return r;
         }
@@ -371,6 +371,7 @@ public:
             case 256: r = setup_warp<256>(); break;
             case 512: r = setup_warp<512>(); break;
             case 1024: r = setup_warp<1024>(); break;
+            case 2048: r = setup_warp<2048>(); break;
         }
         if (r == CCMSAV_OK) warp_path = true;
         return r;
@@ -410,7 +411,8 @@ public:
             case 128: launch_warp_ffts<128>(s, anchor); break;
             case 256: launch_warp_ffts<256>(s, anchor); break;
             case 512: launch_warp_ffts<512>(s, anchor); break;
-            default: launch_warp_ffts<1024>(s, anchor); break;
+            case 1024: launch_warp_ffts<1024>(s, anchor); break;
+            default: launch_warp_ffts<2048>(s, anchor); break;
         }
     }
     void warp_inverse(const SpecCoef& s, int anchor) {
@@ -420,7 +422,8 @@ public:
             case 128: launch_warp_inverse<128>(s, anchor); break;
             case 256: launch_warp_inverse<256>(s, anchor); break;
             case 512: launch_warp_inverse<512>(s, anchor); break;
-            default: launch_warp_inverse<1024>(s, anchor); break;
+            case 1024: launch_warp_inverse<1024>(s, anchor); break;
+            default: launch_warp_inverse<2048>(s, anchor); break;
         }
     }
 

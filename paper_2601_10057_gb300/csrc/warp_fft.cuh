@@ -11,8 +11,8 @@
 //      written to the buffer in natural order.
 // One smem round trip per stage pair instead of one per radix-8 stage, no
 // block barriers (only __syncwarp), and 32 independent values per lane.
-// Supported lines: M in {64, 128, 256, 512, 1024} (N = 2M in 128 .. 2048);
-// G = 2^floor(log2(M)/2) <= E = M / G <= 32.
+// Supported lines: M in {64, ..., 2048} (N = 2M in 128 .. 4096);
+// G = 2^floor(log2(M)/2) <= 32, E = M / G <= 64.
 #pragma once
 #include "dct_device.cuh"
 
@@ -57,16 +57,88 @@ __device__ __forceinline__ void w32(int j, double& c, double& s) {
     }
 }
 
+// 64th roots of unity: w64(j) = cos(2 pi j / 64), sin(2 pi j / 64), j = 0..63
+__device__ __forceinline__ void w64(int j, double& c, double& s) {
+    switch (j & 63) {
+        case 0: c = 1.0; s = 0.0; break;
+        case 1: c = 0.9951847266721969; s = 0.0980171403295606; break;
+        case 2: c = 0.9807852804032304; s = 0.19509032201612825; break;
+        case 3: c = 0.9569403357322088; s = 0.29028467725446233; break;
+        case 4: c = 0.9238795325112867; s = 0.3826834323650898; break;
+        case 5: c = 0.881921264348355; s = 0.47139673682599764; break;
+        case 6: c = 0.8314696123025452; s = 0.5555702330196022; break;
+        case 7: c = 0.773010453362737; s = 0.6343932841636455; break;
+        case 8: c = 0.7071067811865476; s = 0.7071067811865475; break;
+        case 9: c = 0.6343932841636455; s = 0.773010453362737; break;
+        case 10: c = 0.5555702330196023; s = 0.8314696123025452; break;
+        case 11: c = 0.4713967368259978; s = 0.8819212643483549; break;
+        case 12: c = 0.38268343236508984; s = 0.9238795325112867; break;
+        case 13: c = 0.29028467725446233; s = 0.9569403357322089; break;
+        case 14: c = 0.19509032201612833; s = 0.9807852804032304; break;
+        case 15: c = 0.09801714032956077; s = 0.9951847266721968; break;
+        case 16: c = 0.0; s = 1.0; break;
+        case 17: c = -0.09801714032956065; s = 0.9951847266721969; break;
+        case 18: c = -0.1950903220161282; s = 0.9807852804032304; break;
+        case 19: c = -0.29028467725446216; s = 0.9569403357322089; break;
+        case 20: c = -0.3826834323650897; s = 0.9238795325112867; break;
+        case 21: c = -0.4713967368259977; s = 0.881921264348355; break;
+        case 22: c = -0.555570233019602; s = 0.8314696123025455; break;
+        case 23: c = -0.6343932841636454; s = 0.7730104533627371; break;
+        case 24: c = -0.7071067811865475; s = 0.7071067811865476; break;
+        case 25: c = -0.773010453362737; s = 0.6343932841636455; break;
+        case 26: c = -0.8314696123025453; s = 0.5555702330196022; break;
+        case 27: c = -0.8819212643483549; s = 0.47139673682599786; break;
+        case 28: c = -0.9238795325112867; s = 0.3826834323650899; break;
+        case 29: c = -0.9569403357322088; s = 0.2902846772544624; break;
+        case 30: c = -0.9807852804032304; s = 0.1950903220161286; break;
+        case 31: c = -0.9951847266721968; s = 0.09801714032956083; break;
+        case 32: c = -1.0; s = 0.0; break;
+        case 33: c = -0.9951847266721969; s = -0.09801714032956059; break;
+        case 34: c = -0.9807852804032304; s = -0.19509032201612836; break;
+        case 35: c = -0.9569403357322089; s = -0.2902846772544621; break;
+        case 36: c = -0.9238795325112868; s = -0.38268343236508967; break;
+        case 37: c = -0.881921264348355; s = -0.47139673682599764; break;
+        case 38: c = -0.8314696123025455; s = -0.555570233019602; break;
+        case 39: c = -0.7730104533627371; s = -0.6343932841636453; break;
+        case 40: c = -0.7071067811865477; s = -0.7071067811865475; break;
+        case 41: c = -0.6343932841636459; s = -0.7730104533627367; break;
+        case 42: c = -0.5555702330196022; s = -0.8314696123025452; break;
+        case 43: c = -0.47139673682599786; s = -0.8819212643483549; break;
+        case 44: c = -0.38268343236509034; s = -0.9238795325112865; break;
+        case 45: c = -0.29028467725446244; s = -0.9569403357322088; break;
+        case 46: c = -0.19509032201612866; s = -0.9807852804032303; break;
+        case 47: c = -0.09801714032956045; s = -0.9951847266721969; break;
+        case 48: c = 0.0; s = -1.0; break;
+        case 49: c = 0.09801714032956009; s = -0.9951847266721969; break;
+        case 50: c = 0.1950903220161283; s = -0.9807852804032304; break;
+        case 51: c = 0.29028467725446205; s = -0.9569403357322089; break;
+        case 52: c = 0.38268343236509; s = -0.9238795325112866; break;
+        case 53: c = 0.4713967368259976; s = -0.881921264348355; break;
+        case 54: c = 0.5555702330196018; s = -0.8314696123025455; break;
+        case 55: c = 0.6343932841636456; s = -0.7730104533627369; break;
+        case 56: c = 0.7071067811865474; s = -0.7071067811865477; break;
+        case 57: c = 0.7730104533627367; s = -0.6343932841636459; break;
+        case 58: c = 0.8314696123025452; s = -0.5555702330196022; break;
+        case 59: c = 0.8819212643483548; s = -0.4713967368259979; break;
+        case 60: c = 0.9238795325112865; s = -0.3826834323650904; break;
+        case 61: c = 0.9569403357322088; s = -0.2902846772544625; break;
+        case 62: c = 0.9807852804032303; s = -0.19509032201612872; break;
+        case 63: c = 0.9951847266721969; s = -0.0980171403295605; break;
+        default: c = 1.0; s = 0.0; break;
+    }
+}
+
 // x * W_R^i (forward: exp(-2 pi i I / R); INV: conjugate)
 template <typename T, int R, bool INV>
 __device__ __forceinline__ cplx<T> twid(cplx<T> x, int i) {
-    const int j = (i * (32 / R)) & 31;
+    constexpr int RM = R > 32 ? 64 : 32;          // table of RM-th roots of unity
+    const int j = (i * (RM / R)) & (RM - 1);
     if (j == 0) return x;
-    if (j == 8) return INV ? mk(-x.y, x.x) : mk(x.y, -x.x);
-    if (j == 16) return mk(-x.x, -x.y);
-    if (j == 24) return INV ? mk(x.y, -x.x) : mk(-x.y, x.x);
+    if (j == RM / 4) return INV ? mk(-x.y, x.x) : mk(x.y, -x.x);
+    if (j == RM / 2) return mk(-x.x, -x.y);
+    if (j == 3 * RM / 4) return INV ? mk(x.y, -x.x) : mk(-x.y, x.x);
     double c, s;
-    w32(j, c, s);
+    if (RM == 64) w64(j, c, s); else w32(j, c, s);
     const T cc = (T)c, ss = INV ? (T)s : (T)(-s);     // W = c + i ss
     return mk(x.x * cc - x.y * ss, x.x * ss + x.y * cc);
 }
@@ -104,6 +176,7 @@ template <> struct Shape<128>  { static constexpr int E = 16, G = 8;  };
 template <> struct Shape<256>  { static constexpr int E = 16, G = 16; };
 template <> struct Shape<512>  { static constexpr int E = 32, G = 16; };
 template <> struct Shape<1024> { static constexpr int E = 32, G = 32; };
+template <> struct Shape<2048> { static constexpr int E = 64, G = 32; };
 
 // Per-line buffer length (complex values) for the transpose and the
 // natural-order result.  Padded (SWZ = false): rows of G + 1 values; + 2 so

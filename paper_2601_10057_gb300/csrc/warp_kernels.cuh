@@ -102,7 +102,7 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
 
 // ------------------------------------------------------------------ kw_coldct_gram
 template <int M>
-__global__ void __launch_bounds__(kWarps * 32, 3)
+__global__ void __launch_bounds__(kWarps * 32, M <= 1024 ? 3 : 1)
 kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* __restrict__ part,
                const cplx<float>* __restrict__ tw2, const wf::PairTw* __restrict__ twF,
                const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc) {
@@ -289,7 +289,7 @@ template <int M> struct InvGeo {
 };
 
 template <int M>
-__global__ void __launch_bounds__(kWarpsInv * 32, 3)
+__global__ void __launch_bounds__(kWarpsInv * 32, M <= 1024 ? 3 : 1)
 kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __restrict__ psi_new,
         const cplx<float>* __restrict__ tw2, const wf::PairTw* __restrict__ twI,
         const float* __restrict__ phn, const float* __restrict__ pho,

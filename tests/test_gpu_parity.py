@@ -290,3 +290,22 @@ def test_fp32_against_fp64_after_1000_steps_N2048():
     assert e["phi_l2"] < 5e-6 and e["psi_l2"] < 1e-6, e
     assert e["phi_max"] < 1e-4 and e["psi_max"] < 2e-5, e
     assert e["mass32"] < 5e-11 and e["mass64"] < 5e-11, e
+
+
+def test_fp32_warp_path_N4096_against_fp64():
+    """Line length M = 2048 of the FP32 warp FFTs (64 values per lane): three
+    vesicles at N = 4096, 3 steps against the FP64 path (block FFTs, the same
+    code that matches the oracle at N <= 2048); bound 5e-6 of the max-norm
+    as for the other line lengths."""
+    w = I.workload("three_vesicles", N=4096)
+    out = {}
+    for prec in ("fp64", "fp32"):
+        sim = cc.Simulation(w.params, w.N, precision=prec)
+        sim.set_state(w.phi0, w.psi0)
+        sim.step(3)
+        sim.sync()
+        out[prec] = sim.state()
+        sim.close()
+    e = (rel(out["fp32"][0], out["fp64"][0]), rel(out["fp32"][1], out["fp64"][1]))
+    print("fp32 N=4096 vs fp64", e)
+    assert max(e) < 5e-6, e
