@@ -579,7 +579,11 @@ public:
             k_coldct_gram<T><<<N, 512, sm_col, st>>>(bufB, bufA, part2, N, FG, twM, twP, ev, s);
             mark(2);
         }
-        k_solve<<<kSolveBlocks, kSolveThreads, 0, st>>>(part1, so.nb1, part2, so.nb2, part3, sc, so);
+        {   // partial rows: FP64, or float pairs on the FP32 path
+            using P = typename PartialOf<T>::type;
+            k_solve<P><<<kSolveBlocks, kSolveThreads, 0, st>>>(reinterpret_cast<const P*>(part1), so.nb1,
+                                                               reinterpret_cast<const P*>(part2), so.nb2, part3, sc, so);
+        }
         mark(3);
         if (warp_path) {
             bdf1_launch = so.bdf1;

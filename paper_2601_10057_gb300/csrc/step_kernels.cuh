@@ -43,6 +43,7 @@
 //   k_irow        inverse DCT along x and phi^{n+1} = phi_bar + d_phi,
 //                 psi^{n+1} = psi_bar + d_psi.
 #pragma once
+#include <type_traits>
 #include "dct_device.cuh"
 
 namespace ccm {
@@ -141,6 +142,7 @@ __device__ void block_sum_store(T (&v)[NV], double* out, double* sm) {
     __syncthreads();
 }
 
+
 // Warp sum carried as an unevaluated pair hi + lo (error-free transformation
 // TwoSum of Knuth / Dekker double-length arithmetic), so that a warp of FP32
 // values sums to ~2^-44 relative accuracy without FP64 per element.
@@ -173,6 +175,15 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float x) {
     hi = s;
     lo += e;
 }
+
+// (hi, lo) += (bh, bl) in double-float arithmetic (TwoSum of the high parts)
+__device__ __forceinline__ void df_add2(float& hi, float& lo, float bh, float bl) {
+    float s, e;
+    two_sum(hi, bh, s, e);
+    e += lo + bl;
+    hi = s + e;
+    lo = e - (hi - s);
+}
 template <int G>
 __device__ __forceinline__ double group_sum_exact(float hi, float lo) {
 #pragma unroll
@@ -188,6 +199,47 @@ __device__ __forceinline__ double group_sum_exact(float hi, float lo) {
     return (double)hi + (double)lo;
 }
 
+// The same group sum kept as an unevaluated pair (no FP64 instruction)
+template <int G>
+__device__ __forceinline__ float2 group_sum_df(float hi, float lo) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1)
+        df_add2(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+    return make_float2(hi, lo);
+}
+
+// Partial-sum rows read by k_solve: FP64 on the FP64 path; on the FP32 path
+// unevaluated float pairs (hi, lo), formed without FP64 instructions (FP64
+// issues at a small fraction of the FP32 rate on GB300), 8 bytes like a double.
+template <typename T> struct PartialOf { using type = double; };
+template <> struct PartialOf<float> { using type = float2; };
+
+// block_sum_store into a partial row of the precision's type: for FP32 the
+// T-precision warp sums are added over the warps in double-float.
+template <int NV, typename T>
+__device__ void block_sum_store_part(T (&v)[NV], typename PartialOf<T>::type* out, double* sm) {
+    if constexpr (std::is_same<T, double>::value) {
+        block_sum_store<NV, T>(v, out, sm);
+    } else {
+        float* smf = reinterpret_cast<float*>(sm);
+        const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+        const int nthr = blockDim.x * blockDim.y;
+        const int lane = tid & 31, warp = tid >> 5, nw = (nthr + 31) >> 5;
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            const float sw = warp_sum(v[i]);
+            if (lane == 0) smf[warp * NV + i] = sw;
+        }
+        __syncthreads();
+        if (tid < NV) {
+            float hi = 0.f, lo = 0.f;
+            for (int w = 0; w < nw; ++w) df_add(hi, lo, smf[w * NV + tid]);
+            out[tid] = make_float2(hi, lo);
+        }
+        __syncthreads();
+    }
+}
+
 // Per-thread accumulator of a field sum: double-float for FP32 fields, plain
 // FP64 for FP64 fields.
 template <typename T> struct ExactSum;
@@ -195,6 +247,7 @@ template <> struct ExactSum<float> {
     float hi = 0.f, lo = 0.f;
     __device__ __forceinline__ void add(float x) { df_add(hi, lo, x); }
     __device__ __forceinline__ double warp_total() { return group_sum_exact<32>(hi, lo); }
+    __device__ __forceinline__ float2 warp_pair() { return group_sum_df<32>(hi, lo); }
 };
 template <> struct ExactSum<double> {
     double s = 0.0;
@@ -401,27 +454,53 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
             sum_o.add(pso[g]);
         }
     }
-    double* prow = part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * NRED1;
+    const size_t prow_i = (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * NRED1;
     const int lane = tid & 31, wp = tid >> 5;
     const T w0 = warp_sum(acc0), w1 = warp_sum(acc1), w2 = warp_sum(acc2);
-    const double sn = sum_n.warp_total(), so = sum_o.warp_total();
     mm = warp_min(mm);
-    if (lane == 0) {
-        sred[wp * 4 + 0] = (double)w0; sred[wp * 4 + 1] = (double)w1; sred[wp * 4 + 2] = (double)w2;
-        smean[0][wp] = sn; smean[1][wp] = so; smin[wp] = mm;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
-        T m = smin[0];
-        for (int w = 0; w < TX * TY / 32; ++w) {
-            a0 += sred[w * 4]; a1 += sred[w * 4 + 1]; a2 += sred[w * 4 + 2];
-            a3 += smean[0][w]; a4 += smean[1][w];
-            m = min(m, smin[w]);
+    if constexpr (std::is_same<T, float>::value) {
+        // partial row of float pairs: I_V, I_W, I_Z, sum psi^n, sum psi^{n-1}, ..., min mobility
+        float* sf = reinterpret_cast<float*>(sred);      // 8 floats per warp (sred holds 4 doubles per warp)
+        const float2 sn = sum_n.warp_pair(), so = sum_o.warp_pair();
+        if (lane == 0) {
+            sf[wp * 8 + 0] = w0; sf[wp * 8 + 1] = w1; sf[wp * 8 + 2] = w2; sf[wp * 8 + 3] = sn.x;
+            sf[wp * 8 + 4] = sn.y; sf[wp * 8 + 5] = so.x; sf[wp * 8 + 6] = so.y; sf[wp * 8 + 7] = mm;
         }
-        prow[0] = a0; prow[1] = a1; prow[2] = a2; prow[3] = a3; prow[4] = a4;
-        prow[5] = 0; prow[6] = 0; prow[7] = 0;
-        prow[8] = (double)m; prow[9] = 0;
+        __syncthreads();
+        float2* prow = reinterpret_cast<float2*>(part) + prow_i;
+        if (tid < 5) {
+            float hi = 0.f, lo = 0.f;
+            for (int w = 0; w < TX * TY / 32; ++w) {
+                if (tid < 3) df_add(hi, lo, sf[w * 8 + tid]);
+                else df_add2(hi, lo, sf[w * 8 + 3 + 2 * (tid - 3)], sf[w * 8 + 4 + 2 * (tid - 3)]);
+            }
+            prow[tid] = make_float2(hi, lo);
+        } else if (tid == 5) {
+            float m = sf[7];
+            for (int w = 1; w < TX * TY / 32; ++w) m = fminf(m, sf[w * 8 + 7]);
+            prow[5] = prow[6] = prow[7] = prow[9] = make_float2(0.f, 0.f);
+            prow[8] = make_float2(m, 0.f);
+        }
+    } else {
+        double* prow = part + prow_i;
+        const double sn = sum_n.warp_total(), so = sum_o.warp_total();
+        if (lane == 0) {
+            sred[wp * 4 + 0] = (double)w0; sred[wp * 4 + 1] = (double)w1; sred[wp * 4 + 2] = (double)w2;
+            smean[0][wp] = sn; smean[1][wp] = so; smin[wp] = mm;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+            T m = smin[0];
+            for (int w = 0; w < TX * TY / 32; ++w) {
+                a0 += sred[w * 4]; a1 += sred[w * 4 + 1]; a2 += sred[w * 4 + 2];
+                a3 += smean[0][w]; a4 += smean[1][w];
+                m = min(m, smin[w]);
+            }
+            prow[0] = a0; prow[1] = a1; prow[2] = a2; prow[3] = a3; prow[4] = a4;
+            prow[5] = 0; prow[6] = 0; prow[7] = 0;
+            prow[8] = (double)m; prow[9] = 0;
+        }
     }
 }
 
@@ -581,7 +660,7 @@ k_coldct_gram(const T* __restrict__ in, T* __restrict__ spec, double* __restrict
             gram_accumulate(acc, v, isig, itau);
         }
     }
-    block_sum_store<NRED2, T>(acc, part + (size_t)kx * NRED2, sred);
+    block_sum_store_part<NRED2, T>(acc, reinterpret_cast<typename PartialOf<T>::type*>(part) + (size_t)kx * NRED2, sred);
 }
 
 // ------------------------------------------------------------------ k_solve
@@ -622,8 +701,9 @@ __device__ __forceinline__ void solve_slice(int n, int b, int& r0, int& cnt) {
     cnt = min(n, r0 + per) - r0;
 }
 
-static __global__ void __launch_bounds__(kSolveThreads)
-k_solve(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, int nb2,
+template <typename P>
+__global__ void __launch_bounds__(kSolveThreads)
+k_solve(const P* __restrict__ p1, int nb1, const P* __restrict__ p2, int nb2,
         double* __restrict__ slices, DevScalars* sc, SolveCoef co) {
     constexpr int NR = NRQ;
     constexpr unsigned FULL = 0xffffffffu;
@@ -641,21 +721,39 @@ k_solve(const double* __restrict__ p1, int nb1, const double* __restrict__ p2, i
     if (warp == 0 && lane < NR) {
         const int c = lane;
         const bool in1 = c < NRED1;
-        const double* col = in1 ? p1 + c : p2 + (c - NRED1);
+        const P* col = in1 ? p1 + c : p2 + (c - NRED1);
         const int stride = in1 ? NRED1 : NRED2;
         int r0, cnt;
         solve_slice(in1 ? nb1 : nb2, blockIdx.x, r0, cnt);
         double acc = 0.0;
         long long kmin = 0x7fffffffffffffffLL;
-        for (int r = 0; r < cnt; r += 8) {
-            double v[8];
+        if constexpr (std::is_same<P, float2>::value) {
+            // FP32 path: float pairs added in double-float, one conversion per column
+            float hi = 0.f, lo = 0.f, fm = 3.0e38f;
+            for (int r = 0; r < cnt; r += 8) {
+                float2 v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) v[u] = (r + u < cnt) ? col[(size_t)(r0 + r + u) * stride] : 0.0;
+                for (int u = 0; u < 8; ++u) v[u] = (r + u < cnt) ? col[(size_t)(r0 + r + u) * stride] : make_float2(0.f, 0.f);
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                if (r + u >= cnt) break;
-                if (c == kSolveMinCol) kmin = min(kmin, order_key(v[u]));
-                else acc += v[u];
+                for (int u = 0; u < 8; ++u) {
+                    if (r + u >= cnt) break;
+                    if (c == kSolveMinCol) fm = fminf(fm, v[u].x);
+                    else df_add2(hi, lo, v[u].x, v[u].y);
+                }
+            }
+            if (c == kSolveMinCol) kmin = order_key((double)fm);
+            else acc = (double)hi + (double)lo;
+        } else {
+            for (int r = 0; r < cnt; r += 8) {
+                double v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) v[u] = (r + u < cnt) ? col[(size_t)(r0 + r + u) * stride] : 0.0;
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    if (r + u >= cnt) break;
+                    if (c == kSolveMinCol) kmin = min(kmin, order_key(v[u]));
+                    else acc += v[u];
+                }
             }
         }
         slices[(size_t)blockIdx.x * NR + c] = (c == kSolveMinCol) ? __longlong_as_double(kmin) : acc;

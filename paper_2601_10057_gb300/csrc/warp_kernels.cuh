@@ -164,7 +164,7 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
             *reinterpret_cast<float4*>(dst + (size_t)(g < 5 ? g : g - 1) * SpecRow<M>::FS) = o;
         }
     }
-    block_sum_store<NRED2, float>(acc, part + (size_t)blockIdx.x * NRED2, sred);
+    block_sum_store_part<NRED2, float>(acc, reinterpret_cast<float2*>(part) + (size_t)blockIdx.x * NRED2, sred);
 }
 
 // ------------------------------------------------------------------ kw_comb_icolT
