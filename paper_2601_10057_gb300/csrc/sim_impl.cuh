@@ -82,6 +82,7 @@ public:
     int nbd = 0;
     // CUDA graphs of three BDF2 steps, one per phase of the three-level rotation
     cudaGraphExec_t gexec[3] = {nullptr, nullptr, nullptr};
+    cudaGraphExec_t gexec1[3] = {nullptr, nullptr, nullptr};   // one BDF2 step per phase
     bool own_stream = false;
     bool graphs_failed = false;
     // tracing: event marks between the kernels of traced steps
@@ -96,6 +97,7 @@ public:
         if (st) cudaStreamSynchronize(st); else cudaDeviceSynchronize();
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         for (int i = 0; i < 3; ++i) if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
+        for (int i = 0; i < 3; ++i) if (gexec1[i]) cudaGraphExecDestroy(gexec1[i]);
         release();
         if (own_stream && st) cudaStreamDestroy(st);
     }
@@ -131,6 +133,23 @@ public:
         const cudaError_t e2 = cudaGraphInstantiate(&gexec[ph], g, 0);
         cudaGraphDestroy(g);
         if (e2 != cudaSuccess) { gexec[ph] = nullptr; return CCMSAV_ECUDA; }
+        return CCMSAV_OK;
+    }
+
+    // One BDF2 step from the current phase into gexec1[phase] (nothing
+    // executes while capturing: counters and the level rotation are restored).
+    int capture_single() {
+        const int ph = cur, c0 = cur, p0 = prev, s0r = spare;
+        const long long s0 = steps_taken, l0 = nlaunch;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CCMSAV_ECUDA;
+        const int r = queue_one_step();
+        const cudaError_t e = cudaStreamEndCapture(st, &g);
+        steps_taken = s0; nlaunch = l0; cur = c0; prev = p0; spare = s0r;
+        if (r != CCMSAV_OK || e != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); return CCMSAV_ECUDA; }
+        const cudaError_t e2 = cudaGraphInstantiate(&gexec1[ph], g, 0);
+        cudaGraphDestroy(g);
+        if (e2 != cudaSuccess) { gexec1[ph] = nullptr; return CCMSAV_ECUDA; }
         return CCMSAV_OK;
     }
 
@@ -629,6 +648,18 @@ public:
             steps_taken += 3;
             nlaunch += 3 * per_step;
             nsteps -= 3;
+        }
+        // the remaining one or two steps from single-step graphs (one launch
+        // each instead of six; step-at-a-time callers take this path)
+        while (nsteps > 0 && !graphs_failed) {
+            const int ph = cur;
+            if (!gexec1[ph] && capture_single() != CCMSAV_OK) { graphs_failed = true; break; }
+            CCM_CUDA(cudaGraphLaunch(gexec1[ph], st));
+            const int nw = spare;
+            spare = prev; prev = cur; cur = nw;
+            steps_taken += 1;
+            nlaunch += per_step;
+            --nsteps;
         }
         while (nsteps-- > 0)
             if ((r = queue_one_step())) return r;
