@@ -667,8 +667,9 @@ public:
     }
 
     int device_status() override {
+        // one wait: the copy into the pinned mirror is ordered after the queued steps
+        CCM_CUDA(cudaMemcpyAsync(sc_host, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
         CCM_CUDA(cudaStreamSynchronize(st));
-        CCM_CUDA(cudaMemcpy(sc_host, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost));
         if (sc_host->status != 0) { poisoned = true; return sc_host->status; }
         return CCMSAV_OK;
     }

@@ -309,3 +309,24 @@ def test_fp32_warp_path_N4096_against_fp64():
     e = (rel(out["fp32"][0], out["fp64"][0]), rel(out["fp32"][1], out["fp64"][1]))
     print("fp32 N=4096 vs fp64", e)
     assert max(e) < 5e-6, e
+
+
+def test_largest_grid_N8192_fp32_against_fp64():
+    """The largest grid the library takes (N = 8192, sixteen vesicles): two
+    steps of the FP32 path against the FP64 path (bound 5e-6 of the
+    max-norm) and the FP32 stored mass against the initial mass."""
+    w = I.workload("lattice16", N=8192)
+    m0 = float(np.sum(w.psi0)) * (w.params.L / w.N) ** 2
+    out = {}
+    for prec in ("fp64", "fp32"):
+        sim = cc.Simulation(w.params, w.N, precision=prec)
+        sim.set_state(w.phi0, w.psi0)
+        sim.step(2)
+        sim.sync()
+        out[prec] = (*sim.state(), sim.mass())
+        sim.close()
+    e = (rel(out["fp32"][0], out["fp64"][0]), rel(out["fp32"][1], out["fp64"][1]))
+    drift = abs(out["fp32"][2] - m0) / m0
+    print("fp32 N=8192 vs fp64", e, "mass drift", drift)
+    assert max(e) < 5e-6, e
+    assert drift < 5e-11, drift
