@@ -471,6 +471,51 @@ def test_temporal_convergence_second_order():
     assert all(1.8 < r < 2.5 for r in rates), rates
 
 
+def _restrict_to_coarse(u):
+    """Fine grid (2N cells) to coarse (N): a coarse centre is the midpoint of
+    fine centres 2I and 2I+1; 4-point Lagrange weights (-1, 9, 9, -1)/16 per
+    axis (exact for cubics), mirrored ghosts at the walls (Neumann)."""
+    def along(v, axis):
+        v = np.moveaxis(v, axis, 0)
+        g = np.concatenate([v[:1], v, v[-1:]], axis=0)
+        i = np.arange(0, v.shape[0], 2)
+        return np.moveaxis((-g[i] + 9 * g[i + 1] + 9 * g[i + 2] - g[i + 3]) / 16.0, 0, axis)
+    return along(along(u, 0), 1)
+
+
+def test_refinement_path_second_order():
+    """P5 (space and time): along the refinement path dt ~ h (N = 16 .. 128,
+    dt halved with h, fixed final time) the difference to the next finer
+    grid falls about 4x per level in both fields, as the paper reports
+    (rates 1.83-2.53).  A smooth ellipse with a wide interface (eps = 0.8);
+    moderate osmotic, area and diffusion coefficients (100, 50, 100): with
+    the table's 1e5 values the transients are far faster than this path's
+    steps.  A wrong stencil weight or a dropped spatial term breaks the rate."""
+    L, eps, T = 2 * math.pi, 0.8, 5e-3
+    sols = {}
+    for N in (16, 32, 64, 128):
+        h = L / N
+        c = (np.arange(N) + 0.5) * h
+        X, Y = np.meshgrid(c, c, indexing="xy")
+        r2 = ((X - math.pi) / 1.3) ** 2 + ((Y - math.pi) / 0.9) ** 2
+        phi0 = np.tanh((2.2 - r2) / (math.sqrt(2) * eps))
+        psi0 = -0.1 * phi0 + 0.7
+        nst = N // 2
+        p = I.shrinkage_params(eps=eps, dt=T / nst, L=L, gamma_in=100.0, gamma_out=100.0,
+                               lam=100.0, gamma_area=50.0)
+        m = O.Model.from_params(N, p)
+        s = O.run(O.initial_state(phi0, psi0, m), m, nst)
+        sols[N] = (s.phi, s.psi, m)
+    rates = {}
+    for f in (0, 1):
+        e = []
+        for N in (16, 32, 64):
+            d = sols[N][f] - _restrict_to_coarse(sols[2 * N][f])
+            e.append(math.sqrt(O.ip(d, d, sols[N][2].h)))
+        rates[f] = [math.log2(e[k] / e[k + 1]) for k in range(2)]
+    assert all(1.8 < r < 2.5 for r in rates[0] + rates[1]), rates
+
+
 def test_parameter_table_golden():
     gold = json.load(open(os.path.join(GOLDEN, "parameter_table.json")))
     for col, mk in (("growth", I.growth_params), ("shrinkage", I.shrinkage_params)):
