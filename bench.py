@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--dct-sweep", action="store_true",
+                    help="only the sweep over N of the line-transform kernels (warp path) and of the "
+                         "step with the warp-FFT against the block-FFT kernels; one JSON line")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the secondary workloads (batch of 64, N=4096, N=8192)")
     return ap.parse_args()
@@ -260,6 +263,63 @@ def extra_workloads(sh, stream):
     return res
 
 
+ALG_BYTES_FP32 = {"k_rowdct_T": 64, "k_coldct_gram": 60, "k_comb_icolT": 36, "k_irow": 32}
+
+
+def dct_sweep():
+    """Per N (128 .. 4096, FP32): the line-transform kernels' event times and
+    algorithmic GB/s on the warp-FFT path, and the step time with the
+    warp-FFT kernels against the block-FFT kernels (the library takes the
+    warp path wherever it exists)."""
+    import torch
+    from paper_2601_10057_gb300 import build as B
+    from paper_2601_10057_gb300 import ccmsav as cc
+    from paper_2601_10057_gb300 import inputs as I
+    B.build()
+    cc.load()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sh = stream.cuda_stream
+    peak, peak_kind = measured_peaks()
+    rows = []
+    for N in (128, 256, 512, 1024, 2048, 4096):
+        w = I.three_vesicles(N=N) if N >= 1024 else I.workload("ellipse_shrink", N=N)
+        k = 300 if N <= 512 else (100 if N <= 2048 else 30)
+        rec = {"N": N, "steps": k}
+        for path in ("warp", "block"):
+            os.environ["CCMSAV_FORCE_BLOCK_FFT"] = "1" if path == "block" else "0"
+            sim = cc.Simulation(w.params, N, precision="fp32", stream=sh)
+            sim.set_state(w.phi0, w.psi0)
+            sim.step(6)
+            sim.sync()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            sim.step(k)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            sim.sync()
+            rec[path + "_ms_per_step"] = round(e0.elapsed_time(e1) / k, 5)
+            if path == "warp":
+                cc.ccmsav_profile(sim.h, True)
+                sim.step(min(k, 60))
+                _, ms, nst = cc.ccmsav_profile_read(sim.h, 0)
+                cc.ccmsav_profile(sim.h, False)
+                sim.sync()
+                kern = {}
+                for i, name in enumerate(cc.KERNEL_NAMES):
+                    if name in ALG_BYTES_FP32 and nst:
+                        t = ms[i] / nst
+                        gbs = ALG_BYTES_FP32[name] * N * N / (t * 1e-3) / 1e9
+                        kern[name] = {"us": round(1e3 * t, 2), "alg_GBps": round(gbs, 1), "frac": round(gbs / peak, 3)}
+                rec["transforms"] = kern
+            sim.close()
+        rec["warp_speedup"] = round(rec["block_ms_per_step"] / rec["warp_ms_per_step"], 2)
+        rows.append(rec)
+    os.environ.pop("CCMSAV_FORCE_BLOCK_FFT", None)
+    print(json.dumps({"dct_sweep": rows, "peak_GBps": peak, "peak_kind": peak_kind, "precision": "fp32",
+                      "workloads": "ellipse_shrink (N <= 512), three_vesicles (N >= 1024)"}), flush=True)
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -405,7 +465,10 @@ def run_ours(args, world, rank, local):
 def main():
     args = parse()
     world, rank, local = dist_setup(args)
-    if args.impl == "reference":
+    if args.dct_sweep:
+        if rank == 0:
+            dct_sweep()
+    elif args.impl == "reference":
         run_reference(args, world, rank)
     else:
         run_ours(args, world, rank, local)

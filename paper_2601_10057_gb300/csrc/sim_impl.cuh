@@ -415,7 +415,7 @@ public:
         kw_comb_icolT<MM><<<N / wRT4, kWarps * 32, wsm_comb, st>>>(reinterpret_cast<const float*>(bufA),
             reinterpret_cast<float*>(bufB), tw2, twI, evf, evp, sf, sc, anchor);
         mark(4);
-        kw_irow<MM><<<(2 * N + InvGeo<MM>::LINES - 1) / InvGeo<MM>::LINES, kWarpsInv * 32, wsm_irow, st>>>(
+        kw_irow<MM><<<(2 * N + InvGeo<MM>::LINES - 1) / InvGeo<MM>::LINES, InvGeo<MM>::WARPS * 32, wsm_irow, st>>>(
             reinterpret_cast<const float*>(bufB),
             reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), tw2, twI,
             reinterpret_cast<const float*>(phi[cur]), reinterpret_cast<const float*>(phi[prev]),

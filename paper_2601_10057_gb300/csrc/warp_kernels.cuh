@@ -274,22 +274,31 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
 }
 
 // ------------------------------------------------------------------ kw_irow
-// kWarpsInv * LPW lines per CTA, line = 2 y + field (phi, psi of row y), so
+// InvGeo<M>::LINES lines per CTA, line = 2 y + field (phi, psi of row y), so
 // that 3 CTAs per SM hold every line of an N = 2048 field at once (one round,
 // no tail).  Phase 1 (all threads): pre-process the transposed rows into
 // the line buffers; phase 2 (per line): inverse four-step FFT, then
 // u^{n+1} = u_bar + du with the compensated (and, for psi on the FP32 path,
 // error-feedback and mass-anchored) final rounding.
-constexpr int kWarpsInv = 9;
+// Warps per CTA of the inverse row kernel: 9 at M = 1024 (3 CTAs of 9 lines
+// per SM hold all 4096 lines of N = 2048: one round); 4 at M = 2048 (3 CTAs
+// per SM); fewer at small M so that the grid still has >= 128 CTAs.
+template <int M> __host__ __device__ constexpr int inv_warps() {
+    return M == 1024 ? 9 : M >= 2048 ? 4 : M == 512 ? 4 : M == 256 ? 2 : 1;
+}
+template <int M> __host__ __device__ constexpr int inv_min_ctas() {
+    return M == 1024 || M >= 2048 ? 3 : 4;
+}
 
 template <int M> struct InvGeo {
-    static constexpr int LINES = kWarpsInv * WGeo<M>::LPW;     // lines per CTA
+    static constexpr int WARPS = inv_warps<M>();
+    static constexpr int LINES = WARPS * WGeo<M>::LPW;          // lines per CTA
     static constexpr int BUF = wf::buf_len<M, true>();         // unpadded, swizzled transpose
     static constexpr size_t smem_bytes() { return (size_t)LINES * BUF * sizeof(cplx<float>); }
 };
 
 template <int M>
-__global__ void __launch_bounds__(kWarpsInv * 32, M <= 1024 ? 3 : 1)
+__global__ void __launch_bounds__(inv_warps<M>() * 32, inv_min_ctas<M>())
 kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __restrict__ psi_new,
         const cplx<float>* __restrict__ tw2, const wf::PairTw* __restrict__ twI,
         const float* __restrict__ phn, const float* __restrict__ pho,
