@@ -153,6 +153,17 @@ int ccmsav_mass(ccmsav_t* h, int sim, double* mass);
 int ccmsav_get_aux(ccmsav_t* h, int sim, double aux[12]);
 int ccmsav_set_aux(ccmsav_t* h, int sim, const double aux[12]);
 
+/* The same twelve scalars copied to the caller's host buffer asynchronously:
+ * the copy is queued on the simulation's stream behind the steps queued so
+ * far, and the call returns at once.  `aux` must stay valid until that copy
+ * has run (ccmsav_sync, or any synchronising call); with page-locked memory
+ * the copy overlaps the following steps.  aux[10] is the device's own count
+ * of steps (it equals get_aux's after set_state, or after set_aux).  The
+ * device status is not checked here: ccmsav_sync reports a device error.
+ * Lets a caller read every step's scalars without stalling the GPU between
+ * steps.  Returns CCMSAV_ESTATE before set_state. */
+int ccmsav_get_aux_async(ccmsav_t* h, int sim, double aux[12]);
+
 /* Two-level field access for exact checkpoint/resume: the previous level
  * phi^{n-1}, psi^{n-1} (host FP64, N*N each). */
 int ccmsav_get_prev_state(ccmsav_t* h, int sim, double* phi_prev, double* psi_prev);

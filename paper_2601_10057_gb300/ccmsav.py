@@ -75,6 +75,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "ccmsav_energy": (i, [vp, i, _DP]),
         "ccmsav_mass": (i, [vp, i, _DP]),
         "ccmsav_get_aux": (i, [vp, i, _DP]),
+        "ccmsav_get_aux_async": (i, [vp, i, _DP]),
         "ccmsav_set_aux": (i, [vp, i, _DP]),
         "ccmsav_grid_size": (i, [vp, i]),
         "ccmsav_launch_count": (C.c_longlong, [vp]),
@@ -171,6 +172,15 @@ def ccmsav_get_aux(h, sim: int):
     return st, out
 
 
+def ccmsav_get_aux_async(h, sim: int, out: np.ndarray) -> int:
+    """Queue the copy of the twelve scalars into ``out`` (float64, 12 values,
+    C-contiguous; ideally page-locked).  ``out`` must stay alive and is valid
+    only after a synchronising call."""
+    if out.dtype != np.float64 or out.size < 12 or not out.flags.c_contiguous:
+        raise ValueError("out must be a C-contiguous float64 array of 12 values")
+    return load().ccmsav_get_aux_async(h, sim, _ptr(out))
+
+
 def ccmsav_set_aux(h, sim: int, aux) -> int:
     aux = _f64(aux)
     return load().ccmsav_set_aux(h, sim, _ptr(aux))
@@ -265,6 +275,10 @@ class Simulation:
         st, a = ccmsav_get_aux(self.h, sim)
         self._check(st, "ccmsav_get_aux")
         return a
+
+    def aux_async(self, out: np.ndarray, sim: int = 0):
+        """Queue the scalars' copy into ``out`` (see ccmsav_get_aux_async)."""
+        self._check(ccmsav_get_aux_async(self.h, sim, out), "ccmsav_get_aux_async")
 
     def set_aux(self, aux, sim: int = 0):
         self._check(ccmsav_set_aux(self.h, sim, aux), "ccmsav_set_aux")

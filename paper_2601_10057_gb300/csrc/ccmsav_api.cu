@@ -227,6 +227,12 @@ int ccmsav_get_aux(ccmsav_t* h, int sim, double aux[12]) {
     return s->get_aux(aux);
 }
 
+int ccmsav_get_aux_async(ccmsav_t* h, int sim, double aux[12]) {
+    ccm::SimBase* s = get(h, sim);
+    if (!s || !aux) return CCMSAV_EINVAL;
+    return s->get_aux_async(aux);
+}
+
 int ccmsav_set_aux(ccmsav_t* h, int sim, const double aux[12]) {
     ccm::SimBase* s = get(h, sim);
     if (!s || !aux) return CCMSAV_EINVAL;

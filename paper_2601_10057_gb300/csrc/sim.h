@@ -18,6 +18,7 @@ public:
     virtual int energy(double out[8]) = 0;
     virtual int mass(double* m) = 0;
     virtual int get_aux(double aux[12]) = 0;
+    virtual int get_aux_async(double aux[12]) = 0;   // queued copy, no wait
     virtual int set_aux(const double aux[12]) = 0;
     virtual int device_status() = 0;      // synchronises the stream
     virtual bool has_state() const = 0;

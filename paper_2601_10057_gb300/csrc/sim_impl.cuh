@@ -17,6 +17,7 @@
 #include <cmath>
 #include <cstdlib>
 #include <cstring>
+#include <cstddef>
 #include <vector>
 #include "sim.h"
 #include "diag_kernels.cuh"
@@ -740,6 +741,14 @@ public:
         aux[4] = q.Vo; aux[5] = q.Uo; aux[6] = q.Wo; aux[7] = q.Zo;
         aux[8] = q.A; aux[9] = q.lamsum; aux[10] = (double)steps_taken; aux[11] = q.mass_mode;
         return r;
+    }
+
+    // the first twelve doubles of DevScalars are aux[0..11] in order
+    int get_aux_async(double aux[12]) override {
+        static_assert(offsetof(DevScalars, mass_mode) == 11 * sizeof(double), "aux layout");
+        if (!have_state) return CCMSAV_ESTATE;
+        CCM_CUDA(cudaMemcpyAsync(aux, sc, 12 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        return CCMSAV_OK;
     }
 
     int set_aux(const double aux[12]) override {

@@ -330,3 +330,20 @@ def test_largest_grid_N8192_fp32_against_fp64():
     print("fp32 N=8192 vs fp64", e, "mass drift", drift)
     assert max(e) < 5e-6, e
     assert drift < 5e-11, drift
+
+
+def test_async_aux_matches_synchronous_read():
+    """ccmsav_get_aux_async queues a copy of the twelve scalars behind the
+    queued steps: after a sync the buffers hold each step's values, equal
+    to ccmsav_get_aux at that point."""
+    w = I.workload("one_vesicle", N=64, dt=1e-5)
+    sim = cc.Simulation(w.params, w.N, precision="fp32")
+    sim.set_state(w.phi0, w.psi0)
+    bufs = np.zeros((5, 12), np.float64)
+    for k in range(5):
+        sim.step(1)
+        sim.aux_async(bufs[k])
+    sim.sync()
+    assert [int(b[10]) for b in bufs] == [1, 2, 3, 4, 5]
+    assert np.array_equal(bufs[-1], sim.aux())
+    sim.close()
