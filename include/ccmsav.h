@@ -184,7 +184,7 @@ long long ccmsav_launch_count(ccmsav_t* h);
  *   [2] forward column DCT + Gram sums   [3] 5x5 solve + SAV update
  *   [4] recovery + inverse column DCT    [5] inverse row DCT
  *   [6] lambda-sum reduction (CCMSAV_TRACK_ENERGY only)
- *   [7] first-level reduction of the per-block partial sums
+ *   [7] unused (0)
  * and in *nsteps the number of steps traced; it then resets the counters. */
 int ccmsav_profile(ccmsav_t* h, int enable);
 int ccmsav_profile_read(ccmsav_t* h, int sim, double ms[8], long long* nsteps);

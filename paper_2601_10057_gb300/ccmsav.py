@@ -199,7 +199,7 @@ def ccmsav_profile(h, enable: bool) -> int:
 
 
 KERNEL_NAMES = ["k_stencil", "k_rowdct_T", "k_coldct_gram", "k_solve", "k_comb_icolT",
-                "k_irow", "k_dnorm+k_add_lamsum", "k_reduce_rows"]
+                "k_irow", "k_dnorm+k_add_lamsum", "unused"]
 
 
 def ccmsav_profile_read(h, sim: int = 0):
