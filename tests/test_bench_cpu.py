@@ -1,6 +1,6 @@
 """bench.py's reference arm (the FP64 CPU oracle on the host cores) prints one
-JSON line with the keys the measurement contract names; run on a small grid
-so that it takes seconds."""
+JSON line with the keys the measurement contract names; run on the smallest
+grid the three-vesicle workload fits (N = 256), so that it takes seconds."""
 import json
 import os
 import subprocess
@@ -10,7 +10,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_reference_arm_json_line():
-    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--N", "64",
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--N", "256",
                         "--steps", "2", "--warmup", "1"], capture_output=True, text=True, timeout=300, cwd=ROOT)
     assert r.returncode == 0, r.stderr[-2000:]
     line = json.loads(r.stdout.strip().splitlines()[-1])
@@ -20,4 +20,4 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["value"] > 0 and line["higher_is_better"] is True
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["unit"] == line["unit"]
-    assert line["config"]["workload"] == "three_vesicles_N64"
+    assert line["config"]["workload"] == "three_vesicles_N256"
