@@ -23,13 +23,17 @@ constexpr int kWarps = 8;
 
 
 
-// Pair-ordered spectra of the warp path: row kx of a field holds, for each
-// pair k = 0 .. M/2, the float4 of modes (k, N-k, M-k, M+k); rows of
-// RS = 4 (M/2 + 1) = N + 4 floats (16-byte aligned), fields of FS = N RS
-// floats, the 7 stored fields (f0', S, H, Q, K, g0', L_P) packed.
+// Pair-ordered spectra of the warp path: for each spectral row kx and each
+// of the 7 stored fields (f0', S, H, Q, K, g0', L_P), the float4 of modes
+// (k, N-k, M-k, M+k) for each pair k = 0 .. M/2, i.e. a row of
+// RS = 4 (M/2 + 1) = N + 4 floats (16-byte aligned).  The layout is kx-major:
+// the 7 field rows of one kx are contiguous (stride KS = 7 RS), so the
+// recovery kernel reads each CTA's rows as one contiguous block and the
+// column kernel writes each kx as one.
 template <int M> struct SpecRow {
     static constexpr int RS = 4 * (M / 2 + 1);
-    static constexpr size_t FS = (size_t)(2 * M) * RS;
+    static constexpr size_t FO = (size_t)RS;          // next field, same kx
+    static constexpr size_t KS = (size_t)7 * RS;      // next kx
 };
 
 template <int M> struct WGeo {
@@ -154,14 +158,14 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
         // spectra in pair order: slot u of pair k holds mode k, N-k, M-k, M+k
         // (k = 0: no mode N, slot 3 repeats mode M; k = M/2: slots 2, 3 repeat
         // modes M/2, 3M/2), one float4 per field
-        float* dst = spec + (size_t)kx * SpecRow<M>::RS + 4 * k;
+        float* dst = spec + (size_t)kx * SpecRow<M>::KS + 4 * k;
 #pragma unroll
         for (int g = 0; g < NF; ++g) {
             if (g == 5) continue;
             float4 o = make_float4(X[g].xk, k == 0 ? 0.f : X[g].xNk, X[g].xMk, X[g].xMpk);
             if (k == 0) o.w = o.z;
             if (k == M / 2) { o.z = o.x; o.w = o.y; }
-            *reinterpret_cast<float4*>(dst + (size_t)(g < 5 ? g : g - 1) * SpecRow<M>::FS) = o;
+            *reinterpret_cast<float4*>(dst + (size_t)(g < 5 ? g : g - 1) * SpecRow<M>::FO) = o;
         }
     }
     block_sum_store_part<NRED2, float>(acc, reinterpret_cast<float2*>(part) + (size_t)blockIdx.x * NRED2, sred);
@@ -197,8 +201,8 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
         const int kx = kx0 + r;
         const float evx = evf[kx];
         const float4 e4 = evp[k];
-        const float* src = spec + (size_t)kx * SpecRow<M>::RS + 4 * k;
-        constexpr size_t FS = SpecRow<M>::FS;
+        const float* src = spec + (size_t)kx * SpecRow<M>::KS + 4 * k;
+        constexpr size_t FS = SpecRow<M>::FO;
         const float4 f0 = __ldg(reinterpret_cast<const float4*>(src));
         const float4 f1 = __ldg(reinterpret_cast<const float4*>(src + FS));
         const float4 f2 = __ldg(reinterpret_cast<const float4*>(src + 2 * FS));
