@@ -358,40 +358,80 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
     // u_bar = u^n + d/3, u_bar - u* = -2d/3 (BDF1: u* = u_bar = u^n)
     const T kst = c.bdf1 ? (T)0 : (T)1, kbar = c.bdf1 ? (T)0 : (T)(1.0 / 3.0), kq = c.bdf1 ? (T)0 : (T)(-2.0 / 3.0);
     const T ih = c.inv_h, ih2 = c.inv_h2;
-    for (int q = tid; q < (TX + 4) * (TYB + 4); q += TX * TY) {
-        const int lj = q / W2, li = q % W2;
-        const int gi = reflect(i0 + li - 2, N), gj = reflect(j0 + lj - 2, N);
-        const size_t g = (size_t)gj * N + gi;
-        const T a = phn[g], da = a - pho[g];
-        sbar[lj * W2 + li] = a + kbar * da;
-        if (lj >= 1 && lj <= TYB + 2 && li >= 1 && li <= TX + 2) {
-            const int o = (lj - 1) * W1 + (li - 1);
-            const T ph = a + kst * da;
-            const T u = psn[g], du = u - pso[g];
-            const T ps = u + kst * du;
-            sph[o] = ph;
-            sps[o] = ps;
-            sdq[o] = kq * du;
-            T sp, cp;
-            sincospi_<T>((T)0.5 * ph, &sp, &cp);
-            sP[o] = (T)0.5 * (c.gin * ((T)1 + sp) * (ps - c.psin) + c.gout * ((T)1 - sp) * (ps - c.psout));
+    const size_t NN = (size_t)N * N;
+    ExactSum<T> sum_n, sum_o;
+    // Halo load: the global loads of NB cells are issued before any of them
+    // is used.  The sums of psi^n and psi^{n-1} over the block's own cells
+    // are taken here, from the loaded values.
+    {
+        constexpr int NCELL = (TX + 4) * (TYB + 4), NT = TX * TY, NB = 5;
+#pragma unroll
+        for (int q0 = 0; q0 < NCELL; q0 += NB * NT) {
+            T ra[NB], rb[NB], rc[NB], rd[NB];
+#pragma unroll
+            for (int u = 0; u < NB; ++u) {
+                const int q = q0 + u * NT + tid;
+                ra[u] = rb[u] = rc[u] = rd[u] = (T)0;
+                if (q < NCELL) {
+                    const int lj = q / W2, li = q % W2;
+                    const size_t g = (size_t)reflect(j0 + lj - 2, N) * N + reflect(i0 + li - 2, N);
+                    ra[u] = phn[g];
+                    rb[u] = pho[g];
+                    if (lj >= 1 && lj <= TYB + 2 && li >= 1 && li <= TX + 2) {
+                        rc[u] = psn[g];
+                        rd[u] = pso[g];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < NB; ++u) {
+                const int q = q0 + u * NT + tid;
+                if (q < NCELL) {
+                    const int lj = q / W2, li = q % W2;
+                    const T a = ra[u], da = a - rb[u];
+                    sbar[lj * W2 + li] = a + kbar * da;
+                    if (lj >= 1 && lj <= TYB + 2 && li >= 1 && li <= TX + 2) {
+                        const int o = (lj - 1) * W1 + (li - 1);
+                        const T du = rc[u] - rd[u];
+                        sph[o] = a + kst * da;
+                        sps[o] = rc[u] + kst * du;
+                        sdq[o] = kq * du;
+                        if (lj >= 2 && lj <= TYB + 1 && li >= 2 && li <= TX + 1
+                            && i0 + li - 2 < N && j0 + lj - 2 < N) {
+                            sum_n.add(rc[u]);
+                            sum_o.add(rd[u]);
+                        }
+                    }
+                }
+            }
         }
     }
     __syncthreads();
-    // Lap phi_bar on the one-cell-halo region (sums of neighbour differences:
-    // each difference of nearby values is exact, so the rounding is relative
-    // to the Laplacian, not to the field)
+    // One-halo region: Lap phi_bar (sums of neighbour differences: each
+    // difference of nearby values is exact, so the rounding is relative to
+    // the Laplacian, not to the field), p(phi*) = sin(pi phi*/2) once per
+    // cell, the P numerator, and on the block's own cells K and the I_Z term.
+    T acc2 = 0;
     for (int q = tid; q < W1 * H1; q += TX * TY) {
-        const int lj = q / W1 + 1, li = q % W1 + 1;
-        const T* b = sbar + lj * W2 + li;
+        const int lj1 = q / W1, li1 = q % W1;
+        const T* b = sbar + (lj1 + 1) * W2 + li1 + 1;
         const T C = b[0];
         slb[q] = (((b[1] - C) + (b[-1] - C)) + ((b[W2] - C) + (b[-W2] - C))) * ih2;
+        const T ph = sph[q], ps = sps[q];
+        T sp, cp;
+        sincospi_<T>((T)0.5 * ph, &sp, &cp);
+        sP[q] = (T)0.5 * (c.gin * ((T)1 + sp) * (ps - c.psin) + c.gout * ((T)1 - sp) * (ps - c.psout));
+        const int gi = i0 + li1 - 1, gj = j0 + lj1 - 1;
+        if (lj1 >= 1 && lj1 <= TYB && li1 >= 1 && li1 <= TX && gi < N && gj < N) {
+            const T fin = c.hgin * (ps - c.psin) * (ps - c.psin) + c.bin;
+            const T fout = c.hgout * (ps - c.psout) * (ps - c.psout) + c.bout;
+            out[4 * NN + (size_t)gj * N + gi] = (T)0.5 * ((T)1.5707963267948966192 * cp) * (fin - fout);
+            acc2 += ((T)1 + sp) * fin + ((T)1 - sp) * fout;
+        }
     }
     __syncthreads();
-    T acc0 = 0, acc1 = 0, acc2 = 0;
+    T acc0 = 0, acc1 = 0;
     T mm = (T)1e30;
-    ExactSum<T> sum_n, sum_o;
-    const size_t NN = (size_t)N * N;
     const int gi = i0 + threadIdx.x;
     const int li = threadIdx.x + 1;
     for (int jj = threadIdx.y; jj < TYB; jj += TY) {
@@ -400,7 +440,6 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
         const size_t g = inside ? (size_t)gj * N + gi : 0;
         const int o = lj * W1 + li;
         const T pC = sph[o], pE = sph[o + 1], pW = sph[o - 1], pN = sph[o + W1], pS = sph[o - W1];
-        const T qC = sps[o];
         const T lapp = (((pE - pC) + (pW - pC)) + ((pN - pC) + (pS - pC))) * ih2;
         const T dC = sdq[o];
         const T lapd = (((sdq[o + 1] - dC) + (sdq[o - 1] - dC)) + ((sdq[o + W1] - dC) + (sdq[o - W1] - dC))) * ih2;
@@ -415,12 +454,6 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
         const T Snum = pC * (p2 - (T)1 - c.beta) * c.inv_eps;
         const T Hv = (T)1.0606601717798212866 * (p3m * c.inv_eps - c.eps * lapp);   // 3 sqrt2 / 4
         const T Qnum = (T)6 * (pC * gbar - divp2g) + p3m * ((T)3 * p2 - (T)1) * c.inv_eps2;
-        T sp, cp;
-        sincospi_<T>((T)0.5 * pC, &sp, &cp);
-        const T dp = (T)1.5707963267948966192 * cp;
-        const T fin = c.hgin * (qC - c.psin) * (qC - c.psin) + c.bin;
-        const T fout = c.hgout * (qC - c.psout) * (qC - c.psout) + c.bout;
-        const T Knum = (T)0.5 * dp * (fin - fout);
         const T PC = sP[o];
         // face mobilities M(A phi*) and the flux divergence of P
         auto mob = [&](T a) { T s = a * a - (T)1; return (T)1 - c.M0 * s * s; };
@@ -436,22 +469,17 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
             out[1 * NN + g] = Snum;
             out[2 * NN + g] = Hv;
             out[3 * NN + g] = Qnum;
-            out[4 * NN + g] = Knum;
             out[5 * NN + g] = PC;
             out[6 * NN + g] = g0;
             out[7 * NN + g] = LP;
             const T vv = p2 - (T)1 - c.beta;
             acc0 += vv * vv * c.quarter_inv_eps;
             acc1 += (T)6 * p2 * gbar + p3m * p3m * c.inv_eps2;
-            acc2 += ((T)1 + sp) * fin + ((T)1 - sp) * fout;
-            // minimum face mobility over interior faces (boundary faces carry no flux)
+            // minimum face mobility over interior faces: each interior face
+            // is the east or north face of exactly one cell (boundary faces
+            // carry no flux)
             if (gi + 1 < N) mm = min(mm, mE);
-            if (gi > 0) mm = min(mm, mW);
             if (gj + 1 < N) mm = min(mm, mN);
-            if (gj > 0) mm = min(mm, mS);
-            // sums of psi^n and psi^{n-1} to ~1e-13 (mass bookkeeping of the FP32 path)
-            sum_n.add(psn[g]);
-            sum_o.add(pso[g]);
         }
     }
     const size_t prow_i = (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * NRED1;
