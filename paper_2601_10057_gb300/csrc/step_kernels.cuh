@@ -331,10 +331,10 @@ __device__ __forceinline__ double bar_add(double a, double b, double du, double 
 // ------------------------------------------------------------------ k_stencil
 // Tile of TX x TYB cells per block of TX x TY threads (each thread handles
 // TYB / TY cells of one column).  Shared-memory tiles: phi_bar with a
-// two-cell halo (for Lap^2 phi_bar), and phi*, psi*, the P numerator,
-// psi_bar - psi* and Lap phi_bar with a one-cell halo.  Partial sums are
+// two-cell halo (for Lap^2 phi_bar), and phi*, psi* (overwritten in place by
+// the P numerator), psi_bar - psi* and Lap phi_bar with a one-cell halo.  Partial sums are
 // accumulated per thread over its cells, then reduced once per block.
-constexpr int TX = 32, TY = 8, TYB = 64;
+constexpr int TX = 64, TY = 4, TYB = 32;
 
 template <typename T>
 __global__ void __launch_bounds__(TX * TY)
@@ -346,8 +346,8 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
     T* sbar = reinterpret_cast<T*>(smraw);              // [TYB+4][W2]
     T* sph = sbar + (TYB + 4) * W2;                     // [H1][W1] each below
     T* sps = sph + H1 * W1;
-    T* sP = sps + H1 * W1;
-    T* sdq = sP + H1 * W1;
+    T* sP = sps;              // the P numerator replaces psi* in the one-halo pass
+    T* sdq = sps + H1 * W1;
     T* slb = sdq + H1 * W1;
     __shared__ double sred[(TX * TY / 32) * 4];
     __shared__ double smean[2][TX * TY / 32];
@@ -533,7 +533,7 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
 }
 
 template <typename T> __host__ __device__ constexpr size_t stencil_smem_bytes() {
-    return ((size_t)(TYB + 4) * (TX + 4) + 5 * (size_t)(TYB + 2) * (TX + 2)) * sizeof(T);
+    return ((size_t)(TYB + 4) * (TX + 4) + 4 * (size_t)(TYB + 2) * (TX + 2)) * sizeof(T);
 }
 
 // The pair k (0 <= k <= M/2) of the line transforms touches the modes
