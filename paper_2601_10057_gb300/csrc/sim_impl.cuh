@@ -61,8 +61,12 @@ public:
     cplx<float>* tw2 = nullptr;
     float* evf = nullptr;
     float4* evp = nullptr;   // eigenvalues in the pair order of the warp-path spectra
-    wf::PairTw* twF = nullptr;   // forward / inverse pair twiddles of the warp path
-    wf::PairTw* twI = nullptr;
+    float* twF = nullptr;        // forward / inverse pair twiddles of the warp path
+    float* twI = nullptr;        // (wf::PairTwTab layout: NP float4, then NP float2)
+    int twNP = 0;                // pairs in each table
+    wf::PairTwTab pair_tab(const float* t) const {
+        return wf::PairTwTab{reinterpret_cast<const float4*>(t), reinterpret_cast<const float2*>(t + 4 * (size_t)twNP)};
+    }
     int wRT = 8, wlds = 0, wRT4 = 4, wlds4 = 0, wKC = 1, wRI = 4;
     int ahead_rt = 0;   // L2 prefetch distance of the row kernel (its resident CTAs)
     size_t wsm_rt = 0, wsm_col = 0, wsm_comb = 0, wsm_irow = 0;
@@ -378,10 +382,22 @@ public:
             v.bx = (float)(0.5 * s1 * std::cos(q - th)); v.by = (float)(0.5 * s1 * std::sin(q - th));
             hf[k] = f; hi[k] = v;
         }
-        if (cudaMalloc(&twF, hf.size() * sizeof(wf::PairTw)) != cudaSuccess) return CCMSAV_ENOMEM;
-        if (cudaMalloc(&twI, hi.size() * sizeof(wf::PairTw)) != cudaSuccess) return CCMSAV_ENOMEM;
-        CCM_CUDA(cudaMemcpyAsync(twF, hf.data(), hf.size() * sizeof(wf::PairTw), cudaMemcpyHostToDevice, st));
-        CCM_CUDA(cudaMemcpyAsync(twI, hi.data(), hi.size() * sizeof(wf::PairTw), cudaMemcpyHostToDevice, st));
+        twNP = Mh / 2 + 1;
+        std::vector<float> pf(6 * (size_t)twNP), pi(6 * (size_t)twNP);
+        for (int k = 0; k < twNP; ++k) {
+            const wf::PairTw* src[2] = {&hf[k], &hi[k]};
+            float* dst[2] = {pf.data(), pi.data()};
+            for (int t = 0; t < 2; ++t) {
+                float* wa = dst[t] + 4 * (size_t)k;
+                float* b = dst[t] + 4 * (size_t)twNP + 2 * (size_t)k;
+                wa[0] = src[t]->wnx; wa[1] = src[t]->wny; wa[2] = src[t]->ax; wa[3] = src[t]->ay;
+                b[0] = src[t]->bx; b[1] = src[t]->by;
+            }
+        }
+        if (cudaMalloc(&twF, pf.size() * sizeof(float)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaMalloc(&twI, pi.size() * sizeof(float)) != cudaSuccess) return CCMSAV_ENOMEM;
+        CCM_CUDA(cudaMemcpyAsync(twF, pf.data(), pf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        CCM_CUDA(cudaMemcpyAsync(twI, pi.data(), pi.size() * sizeof(float), cudaMemcpyHostToDevice, st));
         CCM_CUDA(cudaStreamSynchronize(st));
         int r = CCMSAV_EINVAL;
         if constexpr (std::is_same<T, float>::value)
@@ -404,9 +420,9 @@ public:
         const float* fin = reinterpret_cast<const float*>(bufA);
         float* fB = reinterpret_cast<float*>(bufB);
         const cplx<float>* t2 = tw2;
-        kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, t2, twF, ahead_rt);
+        kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, t2, pair_tab(twF), ahead_rt);
         mark(1);
-        kw_coldct_gram<MM><<<N / wKC, kWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2, t2, twF, evf, evp, sf);
+        kw_coldct_gram<MM><<<N / wKC, kWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2, t2, pair_tab(twF), evf, evp, sf);
         mark(2);
     }
     int bdf1_launch = 0;
@@ -414,11 +430,11 @@ public:
     void launch_warp_inverse(const SpecCoef& s, int anchor) {
         SpecCoefF sf{(float)s.C1, (float)s.C2, (float)s.C3, (float)s.Ct, (float)s.lam};
         kw_comb_icolT<MM><<<N / wRT4, kWarps * 32, wsm_comb, st>>>(reinterpret_cast<const float*>(bufA),
-            reinterpret_cast<float*>(bufB), tw2, twI, evf, evp, sf, sc, anchor);
+            reinterpret_cast<float*>(bufB), tw2, pair_tab(twI), evf, evp, sf, sc, anchor);
         mark(4);
         kw_irow<MM><<<(2 * N + InvGeo<MM>::LINES - 1) / InvGeo<MM>::LINES, InvGeo<MM>::WARPS * 32, wsm_irow, st>>>(
             reinterpret_cast<const float*>(bufB),
-            reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), tw2, twI,
+            reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), tw2, pair_tab(twI),
             reinterpret_cast<const float*>(phi[cur]), reinterpret_cast<const float*>(phi[prev]),
             reinterpret_cast<const float*>(psi[cur]), reinterpret_cast<const float*>(psi[prev]),
             bdf1_launch, sc, anchor);

@@ -264,12 +264,18 @@ __device__ __forceinline__ void pack_fwd_global(const float* __restrict__ x, cpl
 //            b = sqrt(2/N) / 2 e^{-i pi/4} e^{+i pi k / (2N)};
 //   inverse: a = s_k / 2 e^{+i pi k / (2N)} (s_0 = 1/(M sqrt(1/N)), s_k = 1/(M sqrt(2/N))),
 //            b = s_k' / 2 e^{+i pi/4} e^{-i pi k / (2N)} (s_k' = 1/(M sqrt(2/N))).
-struct alignas(16) PairTw { float wnx, wny, ax, ay, bx, by, pad0, pad1; };
+struct PairTw { float wnx, wny, ax, ay, bx, by; };
 
-__device__ __forceinline__ PairTw load_pair_tw(const PairTw* __restrict__ t, int k) {
-    const float4 u = __ldg(reinterpret_cast<const float4*>(t + k));
-    const float4 v = __ldg(reinterpret_cast<const float4*>(t + k) + 1);
-    return PairTw{u.x, u.y, u.z, u.w, v.x, v.y, 0.f, 0.f};
+// Device table of the pairs k = 0 .. NP-1, stored as two arrays (NP float4
+// (wnx, wny, ax, ay), then NP float2 (bx, by)), so that lanes reading
+// consecutive pairs read contiguous 16- and 8-byte words (an array of 32-byte
+// records would touch one 32-byte sector per lane and per load).
+struct PairTwTab { const float4* __restrict__ wa; const float2* __restrict__ b; };
+
+__device__ __forceinline__ PairTw load_pair_tw(const PairTwTab& t, int k) {
+    const float4 u = __ldg(t.wa + k);
+    const float2 v = __ldg(t.b + k);
+    return PairTw{u.x, u.y, u.z, u.w, v.x, v.y};
 }
 
 // Forward post-process of the pair (k, M-k): A = Z[k], B = Z[M-k].  With

@@ -52,7 +52,7 @@ template <int M> struct WGeo {
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32)
 kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
-            const cplx<float>* __restrict__ tw2, const wf::PairTw* __restrict__ twF, int ahead) {
+            const cplx<float>* __restrict__ tw2, wf::PairTwTab twF, int ahead) {
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS, NP = (M / 2 + G) / G;
     constexpr int LDS = 2 * Gm::BUF;                 // floats per line buffer
@@ -108,7 +108,7 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32, M <= 1024 ? 3 : 1)
 kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* __restrict__ part,
-               const cplx<float>* __restrict__ tw2, const wf::PairTw* __restrict__ twF,
+               const cplx<float>* __restrict__ tw2, wf::PairTwTab twF,
                const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc) {
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, KC = Gm::SLOTS / NF;
@@ -179,7 +179,7 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32)
 kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
-              const cplx<float>* __restrict__ tw2, const wf::PairTw* __restrict__ twI,
+              const cplx<float>* __restrict__ tw2, wf::PairTwTab twI,
               const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc,
               DevScalars* __restrict__ dsc, int anchor_mass) {
     using Gm = WGeo<M>;
@@ -304,7 +304,7 @@ template <int M> struct InvGeo {
 template <int M>
 __global__ void __launch_bounds__(inv_warps<M>() * 32, inv_min_ctas<M>())
 kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __restrict__ psi_new,
-        const cplx<float>* __restrict__ tw2, const wf::PairTw* __restrict__ twI,
+        const cplx<float>* __restrict__ tw2, wf::PairTwTab twI,
         const float* __restrict__ phn, const float* __restrict__ pho,
         const float* __restrict__ psn, const float* __restrict__ pso, int bdf1,
         const DevScalars* __restrict__ dsc, int anchor_mass) {
