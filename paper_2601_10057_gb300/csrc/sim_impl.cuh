@@ -213,7 +213,9 @@ public:
 
     // max_carveout: take the whole unified L1 as shared memory (kernels whose
     // occupancy is set by their tiles; the others keep L1 for cached loads)
-    static int set_smem_limit(const void* fn, size_t needed, bool max_carveout = false) {
+    // carveout: preferred shared-memory share of the unified L1 in percent
+    // (-1: the driver's choice; 100: all of it)
+    static int set_smem_limit(const void* fn, size_t needed, int carveout = -1) {
         int dev = 0, optin = 0;
         if (cudaGetDevice(&dev) != cudaSuccess) return 1;
         if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess) return 1;
@@ -221,8 +223,8 @@ public:
         if (cudaFuncGetAttributes(&fa, fn) != cudaSuccess) return 1;
         const int lim = optin - (int)fa.sharedSizeBytes;
         if ((size_t)lim < needed) return 1;
-        if (max_carveout && cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                                 (int)cudaSharedmemCarveoutMaxShared) != cudaSuccess) return 1;
+        if (carveout >= 0 && cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, carveout) != cudaSuccess)
+            return 1;
         return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) != cudaSuccess;
     }
 
@@ -301,7 +303,7 @@ public:
         // opt in to the largest dynamic shared memory each kernel can take (the
         // per-block opt-in limit minus the kernel's static shared memory); the
         // attribute is per kernel, so it must not depend on this simulation's N
-        if (set_smem_limit((const void*)k_stencil<T>, stencil_smem_bytes<T>(), true)) return CCMSAV_ECUDA;
+        if (set_smem_limit((const void*)k_stencil<T>, stencil_smem_bytes<T>(), 100)) return CCMSAV_ECUDA;
         if (set_smem_limit((const void*)k_rowdct_T<T>, sm_rt) || set_smem_limit((const void*)k_coldct_gram<T>, sm_col) ||
             set_smem_limit((const void*)k_comb_icolT<T>, sm_comb) || set_smem_limit((const void*)k_irow<T>, sm_irow))
             return CCMSAV_ECUDA;
@@ -314,6 +316,10 @@ public:
         return CCMSAV_OK;
     }
 
+    // Shared-memory share (percent) for the recovery kernel: about 164 KB, two
+    // of its 68 KB CTAs at N = 2048 and the rest of L1 (about 92 KB) for the
+    // twiddle tables; a third CTA (the whole L1 as shared memory) is slower.
+    static constexpr int kCombCarveout = 72;
     template <int MM> int setup_warp() {
         using Gm = WGeo<MM>;
         constexpr int G = Gm::G, E = Gm::E;
@@ -331,8 +337,8 @@ public:
         wKC = Gm::SLOTS / NF; wsm_col = bb;
         wRT4 = Gm::SLOTS / 2; wsm_comb = bb;
         wsm_irow = InvGeo<MM>::smem_bytes();
-        if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col, true) ||
-            set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
+        if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col, 100) ||
+            set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb, kCombCarveout) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
             return CCMSAV_ECUDA;
         ahead_rt = resident_ctas((const void*)kw_rowdct_T<MM>, kWarps * 32, wsm_rt);
         return CCMSAV_OK;

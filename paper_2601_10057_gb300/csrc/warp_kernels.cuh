@@ -46,16 +46,14 @@ template <int M> struct WGeo {
 
 // ------------------------------------------------------------------ kw_rowdct_T
 // SLOTS rows of field blockIdx.y per CTA (one line per lane group).  The
-// post-processed DCT row replaces the line's complex buffer in place (each
-// lane first holds all its pairs in registers), so the buffers double as the
-// staging area of the transposed write.
+// post-processed DCT row replaces the line's complex buffer in place, so the
+// buffers double as the staging area of the transposed write.
 template <int M>
 __global__ void __launch_bounds__(kWarps * 32)
 kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
             const cplx<float>* __restrict__ tw2, wf::PairTwTab twF, int ahead) {
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS, NP = (M / 2 + G) / G;
-    constexpr int LDS = 2 * Gm::BUF;                 // floats per line buffer
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
@@ -74,33 +72,50 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
         wf::pack_fwd_global<M>(in + f * NN + (size_t)(y0 + slot) * N, v, n2);
         wf::fourstep<float, M, false>(v, buf, tw2, n2);
     }
-    Quad<float> X[NP];
+    // DCT post-process in place, one pair at a time: pair k reads the complex
+    // slots k and M-k and writes its four modes back into them (slot k: modes
+    // k, N-k; slot M-k: modes M-k, M+k; pair 0: modes 0, M in slot 0; pair
+    // M/2: modes M/2, 3M/2 in slot M/2).  No two pairs share a slot, so no
+    // pair has to be held in registers while another is written.  The
+    // pairs go in batches of PB: all loads of a batch are issued before its
+    // stores (the compiler cannot see that the slots are disjoint).
+    constexpr int PB = 8;
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-        const int k = n2 + G * i;
-        if (k <= M / 2) X[i] = wf::post_pair_lean(buf[k], buf[(M - k) & (M - 1)], wf::load_pair_tw(twF, k));
-    }
-    __syncwarp();
-    float* srow = reinterpret_cast<float*>(buf);
+    for (int i0 = 0; i0 < NP; i0 += PB) {
+        cplx<float> A[PB], B[PB];
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-        const int k = n2 + G * i;
-        if (k <= M / 2) {
-            srow[k] = X[i].xk;
-            if (pair_mode_valid(1, k, M)) srow[N - k] = X[i].xNk;
-            if (pair_mode_valid(2, k, M)) srow[M - k] = X[i].xMk;
-            if (pair_mode_valid(3, k, M)) srow[M + k] = X[i].xMpk;
+        for (int b = 0; b < PB; ++b) {
+            const int k = n2 + G * (i0 + b);
+            if (i0 + b < NP && k <= M / 2) { A[b] = buf[k]; B[b] = buf[(M - k) & (M - 1)]; }
+        }
+#pragma unroll
+        for (int b = 0; b < PB; ++b) {
+            const int k = n2 + G * (i0 + b);
+            if (i0 + b < NP && k <= M / 2) {
+                const Quad<float> X = wf::post_pair_lean(A[b], B[b], wf::load_pair_tw(twF, k));
+                if (k == 0) {
+                    buf[0] = mk(X.xk, X.xMk);
+                } else {
+                    buf[k] = mk(X.xk, X.xNk);
+                    if (k < M / 2) buf[M - k] = mk(X.xMk, X.xMpk);
+                }
+            }
         }
     }
     __syncthreads();
-    const float* stage = reinterpret_cast<const float*>(bufs);
-    float* dst = out + f * NN;
+    // transposed write: slot j of each row holds modes j and N - j (j = 0:
+    // modes 0 and M); one float4 of 4 rows per mode
+    const float2* stage = reinterpret_cast<const float2*>(bufs);
+    constexpr int BC = Gm::BUF;                      // float2 per line buffer
+    float* dst = out + f * NN + y0;
     constexpr int R4 = RT / 4;
-    for (int q = threadIdx.x; q < R4 * N; q += blockDim.x) {
-        const int r4 = q % R4, kx = q / R4;
-        const float* s = stage + (size_t)(4 * r4) * LDS + kx;
-        *reinterpret_cast<float4*>(dst + (size_t)kx * N + y0 + 4 * r4) =
-            make_float4(s[0], s[LDS], s[2 * LDS], s[3 * LDS]);
+    for (int q = threadIdx.x; q < R4 * M; q += blockDim.x) {
+        const int r4 = q % R4, j = q / R4;
+        const float2* sp = stage + (size_t)(4 * r4) * BC + j;
+        const float2 v0 = sp[0], v1 = sp[BC], v2 = sp[2 * BC], v3 = sp[3 * BC];
+        const int mb = j == 0 ? M : N - j;
+        *reinterpret_cast<float4*>(dst + (size_t)j * N + 4 * r4) = make_float4(v0.x, v1.x, v2.x, v3.x);
+        *reinterpret_cast<float4*>(dst + (size_t)mb * N + 4 * r4) = make_float4(v0.y, v1.y, v2.y, v3.y);
     }
 }
 
@@ -184,7 +199,6 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
               DevScalars* __restrict__ dsc, int anchor_mass) {
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS / 2, NU = (M / 2 + G - 1) / G;
-    constexpr int LDS = 2 * Gm::BUF;
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
@@ -247,33 +261,36 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
         __syncwarp();
         wf::fourstep<float, M, true>(v, buf, tw2, n2);
     }
-    float4 xo[NU];
     float dhi = 0.f, dlo = 0.f;
 #pragma unroll
     for (int i = 0; i < NU; ++i) {
         const int m = n2 + G * i;
         const cplx<float> a = buf[m], b = buf[M - 1 - m];
-        xo[i] = make_float4(a.x, b.y, a.y, b.x);
         df_add(dhi, dlo, a.x); df_add(dhi, dlo, b.y); df_add(dhi, dlo, a.y); df_add(dhi, dlo, b.x);
     }
     // FP32 path: the zero-mean psi increment's kx = 0 column should sum to 0
     // over y; record what the FP32 transform left (removed in kw_irow)
     const double dsum = group_sum_exact<G>(dhi, dlo);
     if (anchor_mass && (slot & 1) == 1 && kx0 + (slot >> 1) == 0 && n2 == 0) dsc->dc_col = dsum;
-    __syncwarp();
-    float* srow = reinterpret_cast<float*>(buf);
-#pragma unroll
-    for (int i = 0; i < NU; ++i) *reinterpret_cast<float4*>(srow + 4 * (n2 + G * i)) = xo[i];
     __syncthreads();
-    const float* stage = reinterpret_cast<const float*>(bufs);
+    // transposed write straight from the line buffers: after the inverse
+    // transform slot m holds the samples y = 4m, 4m+2 and slot M-1-m the
+    // samples y = 4m+3, 4m+1 (the even/odd reordering undone in the indexing)
+    const float2* stage = reinterpret_cast<const float2*>(bufs);
+    constexpr int BC = Gm::BUF;                      // float2 per line buffer
     constexpr int R4 = RT / 4;
-    for (int q = threadIdx.x; q < 2 * R4 * N; q += blockDim.x) {
-        const int r4 = q % R4, rest = q / R4;
-        const int y = rest % N, fld = rest / N;
+    for (int q = threadIdx.x; q < 2 * R4 * (M / 2); q += blockDim.x) {
+        const int m = q % (M / 2), rest = q / (M / 2);
+        const int r4 = rest % R4, fld = rest / R4;
         // line of row 4 r4 + i and field fld is buffer 2 (4 r4 + i) + fld
-        const float* s = stage + (size_t)(8 * r4 + fld) * LDS + y;
-        *reinterpret_cast<float4*>(out + fld * NN + (size_t)y * N + kx0 + 4 * r4) =
-            make_float4(s[0], s[2 * LDS], s[4 * LDS], s[6 * LDS]);
+        const float2* sp = stage + (size_t)(8 * r4 + fld) * BC;
+        const float2 a0 = sp[m], a1 = sp[2 * BC + m], a2 = sp[4 * BC + m], a3 = sp[6 * BC + m];
+        const float2 b0 = sp[M - 1 - m], b1 = sp[2 * BC + M - 1 - m], b2 = sp[4 * BC + M - 1 - m], b3 = sp[6 * BC + M - 1 - m];
+        float* d = out + fld * NN + (size_t)(4 * m) * N + kx0 + 4 * r4;
+        *reinterpret_cast<float4*>(d) = make_float4(a0.x, a1.x, a2.x, a3.x);
+        *reinterpret_cast<float4*>(d + N) = make_float4(b0.y, b1.y, b2.y, b3.y);
+        *reinterpret_cast<float4*>(d + 2 * (size_t)N) = make_float4(a0.y, a1.y, a2.y, a3.y);
+        *reinterpret_cast<float4*>(d + 3 * (size_t)N) = make_float4(b0.x, b1.x, b2.x, b3.x);
     }
 }
 
