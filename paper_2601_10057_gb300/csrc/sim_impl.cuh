@@ -303,7 +303,11 @@ public:
         // opt in to the largest dynamic shared memory each kernel can take (the
         // per-block opt-in limit minus the kernel's static shared memory); the
         // attribute is per kernel, so it must not depend on this simulation's N
-        if (set_smem_limit((const void*)k_stencil<T>, stencil_smem_bytes<T>(), 100)) return CCMSAV_ECUDA;
+        // FP32: about 164 KB of shared memory (three 46 KB tiles per SM) and
+        // ~92 KB of L1 for the halo re-reads of neighbouring tiles measured
+        // faster than four tiles with a 28 KB L1; FP64 tiles are twice the size
+        if (set_smem_limit((const void*)k_stencil<T>, stencil_smem_bytes<T>(), std::is_same<T, float>::value ? 72 : 100))
+            return CCMSAV_ECUDA;
         if (set_smem_limit((const void*)k_rowdct_T<T>, sm_rt) || set_smem_limit((const void*)k_coldct_gram<T>, sm_col) ||
             set_smem_limit((const void*)k_comb_icolT<T>, sm_comb) || set_smem_limit((const void*)k_irow<T>, sm_irow))
             return CCMSAV_ECUDA;
