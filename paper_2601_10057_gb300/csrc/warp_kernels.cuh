@@ -162,8 +162,9 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
         for (int u = 0; u < 4; ++u) {
             if (!pair_mode_valid(u, k, M)) continue;
             const float s = evx + ev_u[u];
-            const float isig = 1.0f / (sc.C1 + s * (sc.C2 + sc.C3 * s));
-            const float itau = 1.0f / (sc.Ct + sc.lam * s);
+            // correctly rounded reciprocals (the same values as 1.0f / x)
+            const float isig = __frcp_rn(sc.C1 + s * (sc.C2 + sc.C3 * s));
+            const float itau = __frcp_rn(sc.Ct + sc.lam * s);
             float v[NF];
 #pragma unroll
             for (int g = 0; g < NF; ++g)
@@ -227,8 +228,8 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
         auto comb = [&](float a0, float a1, float a2, float a3, float a4, float a6, float a7, float ev,
                         float& vp, float& vq) {
             const float s = evx + ev;
-            vp = (a0 - aS * a1 - aH * a2 - aQ * a3 - aK * a4) * (1.0f / (sc.C1 + s * (sc.C2 + sc.C3 * s)));
-            vq = (a6 + aL * a7) * (1.0f / (sc.Ct + sc.lam * s));
+            vp = (a0 - aS * a1 - aH * a2 - aQ * a3 - aK * a4) * __frcp_rn(sc.C1 + s * (sc.C2 + sc.C3 * s));
+            vq = (a6 + aL * a7) * __frcp_rn(sc.Ct + sc.lam * s);
         };
         float vp[4], vq[4];
         comb(f0.x, f1.x, f2.x, f3.x, f4.x, f6.x, f7.x, e4.x, vp[0], vq[0]);
