@@ -248,7 +248,7 @@ __device__ __forceinline__ void pack_fwd_global(const float* __restrict__ x, cpl
     constexpr int E = Shape<M>::E, G = Shape<M>::G;
 #pragma unroll
     for (int n1 = 0; n1 < E / 2; ++n1) {
-        const float4 q = __ldg(reinterpret_cast<const float4*>(x) + (G * n1 + n2));
+        const float4 q = __ldcg(reinterpret_cast<const float4*>(x) + (G * n1 + n2));   // L2 only: keeps L1 for the tables
         v[n1] = mk(q.x, q.z);
         const float ox = __shfl_xor_sync(0xffffffffu, q.w, G - 1);
         const float oy = __shfl_xor_sync(0xffffffffu, q.y, G - 1);
