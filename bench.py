@@ -18,6 +18,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import math
 import os
@@ -66,12 +67,20 @@ def measured_peaks():
         return HBM_FALLBACK_GBS, "fallback"
 
 
+def code_text(src):
+    """C++/CUDA source without comments and with whitespace collapsed: what
+    the compiler sees, so that editing a comment keeps a profile's key."""
+    src = re.sub(r"/\*.*?\*/", " ", src, flags=re.S)
+    src = re.sub(r"//[^\n]*", " ", src)
+    return re.sub(r"\s+", " ", src).strip()
+
+
 def source_hash():
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2601_10057_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(f.encode() + fh.read())
+        with open(os.path.join(csrc, f), encoding="utf-8") as fh:
+            h.update(f.encode() + code_text(fh.read()).encode())
     return h.hexdigest()[:12]
 
 

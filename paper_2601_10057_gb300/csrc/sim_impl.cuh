@@ -303,9 +303,10 @@ public:
         // opt in to the largest dynamic shared memory each kernel can take (the
         // per-block opt-in limit minus the kernel's static shared memory); the
         // attribute is per kernel, so it must not depend on this simulation's N
-        // FP32: about 164 KB of shared memory (three 46 KB tiles per SM) and
-        // ~92 KB of L1 for the halo re-reads of neighbouring tiles measured
-        // faster than four tiles with a 28 KB L1; FP64 tiles are twice the size
+        // FP32: 72 % of 228 KB, rounded up by the driver to the 196 KB
+        // configuration: four 46 KB tiles per SM and 60 KB of L1 for the halo
+        // re-reads (faster than 228 KB with a 28 KB L1, and than 164 KB with
+        // three tiles); FP64 tiles are twice the size
         if (set_smem_limit((const void*)k_stencil<T>, stencil_smem_bytes<T>(), std::is_same<T, float>::value ? 72 : 100))
             return CCMSAV_ECUDA;
         if (set_smem_limit((const void*)k_rowdct_T<T>, sm_rt) || set_smem_limit((const void*)k_coldct_gram<T>, sm_col) ||
@@ -320,9 +321,10 @@ public:
         return CCMSAV_OK;
     }
 
-    // Shared-memory share (percent) for the recovery kernel: about 164 KB, two
-    // of its 68 KB CTAs at N = 2048 and the rest of L1 (about 92 KB) for the
-    // twiddle tables; a third CTA (the whole L1 as shared memory) is slower.
+    // Shared-memory share (percent of 228 KB) for the recovery kernel; the
+    // driver rounds it up to a supported size: 72 % -> 196 KB, two of its
+    // 68 KB CTAs at N = 2048 and 60 KB of L1 for the twiddle tables; a third
+    // CTA (228 KB, 28 KB of L1) is slower.
     static constexpr int kCombCarveout = 72;
     template <int MM> int setup_warp() {
         using Gm = WGeo<MM>;
