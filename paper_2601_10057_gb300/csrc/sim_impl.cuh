@@ -61,12 +61,10 @@ public:
     cplx<float>* tw2 = nullptr;
     float* evf = nullptr;
     float4* evp = nullptr;   // eigenvalues in the pair order of the warp-path spectra
-    float* twF = nullptr;        // forward / inverse pair twiddles of the warp path
-    float* twI = nullptr;        // (wf::PairTwTab layout: NP float4, then NP float2)
-    int twNP = 0;                // pairs in each table
-    wf::PairTwTab pair_tab(const float* t) const {
-        return wf::PairTwTab{reinterpret_cast<const float4*>(t), reinterpret_cast<const float2*>(t + 4 * (size_t)twNP)};
-    }
+    float4* twF = nullptr;       // forward / inverse pair twiddles of the warp path
+    float4* twI = nullptr;       // (wn, a) per pair; b of pair 0 in twF0 / twI0
+    float2 twF0{}, twI0{};
+    wf::PairTwTab pair_tab(const float4* t) const { return wf::PairTwTab{t, t == twF ? twF0 : twI0}; }
     int wRT = 8, wlds = 0, wRT4 = 4, wlds4 = 0, wKC = 1, wRI = 4;
     int ahead_rt = 0;   // L2 prefetch distance of the row kernel (its resident CTAs)
     size_t wsm_rt = 0, wsm_col = 0, wsm_comb = 0, wsm_irow = 0;
@@ -326,6 +324,9 @@ public:
     // 68 KB CTAs at N = 2048 and 60 KB of L1 for the twiddle tables; a third
     // CTA (228 KB, 28 KB of L1) is slower.
     static constexpr int kCombCarveout = 72;
+    // The row kernel (80 registers: three CTAs would fit) at 58 % -> 164 KB:
+    // two 68 KB CTAs per SM and 92 KB of L1 beat three with 28 KB of L1.
+    static constexpr int kRowCarveout = 58;
     template <int MM> int setup_warp() {
         using Gm = WGeo<MM>;
         constexpr int G = Gm::G, E = Gm::E;
@@ -343,7 +344,7 @@ public:
         wKC = Gm::SLOTS / NF; wsm_col = bb;
         wRT4 = Gm::SLOTS / 2; wsm_comb = bb;
         wsm_irow = InvGeo<MM>::smem_bytes();
-        if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col, 100) ||
+        if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt, kRowCarveout) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col, 100) ||
             set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb, kCombCarveout) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
             return CCMSAV_ECUDA;
         ahead_rt = resident_ctas((const void*)kw_rowdct_T<MM>, kWarps * 32, wsm_rt);
@@ -394,22 +395,18 @@ public:
             v.bx = (float)(0.5 * s1 * std::cos(q - th)); v.by = (float)(0.5 * s1 * std::sin(q - th));
             hf[k] = f; hi[k] = v;
         }
-        twNP = Mh / 2 + 1;
-        std::vector<float> pf(6 * (size_t)twNP), pi(6 * (size_t)twNP);
-        for (int k = 0; k < twNP; ++k) {
-            const wf::PairTw* src[2] = {&hf[k], &hi[k]};
-            float* dst[2] = {pf.data(), pi.data()};
-            for (int t = 0; t < 2; ++t) {
-                float* wa = dst[t] + 4 * (size_t)k;
-                float* b = dst[t] + 4 * (size_t)twNP + 2 * (size_t)k;
-                wa[0] = src[t]->wnx; wa[1] = src[t]->wny; wa[2] = src[t]->ax; wa[3] = src[t]->ay;
-                b[0] = src[t]->bx; b[1] = src[t]->by;
-            }
+        const int np = Mh / 2 + 1;
+        std::vector<float4> pf(np), pi(np);
+        for (int k = 0; k < np; ++k) {
+            pf[k] = make_float4(hf[k].wnx, hf[k].wny, hf[k].ax, hf[k].ay);
+            pi[k] = make_float4(hi[k].wnx, hi[k].wny, hi[k].ax, hi[k].ay);
         }
-        if (cudaMalloc(&twF, pf.size() * sizeof(float)) != cudaSuccess) return CCMSAV_ENOMEM;
-        if (cudaMalloc(&twI, pi.size() * sizeof(float)) != cudaSuccess) return CCMSAV_ENOMEM;
-        CCM_CUDA(cudaMemcpyAsync(twF, pf.data(), pf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
-        CCM_CUDA(cudaMemcpyAsync(twI, pi.data(), pi.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        twF0 = make_float2(hf[0].bx, hf[0].by);
+        twI0 = make_float2(hi[0].bx, hi[0].by);
+        if (cudaMalloc(&twF, pf.size() * sizeof(float4)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaMalloc(&twI, pi.size() * sizeof(float4)) != cudaSuccess) return CCMSAV_ENOMEM;
+        CCM_CUDA(cudaMemcpyAsync(twF, pf.data(), pf.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
+        CCM_CUDA(cudaMemcpyAsync(twI, pi.data(), pi.size() * sizeof(float4), cudaMemcpyHostToDevice, st));
         CCM_CUDA(cudaStreamSynchronize(st));
         int r = CCMSAV_EINVAL;
         if constexpr (std::is_same<T, float>::value)

@@ -266,16 +266,22 @@ __device__ __forceinline__ void pack_fwd_global(const float* __restrict__ x, cpl
 //            b = s_k' / 2 e^{+i pi/4} e^{-i pi k / (2N)} (s_k' = 1/(M sqrt(2/N))).
 struct PairTw { float wnx, wny, ax, ay, bx, by; };
 
-// Device table of the pairs k = 0 .. NP-1, stored as two arrays (NP float4
-// (wnx, wny, ax, ay), then NP float2 (bx, by)), so that lanes reading
-// consecutive pairs read contiguous 16- and 8-byte words (an array of 32-byte
-// records would touch one 32-byte sector per lane and per load).
-struct PairTwTab { const float4* __restrict__ wa; const float2* __restrict__ b; };
+// Device table of the pairs k = 0 .. NP-1: one float4 (wnx, wny, ax, ay)
+// per pair (lanes reading consecutive pairs read contiguous 16-byte words).
+// b follows from a for k >= 1, where both carry the same factor
+// sqrt(2/N)/2 (forward) or 1/(M sqrt(2/N))/2 (inverse):
+//   forward b = e^{-i pi/4} conj(a),  inverse b = e^{+i pi/4} conj(a);
+// b of the pair k = 0 (where a has the k = 0 factor) is stored as b0.
+struct PairTwTab { const float4* __restrict__ wa; float2 b0; };
 
+template <bool INV>
 __device__ __forceinline__ PairTw load_pair_tw(const PairTwTab& t, int k) {
     const float4 u = __ldg(t.wa + k);
-    const float2 v = __ldg(t.b + k);
-    return PairTw{u.x, u.y, u.z, u.w, v.x, v.y};
+    constexpr float h = 0.70710678118654752440f;
+    float bx = INV ? (u.z + u.w) * h : (u.z - u.w) * h;
+    float by = INV ? (u.z - u.w) * h : -(u.z + u.w) * h;
+    if (k == 0) { bx = t.b0.x; by = t.b0.y; }
+    return PairTw{u.x, u.y, u.z, u.w, bx, by};
 }
 
 // Forward post-process of the pair (k, M-k): A = Z[k], B = Z[M-k].  With

@@ -92,7 +92,7 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
         for (int b = 0; b < PB; ++b) {
             const int k = n2 + G * (i0 + b);
             if (i0 + b < NP && k <= M / 2) {
-                const Quad<float> X = wf::post_pair_lean(A[b], B[b], wf::load_pair_tw(twF, k));
+                const Quad<float> X = wf::post_pair_lean(A[b], B[b], wf::load_pair_tw<false>(twF, k));
                 if (k == 0) {
                     buf[0] = mk(X.xk, X.xMk);
                 } else {
@@ -149,7 +149,7 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
         const int c = q / (M / 2 + 1), k = q % (M / 2 + 1);
         const int kx = kx0 + c;
         Quad<float> X[NF];
-        const wf::PairTw tw = wf::load_pair_tw(twF, k);
+        const wf::PairTw tw = wf::load_pair_tw<false>(twF, k);
 #pragma unroll
         for (int g = 0; g < NF; ++g) {
             const cplx<float>* b = bufs + (size_t)(c * NF + g) * Gm::BUF;
@@ -239,7 +239,7 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
         // d_psi has zero mean (mass conservation); the FP32 path sets the
         // zero mode exactly and keeps the stored mean with the anchor
         if (anchor_mass && kx == 0 && k == 0) vq[0] = 0.f;
-        const wf::PairTw tw = wf::load_pair_tw(twI, k);
+        const wf::PairTw tw = wf::load_pair_tw<true>(twI, k);
         cplx<float> zk, zMk;
         cplx<float>* b = bufs + (size_t)(2 * r) * Gm::BUF;
         wf::pre_pair_lean(Quad<float>{vp[0], vp[1], vp[2], vp[3]}, tw, zk, zMk);
@@ -342,7 +342,7 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
         const float* row = in + (gl & 1) * NN + (size_t)(gl >> 1) * N;
         const Quad<float> X{__ldg(row + k), k > 0 ? __ldg(row + N - k) : 0.f, __ldg(row + M - k), __ldg(row + M + k)};
         cplx<float> zk, zMk;
-        wf::pre_pair_lean(X, wf::load_pair_tw(twI, k), zk, zMk);
+        wf::pre_pair_lean(X, wf::load_pair_tw<true>(twI, k), zk, zMk);
         cplx<float>* b = bufs + (size_t)l * InvGeo<M>::BUF;
         b[k] = zk;
         if (k > 0) b[M - k] = zMk;
