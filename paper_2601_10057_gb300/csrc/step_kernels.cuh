@@ -97,7 +97,27 @@ struct SolveCoef {
 
 // ------------------------------------------------------------------ helpers
 template <typename T> __device__ __forceinline__ void sincospi_(T x, T* s, T* c);
-template <> __device__ __forceinline__ void sincospi_<float>(float x, float* s, float* c) { sincospif(x, s, c); }
+// FP32: x = j + r with j = rint(x) and |r| <= 1/2 (exact), sin(pi r) =
+// r P(r^2) and cos(pi r) = Q(r^2) with P, Q of degree 4 and 5 fitted in FP64
+// by least squares at Chebyshev nodes (sinpi_fit.py in this package), then
+// the sign (-1)^j.  Error within 2 ulp of 1; about half the instructions of
+// the library routine, which also handles arguments of any size.
+template <> __device__ __forceinline__ void sincospi_<float>(float x, float* s, float* c) {
+    const float j = rintf(x);
+    const float r = x - j, q = r * r;
+    float ps = fmaf(q, 0.0776576623f, -0.598291278f);
+    ps = fmaf(q, ps, 2.55007744f);
+    ps = fmaf(q, ps, -5.1677103f);
+    ps = fmaf(q, ps, 3.14159274f);
+    float pc = fmaf(q, -0.0243963245f, 0.23493731f);
+    pc = fmaf(q, pc, -1.33521199f);
+    pc = fmaf(q, pc, 4.05870914f);
+    pc = fmaf(q, pc, -4.93480206f);
+    pc = fmaf(q, pc, 1.0f);
+    const float sg = (static_cast<int>(j) & 1) ? -1.0f : 1.0f;
+    *s = sg * (r * ps);
+    *c = sg * pc;
+}
 template <> __device__ __forceinline__ void sincospi_<double>(double x, double* s, double* c) { sincospi(x, s, c); }
 
 // bytes (a multiple of 16) at a 16-byte aligned global address into L2.
