@@ -319,14 +319,14 @@ public:
         return CCMSAV_OK;
     }
 
-    // Shared-memory share (percent of 228 KB) for the recovery kernel; the
-    // driver rounds it up to a supported size: 72 % -> 196 KB, two of its
-    // 68 KB CTAs at N = 2048 and 60 KB of L1 for the twiddle tables; a third
-    // CTA (228 KB, 28 KB of L1) is slower.
+    // Shared-memory share (percent of 228 KB) of the 8-line transform kernels;
+    // the driver rounds it up to a supported size: 72 % -> 196 KB, three of
+    // the forward kernels' 65 KB CTAs (swizzled line buffers) or two of the
+    // recovery kernel's 68 KB ones at N = 2048, and 60 KB of L1 for the
+    // twiddle and eigenvalue tables (the full 228 KB leaves 28 KB).
+    static constexpr int kRowCarveout = 72;
+    static constexpr int kColCarveout = 72;
     static constexpr int kCombCarveout = 72;
-    // The row kernel (80 registers: three CTAs would fit) at 58 % -> 164 KB:
-    // two 68 KB CTAs per SM and 92 KB of L1 beat three with 28 KB of L1.
-    static constexpr int kRowCarveout = 58;
     template <int MM> int setup_warp() {
         using Gm = WGeo<MM>;
         constexpr int G = Gm::G, E = Gm::E;
@@ -342,9 +342,9 @@ public:
         const size_t bb = Gm::buf_bytes();
         wRT = Gm::SLOTS; wsm_rt = bb;
         wKC = Gm::SLOTS / NF; wsm_col = bb;
-        wRT4 = Gm::SLOTS / 2; wsm_comb = bb;
+        wRT4 = Gm::SLOTS / 2; wsm_comb = Gm::bufp_bytes();
         wsm_irow = InvGeo<MM>::smem_bytes();
-        if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt, kRowCarveout) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col, 100) ||
+        if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt, kRowCarveout) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col, kColCarveout) ||
             set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb, kCombCarveout) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
             return CCMSAV_ECUDA;
         ahead_rt = resident_ctas((const void*)kw_rowdct_T<MM>, kWarps * 32, wsm_rt);

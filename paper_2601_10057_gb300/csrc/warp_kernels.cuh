@@ -40,8 +40,14 @@ template <int M> struct WGeo {
     static constexpr int E = wf::Shape<M>::E, G = wf::Shape<M>::G;
     static constexpr int LPW = 32 / G;                  // lines per warp
     static constexpr int SLOTS = kWarps * LPW;          // line buffers per CTA
-    static constexpr int BUF = wf::buf_len<M>();        // complex per buffer
+    // complex per buffer: unpadded, XOR-swizzled transpose (M + 2), so that
+    // three 8-line CTAs of the forward kernels fit the 196 KB shared-memory
+    // configuration; padded rows (G + 1 values) for the recovery kernel (two
+    // CTAs per SM, measured faster than three)
+    static constexpr int BUF = wf::buf_len<M, true>();
+    static constexpr int BUFP = wf::buf_len<M>();
     static constexpr size_t buf_bytes() { return (size_t)SLOTS * BUF * sizeof(cplx<float>); }
+    static constexpr size_t bufp_bytes() { return (size_t)SLOTS * BUFP * sizeof(cplx<float>); }
 };
 
 // ------------------------------------------------------------------ kw_rowdct_T
@@ -49,7 +55,7 @@ template <int M> struct WGeo {
 // post-processed DCT row replaces the line's complex buffer in place, so the
 // buffers double as the staging area of the transposed write.
 template <int M>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(kWarps * 32, M <= 1024 ? 3 : 1)
 kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
             const cplx<float>* __restrict__ tw2, wf::PairTwTab twF, int ahead) {
     using Gm = WGeo<M>;
@@ -70,7 +76,7 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
     {
         cplx<float> v[E];
         wf::pack_fwd_global<M>(in + f * NN + (size_t)(y0 + slot) * N, v, n2);
-        wf::fourstep<float, M, false>(v, buf, tw2, n2);
+        wf::fourstep<float, M, false, true>(v, buf, tw2, n2);
     }
     // DCT post-process in place, one pair at a time: pair k reads the complex
     // slots k and M-k and writes its four modes back into them (slot k: modes
@@ -128,7 +134,6 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, KC = Gm::SLOTS / NF;
     extern __shared__ __align__(16) unsigned char smraw[];
-    __shared__ double sred[kWarps * NRED2];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
     const int kx0 = blockIdx.x * KC;
@@ -139,7 +144,7 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
     {
         cplx<float> v[E];
         wf::pack_fwd_global<M>(in + f * NN + (size_t)(kx0 + kc) * N, v, n2);
-        wf::fourstep<float, M, false>(v, bufs + (size_t)slot * Gm::BUF, tw2, n2);
+        wf::fourstep<float, M, false, true>(v, bufs + (size_t)slot * Gm::BUF, tw2, n2);
     }
     __syncthreads();
     float acc[NRED2];
@@ -184,7 +189,9 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
             *reinterpret_cast<float4*>(dst + (size_t)(g < 5 ? g : g - 1) * SpecRow<M>::FO) = o;
         }
     }
-    block_sum_store_part<NRED2, float>(acc, reinterpret_cast<float2*>(part) + (size_t)blockIdx.x * NRED2, sred);
+    __syncthreads();       // the line buffers are free: their start holds the block reduction
+    block_sum_store_part<NRED2, float>(acc, reinterpret_cast<float2*>(part) + (size_t)blockIdx.x * NRED2,
+                                       reinterpret_cast<double*>(smraw));
 }
 
 // ------------------------------------------------------------------ kw_comb_icolT
@@ -241,11 +248,11 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
         if (anchor_mass && kx == 0 && k == 0) vq[0] = 0.f;
         const wf::PairTw tw = wf::load_pair_tw<true>(twI, k);
         cplx<float> zk, zMk;
-        cplx<float>* b = bufs + (size_t)(2 * r) * Gm::BUF;
+        cplx<float>* b = bufs + (size_t)(2 * r) * Gm::BUFP;
         wf::pre_pair_lean(Quad<float>{vp[0], vp[1], vp[2], vp[3]}, tw, zk, zMk);
         b[k] = zk;
         if (k > 0) b[M - k] = zMk;
-        b += Gm::BUF;
+        b += Gm::BUFP;
         wf::pre_pair_lean(Quad<float>{vq[0], vq[1], vq[2], vq[3]}, tw, zk, zMk);
         b[k] = zk;
         if (k > 0) b[M - k] = zMk;
@@ -254,7 +261,7 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int grp = lane / G, n2 = lane % G;
     const int slot = warp * Gm::LPW + grp;              // line = slot: row slot/2, field slot%2
-    cplx<float>* buf = bufs + (size_t)slot * Gm::BUF;
+    cplx<float>* buf = bufs + (size_t)slot * Gm::BUFP;
     {
         cplx<float> v[E];
 #pragma unroll
@@ -278,7 +285,7 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
     // transform slot m holds the samples y = 4m, 4m+2 and slot M-1-m the
     // samples y = 4m+3, 4m+1 (the even/odd reordering undone in the indexing)
     const float2* stage = reinterpret_cast<const float2*>(bufs);
-    constexpr int BC = Gm::BUF;                      // float2 per line buffer
+    constexpr int BC = Gm::BUFP;                     // float2 per line buffer
     constexpr int R4 = RT / 4;
     for (int q = threadIdx.x; q < 2 * R4 * (M / 2); q += blockDim.x) {
         const int m = q % (M / 2), rest = q / (M / 2);
