@@ -103,7 +103,9 @@ int ccmsav_create(ccmsav_t** out, const ccmsav_params* params, int n_sims,
  * U to the initial arc length int f_surf(phi^0) (so U^0 = 0; the paper does
  * not state A).  Resets the step counter, the lambda-sum and the error
  * state; the next step of this simulation is the BDF1 start step.
- * Returns CCMSAV_ENONFINITE if an input value is not finite. */
+ * Returns CCMSAV_ENONFINITE if an input value is not finite (checked on the
+ * device while the fields are uploaded); the simulation then holds no state
+ * until the next successful set_state. */
 int ccmsav_set_state(ccmsav_t* h, int sim, const double* phi, const double* psi);
 
 /* As ccmsav_set_state, from device memory of the handle's precision (FP64

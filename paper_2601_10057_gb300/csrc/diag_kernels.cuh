@@ -115,13 +115,54 @@ k_add_lamsum(const double* __restrict__ part, int nb, double scale, DevScalars* 
     if (threadIdx.x == 0 && sc->status == 0) sc->lamsum += scale * red[0];
 }
 
-// FP64 -> FP32 with the dithered rounding of dither_round (initial psi of
-// the FP32 path, so its stored mass carries no coherent rounding error).
-static __global__ void k_convert_dither(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+// Upload of one FP64 field into the field precision T (FP32 psi: the
+// dithered rounding of dither_round, so its stored mass carries no coherent
+// rounding error), with a flag for non-finite values and, when
+// part is given, per-block compensated (Neumaier) partial sums of the FP64
+// values (part[2 b] + part[2 b + 1]), 256 threads per block.
+template <typename T, bool DITHER>
+__global__ void __launch_bounds__(256) k_upload(const double* __restrict__ in, T* __restrict__ out, size_t n,
+                                                unsigned* __restrict__ bad, double* __restrict__ part) {
+    double s = 0.0, c = 0.0;
+    bool nonfinite = false;
     for (size_t q = blockIdx.x * (size_t)blockDim.x + threadIdx.x; q < n; q += (size_t)gridDim.x * blockDim.x) {
         const double x = in[q];
-        const float s = (float)x;
-        out[q] = dither_round(s, (float)(x - (double)s), dither_key(0xffffffffu, (uint32_t)q) | 1u);
+        nonfinite |= !isfinite(x);
+        if constexpr (DITHER) {
+            const float f = (float)x;
+            out[q] = dither_round(f, (float)(x - (double)f), dither_key(0xffffffffu, (uint32_t)q) | 1u);
+        } else {
+            out[q] = (T)x;
+        }
+        if (part) {
+            const double t = s + x;
+            c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+            s = t;
+        }
+    }
+    if (__any_sync(0xffffffffu, nonfinite) && (threadIdx.x & 31) == 0) atomicOr(bad, 1u);
+    if (part) {
+        // (s, c) pairs added with TwoSum of the high parts, over the warp, then the warps
+        __shared__ double ws[2][8];
+        for (int o = 16; o > 0; o >>= 1) {
+            const double s2 = __shfl_xor_sync(0xffffffffu, s, o), c2 = __shfl_xor_sync(0xffffffffu, c, o);
+            const double t = s + s2, bb = t - s;
+            c += c2 + ((s - (t - bb)) + (s2 - bb));
+            s = t;
+        }
+        const int w = threadIdx.x >> 5;
+        if ((threadIdx.x & 31) == 0) { ws[0][w] = s; ws[1][w] = c; }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double S = ws[0][0], C = ws[1][0];
+            for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+                const double t = S + ws[0][k], bb = t - S;
+                C += ws[1][k] + ((S - (t - bb)) + (ws[0][k] - bb));
+                S = t;
+            }
+            part[2 * blockIdx.x] = S;
+            part[2 * blockIdx.x + 1] = C;
+        }
     }
 }
 

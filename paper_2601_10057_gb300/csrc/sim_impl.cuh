@@ -71,6 +71,9 @@ public:
     DevScalars* sc_host = nullptr;   // pinned
     double* h_part = nullptr;        // pinned, diag partial rows
     void* tmp64 = nullptr;           // FP64 staging for host I/O
+    static constexpr int kUpBlocks = 1024;   // blocks of the upload kernels
+    unsigned* d_upbad = nullptr;     // upload: non-finite flag, then 2 kUpBlocks partial sums
+    double* h_up = nullptr;          // pinned mirror of the same
     bool have_state = false, poisoned = false;
     long long steps_taken = 0;
     long long nlaunch = 0;
@@ -205,6 +208,9 @@ public:
         tw2 = nullptr; evf = nullptr; evp = nullptr; twF = nullptr; twI = nullptr;
         if (sc_host) cudaFreeHost(sc_host);
         if (h_part) cudaFreeHost(h_part);
+        if (h_up) cudaFreeHost(h_up);
+        cudaFree(d_upbad);
+        h_up = nullptr; d_upbad = nullptr;
         bufA = bufB = nullptr; part1 = part2 = partd = part3 = nullptr; twM = nullptr; twP = nullptr;
         ev = nullptr; sc = nullptr; tmp64 = nullptr; sc_host = nullptr; h_part = nullptr;
     }
@@ -254,6 +260,8 @@ public:
         if (cudaMalloc(&partd, (size_t)nbd * NDIAG * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
         if (cudaMalloc(&part3, (size_t)kSolveBlocks * NRQ * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
         if (cudaMalloc(&tmp64, 2 * NN * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaMalloc(&d_upbad, (1 + 2 * kUpBlocks) * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaHostAlloc(&h_up, (1 + 2 * kUpBlocks) * sizeof(double), cudaHostAllocDefault) != cudaSuccess) return CCMSAV_ENOMEM;
         if (cudaMalloc(&sc, sizeof(DevScalars)) != cudaSuccess) return CCMSAV_ENOMEM;
         if (cudaHostAlloc(&sc_host, sizeof(DevScalars), cudaHostAllocDefault) != cudaSuccess) return CCMSAV_ENOMEM;
         if (cudaHostAlloc(&h_part, (size_t)nbd * NDIAG * sizeof(double), cudaHostAllocDefault) != cudaSuccess) return CCMSAV_ENOMEM;
@@ -495,25 +503,42 @@ public:
         return CCMSAV_OK;
     }
 
-    int upload_levels(const double* phi0, const double* psi0, const double* phi1, const double* psi1) {
+    // Uploads the four levels (FP64 host arrays) through the FP64 staging
+    // buffer; the upload kernels flag non-finite values and sum psi0 with
+    // compensated partial sums, so the host touches no field value.  One
+    // synchronisation at the end (the copies and kernels are stream-ordered).
+    int upload_levels(const double* phi0, const double* psi0, const double* phi1, const double* psi1, double* psi_sum) {
         double* d = (double*)tmp64;
         const size_t nb = NN * sizeof(double);
-        auto conv = [&](const double* host, T* dst) -> int {
-            CCM_CUDA(cudaMemcpyAsync(d, host, nb, cudaMemcpyHostToDevice, st));
-            if (std::is_same<T, float>::value && (dst == psi[cur] || dst == psi[prev]))
-                k_convert_dither<<<1024, 256, 0, st>>>(d, reinterpret_cast<float*>(dst), NN);
+        double* dpart = reinterpret_cast<double*>(d_upbad) + 1;
+        CCM_CUDA(cudaMemsetAsync(d_upbad, 0, sizeof(double), st));
+        const double* src[4] = {phi0, psi0, phi1 ? phi1 : phi0, psi1 ? psi1 : psi0};
+        T* dst[4] = {phi[cur], psi[cur], phi[prev], psi[prev]};
+        for (int q = 0; q < 4; ++q) {
+            double* stage = d + (q & 1) * NN;
+            CCM_CUDA(cudaMemcpyAsync(stage, src[q], nb, cudaMemcpyHostToDevice, st));
+            double* part = q == 1 ? dpart : nullptr;
+            if (std::is_same<T, float>::value && (q & 1))
+                k_upload<float, true><<<kUpBlocks, 256, 0, st>>>(stage, reinterpret_cast<float*>(dst[q]), NN, d_upbad, part);
             else
-                k_convert<double, T><<<1024, 256, 0, st>>>(d, dst, NN);
+                k_upload<T, false><<<kUpBlocks, 256, 0, st>>>(stage, dst[q], NN, d_upbad, part);
             ++nlaunch;
             CCM_CUDA(cudaGetLastError());
-            CCM_CUDA(cudaStreamSynchronize(st));
-            return CCMSAV_OK;
-        };
-        int r;
-        if ((r = conv(phi0, phi[cur])) != CCMSAV_OK) return r;
-        if ((r = conv(psi0, psi[cur])) != CCMSAV_OK) return r;
-        if ((r = conv(phi1 ? phi1 : phi0, phi[prev])) != CCMSAV_OK) return r;
-        if ((r = conv(psi1 ? psi1 : psi0, psi[prev])) != CCMSAV_OK) return r;
+        }
+        CCM_CUDA(cudaMemcpyAsync(h_up, d_upbad, (1 + 2 * kUpBlocks) * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CCM_CUDA(cudaStreamSynchronize(st));
+        if (*reinterpret_cast<const unsigned*>(h_up) != 0u) return CCMSAV_ENONFINITE;
+        // conserved mass: the blocks' compensated partials added in a fixed
+        // order (Neumaier), accurate to a few ulps of the sum; a plain running
+        // sum of 10^6..10^8 positive values can be off by 1e-11 relative,
+        // which the FP32 path would then conserve
+        double ssum = 0.0, scomp = 0.0;
+        for (int k = 0; k < 2 * kUpBlocks; ++k) {
+            const double x = h_up[1 + k], t = ssum + x;
+            scomp += std::fabs(ssum) >= std::fabs(x) ? (ssum - t) + x : (x - t) + ssum;
+            ssum = t;
+        }
+        *psi_sum = ssum + scomp;
         return CCMSAV_OK;
     }
 
@@ -538,24 +563,11 @@ public:
     }
 
     int set_state_host(const double* phi0, const double* psi0, const double* phi1, const double* psi1) override {
-        for (size_t q = 0; q < NN; ++q)
-            if (!std::isfinite(phi0[q]) || !std::isfinite(psi0[q]) ||
-                (phi1 && !std::isfinite(phi1[q])) || (psi1 && !std::isfinite(psi1[q])))
-                return CCMSAV_ENONFINITE;
         cur = 0; prev = 1; spare = 2;
-        int r = upload_levels(phi0, psi0, phi1, psi1);
-        if (r) return r;
-        // conserved mass: compensated (Neumaier) summation, accurate to a few
-        // ulps of the sum; a plain running sum of 10^6..10^8 positive values
-        // can be off by 1e-11 relative, which the FP32 path would then conserve
-        double ssum = 0.0, scomp = 0.0;
-        for (size_t q = 0; q < NN; ++q) {
-            const double x = psi0[q], t = ssum + x;
-            scomp += std::fabs(ssum) >= std::fabs(x) ? (ssum - t) + x : (x - t) + ssum;
-            ssum = t;
-        }
-        r = init_scalars_from_fields(ssum + scomp);
-        if (r) return r;
+        double psum = 0.0;
+        int r = upload_levels(phi0, psi0, phi1, psi1, &psum);
+        if (r == CCMSAV_OK) r = init_scalars_from_fields(psum);
+        if (r) { have_state = false; return r; }   // the levels were overwritten: no state
         have_state = true; poisoned = false;
         steps_taken = (phi1 && psi1) ? 1 : 0;   // two given levels: continue with BDF2
         return CCMSAV_OK;
