@@ -25,56 +25,62 @@ __device__ __forceinline__ double at(const T* u, int N, int i, int j) {
     return (double)u[(size_t)j * N + i];
 }
 
+// Blocks of 32 x 8 threads cover 32 x (8 kDiagRows) cells: each thread adds
+// kDiagRows cells before the block reduction.
+enum { kDiagRows = 8 };
+
 template <typename T>
 __global__ void __launch_bounds__(256)
 k_diag(const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ psi,
        double* __restrict__ part, int N, DiagCoef c) {
     __shared__ double sred[8 * NDIAG];
     const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
     double v[NDIAG];
     for (int q = 0; q < NDIAG; ++q) v[q] = 0.0;
-    if (i < N && j < N) {
-        const double aC = at(a, N, i, j), aE = at(a, N, i + 1, j), aW = at(a, N, i - 1, j);
-        const double aN = at(a, N, i, j + 1), aS = at(a, N, i, j - 1);
-        const double bC = at(b, N, i, j), bE = at(b, N, i + 1, j), bW = at(b, N, i - 1, j);
-        const double bN = at(b, N, i, j + 1), bS = at(b, N, i, j - 1);
-        const double la = (aE + aW + aN + aS - 4 * aC) * c.inv_h2;
-        const double lb = (bE + bW + bN + bS - 4 * bC) * c.inv_h2;
-        const double gE = (aE - aC) * c.inv_h, gW = (aC - aW) * c.inv_h, gN = (aN - aC) * c.inv_h, gS = (aC - aS) * c.inv_h;
-        const double gbar = 0.5 * (gE * gE + gW * gW) + 0.5 * (gN * gN + gS * gS);
-        const double vv = aC * aC - 1.0 - c.beta;
-        const double a3 = aC * aC * aC - aC;
-        const double ps = (double)psi[(size_t)j * N + i];
-        double sp, cp;
-        sincospi(0.5 * aC, &sp, &cp);
-        const double fin = 0.5 * c.gin * (ps - c.psin) * (ps - c.psin) + c.bin;
-        const double fout = 0.5 * c.gout * (ps - c.psout) * (ps - c.psout) + c.bout;
-        v[0] = vv * vv * 0.25 * c.inv_eps;
-        v[1] = 6.0 * aC * aC * gbar + a3 * a3 * c.inv_eps * c.inv_eps;
-        v[2] = (1.0 + sp) * fin + (1.0 - sp) * fout;
-        v[3] = 0.25 * (aC * aC - 1.0) * (aC * aC - 1.0);
-        // interior faces owned by this cell: east (i+1/2) and north (j+1/2)
-        const double cE = 2 * aC - bC, cEe = 2 * aE - bE, cNn = 2 * aN - bN;
-        const double dC = aC - bC, dEe = aE - bE, dNn = aN - bN;
-        if (i + 1 < N) {
-            v[4] += gE * gE;
-            v[7] += (cEe - cE) * (cEe - cE) * c.inv_h2;
-            v[8] += (dEe - dC) * (dEe - dC) * c.inv_h2;
+    for (int rr = 0; rr < kDiagRows; ++rr) {
+        const int j = blockIdx.y * 8 * kDiagRows + 8 * rr + (threadIdx.x >> 5);
+        if (i < N && j < N) {
+            const double aC = at(a, N, i, j), aE = at(a, N, i + 1, j), aW = at(a, N, i - 1, j);
+            const double aN = at(a, N, i, j + 1), aS = at(a, N, i, j - 1);
+            const double bC = at(b, N, i, j), bE = at(b, N, i + 1, j), bW = at(b, N, i - 1, j);
+            const double bN = at(b, N, i, j + 1), bS = at(b, N, i, j - 1);
+            const double la = (aE + aW + aN + aS - 4 * aC) * c.inv_h2;
+            const double lb = (bE + bW + bN + bS - 4 * bC) * c.inv_h2;
+            const double gE = (aE - aC) * c.inv_h, gW = (aC - aW) * c.inv_h, gN = (aN - aC) * c.inv_h, gS = (aC - aS) * c.inv_h;
+            const double gbar = 0.5 * (gE * gE + gW * gW) + 0.5 * (gN * gN + gS * gS);
+            const double vv = aC * aC - 1.0 - c.beta;
+            const double a3 = aC * aC * aC - aC;
+            const double ps = (double)psi[(size_t)j * N + i];
+            double sp, cp;
+            sincospi(0.5 * aC, &sp, &cp);
+            const double fin = 0.5 * c.gin * (ps - c.psin) * (ps - c.psin) + c.bin;
+            const double fout = 0.5 * c.gout * (ps - c.psout) * (ps - c.psout) + c.bout;
+            v[0] += vv * vv * 0.25 * c.inv_eps;
+            v[1] += 6.0 * aC * aC * gbar + a3 * a3 * c.inv_eps * c.inv_eps;
+            v[2] += (1.0 + sp) * fin + (1.0 - sp) * fout;
+            v[3] += 0.25 * (aC * aC - 1.0) * (aC * aC - 1.0);
+            // interior faces owned by this cell: east (i+1/2) and north (j+1/2)
+            const double cE = 2 * aC - bC, cEe = 2 * aE - bE, cNn = 2 * aN - bN;
+            const double dC = aC - bC, dEe = aE - bE, dNn = aN - bN;
+            if (i + 1 < N) {
+                v[4] += gE * gE;
+                v[7] += (cEe - cE) * (cEe - cE) * c.inv_h2;
+                v[8] += (dEe - dC) * (dEe - dC) * c.inv_h2;
+            }
+            if (j + 1 < N) {
+                v[4] += gN * gN;
+                v[7] += (cNn - cE) * (cNn - cE) * c.inv_h2;
+                v[8] += (dNn - dC) * (dNn - dC) * c.inv_h2;
+            }
+            v[5] += la * la;
+            v[6] += (2 * la - lb) * (2 * la - lb);
+            v[9] += aC * aC;
+            v[10] += cE * cE;
+            const double w = a3 * c.inv_eps - c.eps * la;
+            v[11] += w * w;
+            v[12] += 0.5 * (1.0 + sp) * fin + 0.5 * (1.0 - sp) * fout;
+            v[13] += ps;
         }
-        if (j + 1 < N) {
-            v[4] += gN * gN;
-            v[7] += (cNn - cE) * (cNn - cE) * c.inv_h2;
-            v[8] += (dNn - dC) * (dNn - dC) * c.inv_h2;
-        }
-        v[5] = la * la;
-        v[6] = (2 * la - lb) * (2 * la - lb);
-        v[9] = aC * aC;
-        v[10] = cE * cE;
-        const double w = a3 * c.inv_eps - c.eps * la;
-        v[11] = w * w;
-        v[12] = 0.5 * (1.0 + sp) * fin + 0.5 * (1.0 - sp) * fout;
-        v[13] = ps;
     }
     block_sum_store<NDIAG, double>(v, part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * NDIAG, sred);
 }
@@ -87,15 +93,17 @@ k_dnorm(const T* __restrict__ phn, const T* __restrict__ pho, const T* __restric
         const T* __restrict__ psn, const T* __restrict__ pso, double* __restrict__ part, int N, double M0) {
     __shared__ double sred[8];
     const int i = blockIdx.x * 32 + (threadIdx.x & 31);
-    const int j = blockIdx.y * 8 + (threadIdx.x >> 5);
     double v[1] = {0.0};
-    if (i < N && j < N) {
-        auto ph = [&](int ii, int jj) { return 2.0 * at(phn, N, ii, jj) - at(pho, N, ii, jj); };
-        auto w = [&](int ii, int jj) { return at(psnew, N, ii, jj) - (2.0 * at(psn, N, ii, jj) - at(pso, N, ii, jj)); };
-        const double pC = ph(i, j), wC = w(i, j);
-        auto mob = [&](double x) { double s = x * x - 1.0; return 1.0 - M0 * s * s; };
-        if (i + 1 < N) { double d = w(i + 1, j) - wC; v[0] += d * d / mob(0.5 * (pC + ph(i + 1, j))); }
-        if (j + 1 < N) { double d = w(i, j + 1) - wC; v[0] += d * d / mob(0.5 * (pC + ph(i, j + 1))); }
+    for (int rr = 0; rr < kDiagRows; ++rr) {
+        const int j = blockIdx.y * 8 * kDiagRows + 8 * rr + (threadIdx.x >> 5);
+        if (i < N && j < N) {
+            auto ph = [&](int ii, int jj) { return 2.0 * at(phn, N, ii, jj) - at(pho, N, ii, jj); };
+            auto w = [&](int ii, int jj) { return at(psnew, N, ii, jj) - (2.0 * at(psn, N, ii, jj) - at(pso, N, ii, jj)); };
+            const double pC = ph(i, j), wC = w(i, j);
+            auto mob = [&](double x) { double s = x * x - 1.0; return 1.0 - M0 * s * s; };
+            if (i + 1 < N) { double d = w(i + 1, j) - wC; v[0] += d * d / mob(0.5 * (pC + ph(i + 1, j))); }
+            if (j + 1 < N) { double d = w(i, j + 1) - wC; v[0] += d * d / mob(0.5 * (pC + ph(i, j + 1))); }
+        }
     }
     block_sum_store<1, double>(v, part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x), sred);
 }

@@ -253,7 +253,7 @@ public:
         b_st = dim3(TX, TY);
         g_st = dim3((N + TX - 1) / TX, (N + TYB - 1) / TYB);
         nb1 = g_st.x * g_st.y;
-        g_dg = dim3((N + 31) / 32, (N + 7) / 8);
+        g_dg = dim3((N + 31) / 32, (N + 8 * kDiagRows - 1) / (8 * kDiagRows));
         nbd = g_dg.x * g_dg.y;
         if (cudaMalloc(&part1, (size_t)nb1 * NRED1 * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
         if (cudaMalloc(&part2, (size_t)N * NRED2 * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;

@@ -192,6 +192,21 @@ def test_nonfinite_input_rejected():
     assert cc.ccmsav_step(sim.h, 1) == cc.CCMSAV_ESTATE
 
 
+@pytest.mark.parametrize("precision,N", [("fp64", 64), ("fp32", 64), ("fp32", 2048)])
+def test_uploaded_conserved_mean_is_exact_sum(precision, N):
+    """set_state sums psi on the device while uploading it (compensated
+    per-thread sums, TwoSum merges, a fixed-order host pass): the conserved
+    mean it keeps equals the exactly rounded mean of the FP64 input."""
+    import math
+    w = I.workload("three_vesicles", N=N) if N >= 1024 else I.workload("one_vesicle", N=N)
+    sim = cc.Simulation(w.params, w.N, precision=precision)
+    sim.set_state(w.phi0, w.psi0)
+    aux = sim.aux()
+    exact = math.fsum(w.psi0.ravel().tolist()) / (N * N)
+    assert abs(aux[11] - exact) <= 1e-14 * abs(exact), (aux[11], exact)
+    sim.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "fp32"])
 def test_resume_is_bit_exact(precision):
     w = I.workload("one_vesicle", N=64, dt=1e-5)
