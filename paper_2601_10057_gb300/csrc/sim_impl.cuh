@@ -503,8 +503,8 @@ public:
         return CCMSAV_OK;
     }
 
-    // Uploads the four levels (FP64 host arrays) through the FP64 staging
-    // buffer; the upload kernels flag non-finite values and sum psi0 with
+    // Uploads the four levels (FP64 host arrays; a missing previous level is
+    // a device copy of level n) through the FP64 staging buffer; the upload kernels flag non-finite values and sum psi0 with
     // compensated partial sums, so the host touches no field value.  One
     // synchronisation at the end (the copies and kernels are stream-ordered).
     int upload_levels(const double* phi0, const double* psi0, const double* phi1, const double* psi1, double* psi_sum) {
@@ -512,9 +512,13 @@ public:
         const size_t nb = NN * sizeof(double);
         double* dpart = reinterpret_cast<double*>(d_upbad) + 1;
         CCM_CUDA(cudaMemsetAsync(d_upbad, 0, sizeof(double), st));
-        const double* src[4] = {phi0, psi0, phi1 ? phi1 : phi0, psi1 ? psi1 : psi0};
+        const double* src[4] = {phi0, psi0, phi1, psi1};
         T* dst[4] = {phi[cur], psi[cur], phi[prev], psi[prev]};
         for (int q = 0; q < 4; ++q) {
+            if (!src[q]) {   // no previous level given: the same values (and rounding) as level n
+                CCM_CUDA(cudaMemcpyAsync(dst[q], dst[q - 2], NN * sizeof(T), cudaMemcpyDeviceToDevice, st));
+                continue;
+            }
             double* stage = d + (q & 1) * NN;
             CCM_CUDA(cudaMemcpyAsync(stage, src[q], nb, cudaMemcpyHostToDevice, st));
             double* part = q == 1 ? dpart : nullptr;
