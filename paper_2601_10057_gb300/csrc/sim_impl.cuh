@@ -66,7 +66,7 @@ public:
     float2 twF0{}, twI0{};
     wf::PairTwTab pair_tab(const float4* t) const { return wf::PairTwTab{t, t == twF ? twF0 : twI0}; }
     int wRT = 8, wlds = 0, wRT4 = 4, wlds4 = 0, wKC = 1, wRI = 4;
-    int ahead_rt = 0;   // L2 prefetch distance of the row kernel (its resident CTAs)
+    int ahead_rt = 0;   // L2 prefetch distance of the row kernel (0: none)
     size_t wsm_rt = 0, wsm_col = 0, wsm_comb = 0, wsm_irow = 0;
     DevScalars* sc_host = nullptr;   // pinned
     double* h_part = nullptr;        // pinned, diag partial rows
@@ -355,7 +355,16 @@ public:
         if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt, kRowCarveout) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col, kColCarveout) ||
             set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb, kCombCarveout) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
             return CCMSAV_ECUDA;
-        ahead_rt = resident_ctas((const void*)kw_rowdct_T<MM>, kWarps * 32, wsm_rt);
+        // L2 prefetch one residency ahead only where few CTAs fit per SM (one
+        // at N = 4096); with three per SM (N <= 2048) it evicts rows before
+        // their use and costs time (73.3 vs 71.5 us at N = 2048)
+        {
+            int dev = 0, nsm = 0;
+            if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+                return CCMSAV_ECUDA;
+            const int res = resident_ctas((const void*)kw_rowdct_T<MM>, kWarps * 32, wsm_rt);
+            ahead_rt = res >= 3 * nsm ? 0 : res;
+        }
         return CCMSAV_OK;
     }
 
