@@ -150,8 +150,36 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
     float acc[NRED2];
 #pragma unroll
     for (int i = 0; i < NRED2; ++i) acc[i] = 0.f;
-    for (int q = threadIdx.x; q < KC * (M / 2 + 1); q += blockDim.x) {
-        const int c = q / (M / 2 + 1), k = q % (M / 2 + 1);
+    static_assert(KC * NF <= 32, "one lane per (column, field) of the pair M/2");
+    if (warp == kWarps - 1) {
+        // pair M/2 (modes M/2 and 3M/2 only) of every column by the last warp,
+        // one lane per (column, field), so that the loop below gives every
+        // thread the same number of pairs; lane 8c adds the column's Gram terms
+        const int c = lane >> 3, g = lane & 7;
+        float xm = 0.f, x3 = 0.f;
+        if (c < KC) {
+            const cplx<float>* b = bufs + (size_t)(c * NF + g) * Gm::BUF;
+            const Quad<float> X = wf::post_pair_lean(b[M / 2], b[M / 2], wf::load_pair_tw<false>(twF, M / 2));
+            xm = X.xk;
+            x3 = X.xNk;
+            if (g != 5)
+                *reinterpret_cast<float4*>(spec + (size_t)(kx0 + c) * SpecRow<M>::KS + (size_t)(g < 5 ? g : g - 1) * SpecRow<M>::FO +
+                                           4 * (M / 2)) = make_float4(xm, x3, xm, x3);
+        }
+#pragma unroll 1
+        for (int mode = 0; mode < 2; ++mode) {       // M/2, then 3M/2
+            float v[NF];
+#pragma unroll
+            for (int u = 0; u < NF; ++u) v[u] = __shfl_sync(0xffffffffu, mode ? x3 : xm, (lane & ~7) + u);
+            if (g == 0 && c < KC) {
+                const float4 eh = evp[M / 2];
+                const float sm = evf[kx0 + c] + (mode ? eh.y : eh.x);
+                gram_accumulate(acc, v, __frcp_rn(sc.C1 + sm * (sc.C2 + sc.C3 * sm)), __frcp_rn(sc.Ct + sc.lam * sm));
+            }
+        }
+    }
+    for (int q = threadIdx.x; q < KC * (M / 2); q += blockDim.x) {
+        const int c = q / (M / 2), k = q % (M / 2);
         const int kx = kx0 + c;
         Quad<float> X[NF];
         const wf::PairTw tw = wf::load_pair_tw<false>(twF, k);
@@ -177,15 +205,14 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
             gram_accumulate(acc, v, isig, itau);
         }
         // spectra in pair order: slot u of pair k holds mode k, N-k, M-k, M+k
-        // (k = 0: no mode N, slot 3 repeats mode M; k = M/2: slots 2, 3 repeat
-        // modes M/2, 3M/2), one float4 per field
+        // (k = 0: no mode N, slot 3 repeats mode M; k = M/2, above: slots 2, 3
+        // repeat modes M/2, 3M/2), one float4 per field
         float* dst = spec + (size_t)kx * SpecRow<M>::KS + 4 * k;
 #pragma unroll
         for (int g = 0; g < NF; ++g) {
             if (g == 5) continue;
             float4 o = make_float4(X[g].xk, k == 0 ? 0.f : X[g].xNk, X[g].xMk, X[g].xMpk);
             if (k == 0) o.w = o.z;
-            if (k == M / 2) { o.z = o.x; o.w = o.y; }
             *reinterpret_cast<float4*>(dst + (size_t)(g < 5 ? g : g - 1) * SpecRow<M>::FO) = o;
         }
     }
