@@ -203,7 +203,7 @@ def run_reference(args, world, rank):
     s = O.initial_state(w.phi0, w.psi0, m)
     s = O.step(s, m)
     t_one = time.perf_counter() - t0
-    warm = min(args.warmup, 1)
+    warm = max(1, min(args.warmup, int(60.0 / max(t_one, 1e-3))))   # the requested warm-up, within ~60 s
     for _ in range(warm):
         s = O.step(s, m)
     k = max(1, min(args.steps, int(budget / max(t_one, 1e-3))))
