@@ -244,7 +244,7 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
     // one item = one spectral row and one pair index k: the four modes
     // k, N-k, M-k, M+k of both lines (d_phi^ from five spectra, d_psi^ from
     // two), one float4 per spectrum in the pair-ordered layout
-#pragma unroll 2
+#pragma unroll 4
     for (int q = threadIdx.x; q < RT * PAIRS; q += blockDim.x) {
         const int r = q / PAIRS, k = q % PAIRS;
         const int kx = kx0 + r;
@@ -368,7 +368,8 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
     const size_t NN = (size_t)N * N;
     const int l0 = blockIdx.x * L;                       // first line of this CTA
     constexpr int PAIRS = M / 2 + 1;
-#pragma unroll 4
+    constexpr int UNR = M >= 2048 ? 8 : 4;    // loads in flight: 8 at 64 values per lane (12 warps per SM)
+#pragma unroll UNR
     for (int q = threadIdx.x; q < L * PAIRS; q += blockDim.x) {
         const int l = q / PAIRS, k = q % PAIRS;
         const int gl = l0 + l;
