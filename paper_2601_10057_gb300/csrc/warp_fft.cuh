@@ -14,6 +14,7 @@
 // Supported lines: M in {64, ..., 2048} (N = 2M in 128 .. 4096);
 // G = 2^floor(log2(M)/2) <= 32, E = M / G <= 64.
 #pragma once
+#include <type_traits>
 #include "dct_device.cuh"
 
 namespace ccm {
@@ -188,12 +189,17 @@ template <int M, bool SWZ = false> __host__ __device__ constexpr int buf_len() {
 }
 
 // Position of element c of transpose row R (E rows of G values).  Padded:
-// R (G + 1) + c.  Swizzled: R G + (c ^ swz(R)), swz(R) = (R / J) mod G with
-// J = E / G; writes (one row, all lanes of a group) and reads (lane n2 reads
-// rows n2 J + j) both touch distinct banks within each half-warp.
+// R (G + 1) + c.  Swizzled: R G + (c ^ swz(R)) with J = E / G and, for
+// E <= 32, swz(R) = 2 (R / J) mod G: the writes (one row, all lanes of a
+// group) touch distinct banks within each half-warp, and since swz is even
+// the columns 2p, 2p + 1 stay adjacent and in order, so a lane reads two
+// values of its row (n2 J + j) with one 16-byte load, on distinct banks within
+// each quarter-warp for G >= 16.  For E = 64, swz(R) = (R / J) mod G with
+// 8-byte reads (measured faster there).
+template <int M> __host__ __device__ constexpr bool wide_reads() { return Shape<M>::E <= 32; }
 template <int M, bool SWZ> __device__ __forceinline__ int tpos(int R, int c) {
-    constexpr int G = Shape<M>::G, J = Shape<M>::E / Shape<M>::G;
-    return SWZ ? R * G + (c ^ ((R / J) & (G - 1))) : R * (G + 1) + c;
+    constexpr int G = Shape<M>::G, J = Shape<M>::E / Shape<M>::G, S = wide_reads<M>() ? 2 : 1;
+    return SWZ ? R * G + (c ^ ((S * (R / J)) & (G - 1))) : R * (G + 1) + c;
 }
 
 // Steps 1-4.  v: this lane's E values in four-step order.  buf: this line's
@@ -223,10 +229,21 @@ __device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>
         }
     }
     __syncwarp();
+    if constexpr (SWZ && wide_reads<M>() && std::is_same<T, float>::value) {
 #pragma unroll
-    for (int j = 0; j < J; ++j)
+        for (int j = 0; j < J; ++j)
 #pragma unroll
-        for (int m = 0; m < G; ++m) v[j * G + m] = buf[tpos<M, SWZ>(n2 * J + j, m)];
+            for (int m = 0; m < G; m += 2) {
+                const float4 q = *reinterpret_cast<const float4*>(buf + tpos<M, SWZ>(n2 * J + j, m));
+                v[j * G + m] = mk(q.x, q.y);
+                v[j * G + m + 1] = mk(q.z, q.w);
+            }
+    } else {
+#pragma unroll
+        for (int j = 0; j < J; ++j)
+#pragma unroll
+            for (int m = 0; m < G; ++m) v[j * G + m] = buf[tpos<M, SWZ>(n2 * J + j, m)];
+    }
     __syncwarp();
 #pragma unroll
     for (int j = 0; j < J; ++j) {
