@@ -21,3 +21,15 @@ def test_reference_arm_json_line():
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["unit"] == line["unit"]
     assert line["config"]["workload"] == "three_vesicles_N256"
+
+
+def test_source_hash_ignores_comments_and_whitespace():
+    """The key of the committed ncu traffic file: what the compiler sees.
+    Comment and layout edits keep it; a change of code changes it."""
+    import bench
+    a = "int f(int x) {  // the sum\n    return x + 1; /* one */\n}\n"
+    b = "int f(int x) {\n  // a different comment\n  return x + 1;\n}"
+    c = "int f(int x) {\n    return x + 2;\n}\n"
+    assert bench.code_text(a) == bench.code_text(b)
+    assert bench.code_text(a) != bench.code_text(c)
+    assert "//" not in bench.code_text(a) and "/*" not in bench.code_text(a)
