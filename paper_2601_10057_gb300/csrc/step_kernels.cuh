@@ -279,8 +279,12 @@ template <> struct ExactSum<double> {
 // index -1 -> 0, -2 -> 1, N -> N-1, N+1 -> N-2 (for halo 1 this is the
 // mirror phi_0 = phi_1 of Appendix D; for halo 2 it makes Lap phi at a ghost
 // cell equal the mirror of Lap phi, i.e. Lap^2 = Lap o Lap with mirrored ghosts).
+// Tile cells farther out than that (the tile's far side on grids smaller than
+// the tile) feed only results outside the grid, which are never stored; they
+// are clamped into the grid so that every load stays inside the field.
 __device__ __forceinline__ int reflect(int i, int N) {
-    return i < 0 ? -1 - i : (i >= N ? 2 * N - 1 - i : i);
+    i = i < 0 ? -1 - i : (i >= N ? 2 * N - 1 - i : i);
+    return min(max(i, 0), N - 1);
 }
 
 // Counter-based 32-bit hash (the "lowbias32" integer mixer: xor-shifts and
@@ -380,46 +384,58 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
     const T ih = c.inv_h, ih2 = c.inv_h2;
     const size_t NN = (size_t)N * N;
     ExactSum<T> sum_n, sum_o;
-    // Halo load: the global loads of NB cells are issued before any of them
-    // is used.  The sums of psi^n and psi^{n-1} over the block's own cells
-    // are taken here, from the loaded values.
+    // Halo load: thread (cx, ty) = (tid mod TX, tid / TX) takes tile column cx
+    // in rows ty, ty + TY, ... (so its column, its reflection and its column
+    // tests are fixed); the four right-hand halo columns TX .. TX + 3 are one
+    // more item of the first 4 (TYB + 4) threads.  The global loads of NB
+    // items are issued before any of them is used.  The sums of psi^n and
+    // psi^{n-1} over the block's own cells are taken here, from the loaded
+    // values.
     {
-        constexpr int NCELL = (TX + 4) * (TYB + 4), NT = TX * TY, NB = 5;
+        constexpr int NT = TX * TY, RH = TYB + 4, NR = RH / TY, NI = NR + 1, NB = (NI + 1) / 2;
+        static_assert(RH % TY == 0 && 4 * RH <= NT, "halo load mapping");
+        const int cx = tid % TX, ty = tid / TX;
+        const int gxc = reflect(i0 + cx - 2, N);
+        const int ex_r = tid >> 2, ex_c = TX + (tid & 3);
+        const bool ex_on = tid < 4 * RH;
+        const int gxe = reflect(i0 + ex_c - 2, N);
 #pragma unroll
-        for (int q0 = 0; q0 < NCELL; q0 += NB * NT) {
+        for (int u0 = 0; u0 < NI; u0 += NB) {
             T ra[NB], rb[NB], rc[NB], rd[NB];
 #pragma unroll
-            for (int u = 0; u < NB; ++u) {
-                const int q = q0 + u * NT + tid;
-                ra[u] = rb[u] = rc[u] = rd[u] = (T)0;
-                if (q < NCELL) {
-                    const int lj = q / W2, li = q % W2;
-                    const size_t g = (size_t)reflect(j0 + lj - 2, N) * N + reflect(i0 + li - 2, N);
-                    ra[u] = phn[g];
-                    rb[u] = pho[g];
+            for (int b = 0; b < NB; ++b) {
+                const int u = u0 + b;
+                ra[b] = rb[b] = rc[b] = rd[b] = (T)0;
+                const bool ex = u == NR;
+                if (u < NI && (!ex || ex_on)) {
+                    const int lj = ex ? ex_r : ty + TY * u, li = ex ? ex_c : cx;
+                    const size_t g = (size_t)reflect(j0 + lj - 2, N) * N + (ex ? gxe : gxc);
+                    ra[b] = phn[g];
+                    rb[b] = pho[g];
                     if (lj >= 1 && lj <= TYB + 2 && li >= 1 && li <= TX + 2) {
-                        rc[u] = psn[g];
-                        rd[u] = pso[g];
+                        rc[b] = psn[g];
+                        rd[b] = pso[g];
                     }
                 }
             }
 #pragma unroll
-            for (int u = 0; u < NB; ++u) {
-                const int q = q0 + u * NT + tid;
-                if (q < NCELL) {
-                    const int lj = q / W2, li = q % W2;
-                    const T a = ra[u], da = a - rb[u];
+            for (int b = 0; b < NB; ++b) {
+                const int u = u0 + b;
+                const bool ex = u == NR;
+                if (u < NI && (!ex || ex_on)) {
+                    const int lj = ex ? ex_r : ty + TY * u, li = ex ? ex_c : cx;
+                    const T a = ra[b], da = a - rb[b];
                     sbar[lj * W2 + li] = a + kbar * da;
                     if (lj >= 1 && lj <= TYB + 2 && li >= 1 && li <= TX + 2) {
                         const int o = (lj - 1) * W1 + (li - 1);
-                        const T du = rc[u] - rd[u];
+                        const T du = rc[b] - rd[b];
                         sph[o] = a + kst * da;
-                        sps[o] = rc[u] + kst * du;
+                        sps[o] = rc[b] + kst * du;
                         sdq[o] = kq * du;
                         if (lj >= 2 && lj <= TYB + 1 && li >= 2 && li <= TX + 1
                             && i0 + li - 2 < N && j0 + lj - 2 < N) {
-                            sum_n.add(rc[u]);
-                            sum_o.add(rd[u]);
+                            sum_n.add(rc[b]);
+                            sum_o.add(rd[b]);
                         }
                     }
                 }
