@@ -194,6 +194,83 @@ def test_surface_energy_is_arc_length():
     assert O.surface_integral(phi, m) == pytest.approx(2 * math.pi * R, rel=5e-3)
 
 
+# ------------------------- physical energy components (Sec. 2.1, eq. energy_densities)
+
+@pytest.mark.parametrize("c,q", [(0.3, 0.55), (-0.7, 0.9), (1.1, 0.2)])
+def test_physical_energy_closed_forms_uniform(c, q):
+    """Uniform phi = c, psi = q (Delta_h phi = 0, no gradients):
+    F_bend = gamma_bend 3 sqrt2/(16 eps) |Omega| ((c^3 - c)/eps)^2,
+    F_osm = |Omega| [(1 + p(c)) f_in(q) + (1 - p(c)) f_out(q)] / 2,
+    F_surf = gamma_surf |Omega| 3 sqrt2/4 g(c)/eps, F_area = gamma_area/2 (int f_surf - A)^2,
+    and the total is their sum (energy_functional)."""
+    m = model(8, eps=0.25, L=1.7, gamma_bend=0.7, gamma_surf=1.3, gamma_area=2.5, beta_in=0.3, beta_out=-0.2)
+    area = m.L ** 2
+    phi, psi = np.full((8, 8), c), np.full((8, 8), q)
+    A = 0.37
+    e = O.physical_energy(phi, psi, m, A)
+    bend = m.gamma_bend * 3 * SQ2 / (16 * m.eps) * area * ((c ** 3 - c) / m.eps) ** 2
+    pc = math.sin(math.pi * c / 2)
+    fi = m.gamma_in / 2 * (q - m.psi_in) ** 2 + m.beta_in
+    fo = m.gamma_out / 2 * (q - m.psi_out) ** 2 + m.beta_out
+    osm = area * ((1 + pc) * fi + (1 - pc) * fo) / 2
+    arc = area * 3 * SQ2 / 4 * (c * c - 1) ** 2 / 4 / m.eps
+    surf = m.gamma_surf * arc
+    ar = m.gamma_area / 2 * (arc - A) ** 2
+    assert e["bend"] == pytest.approx(bend, rel=1e-13, abs=1e-300)
+    assert e["osm"] == pytest.approx(osm, rel=1e-13)
+    assert e["surf"] == pytest.approx(surf, rel=1e-13, abs=1e-300)
+    assert e["arc_length"] == pytest.approx(arc, rel=1e-13, abs=1e-300)
+    assert e["area"] == pytest.approx(ar, rel=1e-13)
+    assert e["total"] == pytest.approx(surf + bend + ar + osm, rel=1e-13)
+
+
+def test_physical_energy_bruteforce_tiny_grid():
+    """F_bend and F_osm on a random 4 x 4 field against explicit cell loops:
+    w_ij = (phi^3 - phi)/eps - eps (sum of the four neighbour differences)/h^2
+    with Neumann ghosts by mirroring (Appendix D), F_bend = gamma_bend
+    3 sqrt2/(16 eps) h^2 sum w^2; F_osm = h^2 sum f_osm(phi_ij, psi_ij)."""
+    N = 4
+    m = model(N, L=2.0, eps=0.4, gamma_bend=0.9)
+    h = m.h
+    rng = np.random.default_rng(21)
+    phi = rng.uniform(-1.2, 1.2, (N, N))
+    psi = rng.uniform(0.0, 1.0, (N, N))
+
+    def at(j, i):
+        return phi[min(max(j, 0), N - 1), min(max(i, 0), N - 1)]
+
+    bend = osm = 0.0
+    for j in range(N):
+        for i in range(N):
+            c = phi[j, i]
+            lap = sum(at(j + dj, i + di) - c for dj, di in ((0, 1), (0, -1), (1, 0), (-1, 0))) / h ** 2
+            w = (c ** 3 - c) / m.eps - m.eps * lap
+            bend += w * w
+            pc = math.sin(math.pi * c / 2)
+            fi = m.gamma_in / 2 * (psi[j, i] - m.psi_in) ** 2 + m.beta_in
+            fo = m.gamma_out / 2 * (psi[j, i] - m.psi_out) ** 2 + m.beta_out
+            osm += 0.5 * (1 + pc) * fi + 0.5 * (1 - pc) * fo
+    bend *= m.gamma_bend * 3 * SQ2 / (16 * m.eps) * h * h
+    osm *= h * h
+    e = O.physical_energy(phi, psi, m, 0.0)
+    assert e["bend"] == pytest.approx(bend, rel=1e-13)
+    assert e["osm"] == pytest.approx(osm, rel=1e-13)
+
+
+@pytest.mark.parametrize("R", [1.0, 0.8])
+def test_bending_energy_of_a_circle(R):
+    """For phi = tanh(d/(sqrt2 eps)) the flat profile solves g'(phi)/eps =
+    eps phi'' exactly, so across a circle of radius R the bending density's
+    bracket is -eps phi'/R and int f_bend = 3 sqrt2 eps/(16 R^2) int phi'^2 dd
+    2 pi R = pi/(2R) (int phi'^2 dd = 2 sqrt2/(3 eps)), up to O((eps/R)^2)
+    and discretisation errors (about 0.3 % here)."""
+    N, L, eps = 512, 4.0, 0.04
+    phi = I.vesicle_phi(N, L, eps, (L / 2, L / 2), lambda th: R + 0 * th)
+    m = model(N, eps=eps, L=L, gamma_bend=1.0)
+    e = O.physical_energy(phi, np.full_like(phi, 0.5), m, 0.0)
+    assert e["bend"] == pytest.approx(math.pi / (2 * R), rel=1e-2)
+
+
 @pytest.mark.parametrize("which", ["S", "H", "Q", "K", "P"])
 def test_variational_derivatives(which):
     """P6: (F, delta)_h equals the derivative of the matching discrete SAV
