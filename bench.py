@@ -31,11 +31,28 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 HBM_FALLBACK_GBS = 6800.0
-PASSES = {  # algorithmic field passes (reads + writes of N x N fields) per launch
+# Field passes (N x N reads + writes) per launch of each step kernel as
+# implemented (the stencil's 8 outputs are written and re-read by the row
+# transform; the inverse-row kernel reads the four levels of the increment form).
+PASSES = {
     "k_stencil": 12, "k_rowdct_T": 16, "k_coldct_gram": 15, "k_solve": 0,
     "k_comb_icolT": 9, "k_irow": 8,
 }
-STEP_PASSES_MIN_SCHEDULE = 40   # dependency-minimal schedule of one step
+# The dependency-minimal schedule of one step (40 field passes): its phases,
+# the kernels that implement each phase here, and the phase's algorithmic
+# passes (K1 reads 4 levels and writes 8 row-transformed fields; K2 reads 8
+# and writes 7 spectra; K4 reads 7 and writes 2; K5 reads 2 and writes 2).
+PHASES = {
+    "K1 stencil + row DCT": (("k_stencil", "k_rowdct_T"), 12),
+    "K2 column DCT + Gram": (("k_coldct_gram",), 15),
+    "K3 5x5 solve": (("k_solve",), 0),
+    "K4 recovery + inverse column DCT": (("k_comb_icolT",), 9),
+    "K5 inverse row DCT": (("k_irow",), 4),
+}
+STEP_PASSES_MIN_SCHEDULE = sum(p for _, p in PHASES.values())   # 40
+# Files whose code sets the step kernels' DRAM traffic (launch geometry included)
+KERNEL_SOURCES = ("dct_device.cuh", "diag_kernels.cuh", "sim.h", "sim_f32.cu", "sim_f64.cu",
+                  "sim_impl.cuh", "step_kernels.cuh", "warp_fft.cuh", "warp_kernels.cuh")
 
 
 def parse():
@@ -48,7 +65,9 @@ def parse():
     ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--accuracy-steps", type=int, default=1000,
+                    help="steps of the FP32-vs-FP64 accuracy run on the headline workload")
     ap.add_argument("--dct-sweep", action="store_true",
                     help="only the sweep over N of the line-transform kernels (warp path) and of the "
                          "step with the warp-FFT against the block-FFT kernels; one JSON line")
@@ -76,9 +95,12 @@ def code_text(src):
 
 
 def source_hash():
+    """Hash of the step kernels' code (comments and layout ignored)."""
     h = hashlib.sha1()
     csrc = os.path.join(ROOT, "paper_2601_10057_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
+        if f not in KERNEL_SOURCES:
+            continue
         with open(os.path.join(csrc, f), encoding="utf-8") as fh:
             h.update(f.encode() + code_text(fh.read()).encode())
     return h.hexdigest()[:12]
@@ -175,20 +197,72 @@ def barrier(world):
         dist.barrier()
 
 
-def cpu_oracle_sample(w, seconds, max_steps=None):
-    """Time the FP64 oracle (as it stands) on the host cores."""
-    from oracle import ccmsav_oracle as O
-    m = O.Model.from_params(w.N, w.params)
-    s = O.initial_state(w.phi0, w.psi0, m)
-    s = O.step(s, m)                    # the BDF1 start step, untimed
-    n, t0 = 0, time.perf_counter()
-    while True:
-        s = O.step(s, m)
-        n += 1
-        el = time.perf_counter() - t0
-        if el >= seconds or (max_steps and n >= max_steps):
-            break
-    return w.N * w.N * n / el, n, el
+ORACLE_SAMPLE = r"""
+import json, sys, time
+sys.path.insert(0, sys.argv[1])
+from oracle import ccmsav_oracle as O
+from paper_2601_10057_gb300 import inputs as I
+w = I.three_vesicles(N=int(sys.argv[2]), seed=int(sys.argv[3]))
+seconds = float(sys.argv[4])
+m = O.Model.from_params(w.N, w.params)
+s = O.step(O.initial_state(w.phi0, w.psi0, m), m)   # the BDF1 start step, untimed
+n, t0 = 0, time.perf_counter()
+while True:
+    s = O.step(s, m)
+    n += 1
+    el = time.perf_counter() - t0
+    if el >= seconds:
+        break
+print(json.dumps({"value": w.N * w.N * n / el, "steps": n, "seconds": el}))
+"""
+
+
+def cpu_oracle_sample(N, seed, seconds, threads=None):
+    """Time the FP64 oracle (as it stands) on the host cores in a child
+    process (no GPU use): all cores, or `threads` BLAS/OpenMP threads."""
+    env = dict(os.environ)
+    if threads:
+        for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = str(threads)
+    r = subprocess.run([sys.executable, "-c", ORACLE_SAMPLE, ROOT, str(N), str(seed), str(seconds)],
+                       capture_output=True, text=True, env=env, timeout=20 * seconds + 600)
+    if r.returncode != 0:
+        raise RuntimeError(r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def accuracy_vs_fp64(ws, steps, sh):
+    """FP32-bulk against the FP64 GPU path (which matches the oracle to
+    1e-12) after `steps` steps from the same initial states: phi and psi
+    max-abs error relative to the FP64 field's max-norm and RMS error
+    relative to its RMS (maxima over the simulations), and the relative
+    drift of the stored mass h^2 sum psi in both precisions."""
+    import numpy as np
+    from paper_2601_10057_gb300 import ccmsav as cc
+    out = {}
+    for prec in ("fp64", "fp32"):
+        sim = cc.Simulation(None if len(ws) > 1 else ws[0].params, [w.N for w in ws],
+                            per_sim=[w.params for w in ws] if len(ws) > 1 else None, precision=prec, stream=sh)
+        for j, w in enumerate(ws):
+            sim.set_state(w.phi0, w.psi0, sim=j)
+        sim.step(steps)
+        sim.sync()
+        out[prec] = [(*sim.state(sim=j), sim.mass(sim=j)) for j in range(len(ws))]
+        sim.close()
+    e = {"steps": steps, "phi_max": 0.0, "phi_l2": 0.0, "psi_max": 0.0, "psi_l2": 0.0,
+         "mass_drift_fp32": 0.0, "mass_drift_fp64": 0.0}
+    for j, w in enumerate(ws):
+        (p64, q64, m64), (p32, q32, m32) = out["fp64"][j], out["fp32"][j]
+        m0 = (w.params.L / w.N) ** 2 * math.fsum(w.psi0.ravel().tolist())
+        e["phi_max"] = max(e["phi_max"], float(np.abs(p32 - p64).max() / np.abs(p64).max()))
+        e["psi_max"] = max(e["psi_max"], float(np.abs(q32 - q64).max() / np.abs(q64).max()))
+        e["phi_l2"] = max(e["phi_l2"], float(np.sqrt(np.mean((p32 - p64) ** 2) / np.mean(p64 ** 2))))
+        e["psi_l2"] = max(e["psi_l2"], float(np.sqrt(np.mean((q32 - q64) ** 2) / np.mean(q64 ** 2))))
+        e["mass_drift_fp32"] = max(e["mass_drift_fp32"], abs(m32 - m0) / abs(m0))
+        e["mass_drift_fp64"] = max(e["mass_drift_fp64"], abs(m64 - m0) / abs(m0))
+    e = {k: (float(f"{v:.3g}") if isinstance(v, float) else v) for k, v in e.items()}
+    e["reference"] = "FP64 GPU path (itself within 1e-12 of the oracle)"
+    return e
 
 
 def run_reference(args, world, rank):
@@ -259,12 +333,13 @@ def extra_workloads(sh, stream):
         return out
 
     res = {}
-    for name, make, k in (("batch64_N128-512", lambda: I.batch_64(), 60),
-                          ("three_vesicles_N4096", lambda: [I.three_vesicles(N=4096)], 30),
-                          ("lattice16_N8192", lambda: [I.lattice_16(N=8192)], 12)):
+    for name, make, k, ka in (("batch64_N128-512", lambda: I.batch_64(), 60, 200),
+                              ("three_vesicles_N4096", lambda: [I.three_vesicles(N=4096)], 30, 100),
+                              ("lattice16_N8192", lambda: [I.lattice_16(N=8192)], 12, 20)):
         try:
             ws = make()
             res[name] = run(ws, k)
+            res[name]["accuracy"] = accuracy_vs_fp64(ws, ka, sh)
             if len(ws) > 1:
                 res[name]["sizes"] = {str(n): sum(1 for w in ws if w.N == n) for n in sorted({w.N for w in ws})}
         except Exception as e:             # reported, not fatal: the headline line still prints
@@ -273,6 +348,34 @@ def extra_workloads(sh, stream):
 
 
 ALG_BYTES_FP32 = {"k_rowdct_T": 64, "k_coldct_gram": 60, "k_comb_icolT": 36, "k_irow": 32}
+
+
+def phase_roofline(per_launch, NN, esize, peak, peak_kind, workload):
+    """Roofline of the dominant phase of the 40-pass schedule: the phase's
+    algorithmic bytes per step (its passes x N^2 x element size) over the
+    summed event times of the kernels that implement it, against the measured
+    copy bandwidth; traffic = the ncu DRAM bytes of those kernels per step
+    (null when the committed capture is of other kernel sources)."""
+    times = {ph: sum(per_launch[k] for k in ks) for ph, (ks, _) in PHASES.items()}
+    dom = max((ph for ph in PHASES if PHASES[ph][1] > 0), key=lambda ph: times[ph])
+    ks, passes = PHASES[dom]
+    alg = passes * NN * esize
+    achieved = alg / (times[dom] * 1e-3) / 1e9
+    tr = [ncu_traffic(k, workload) for k in ks]
+    traffic = sum(tr) if all(t is not None for t in tr) else None
+    step_tr = [ncu_traffic(k, workload) for k in PASSES]
+    step_traffic = sum(step_tr) if all(t is not None for t in step_tr) else None
+    phases = {ph: {"us": round(1e3 * times[ph], 2), "alg_passes": p,
+                   "frac": (round(p * NN * esize / (times[ph] * 1e-3) / 1e9 / peak, 4) if p and times[ph] > 0 else None)}
+              for ph, (_, p) in PHASES.items()}
+    return {"bound": "hbm", "unit": "GB/s", "phase": dom, "kernels": list(ks),
+            "achieved": round(achieved, 1), "peak": peak, "peak_kind": peak_kind,
+            "frac": round(achieved / peak, 4), "traffic": traffic, "alg_bytes_per_launch": alg,
+            "traffic_ratio_step": (round(step_traffic / (STEP_PASSES_MIN_SCHEDULE * NN * esize), 3)
+                                   if step_traffic else None),
+            "phases": phases,
+            "timing": "per-kernel CUDA events recorded between the kernels of traced steps (direct launches, "
+                      "no graph); their sum exceeds the graph-launched step time by the gaps between launches"}
 
 
 def dct_sweep():
@@ -378,12 +481,11 @@ def run_ours(args, world, rank, local):
     cc.ccmsav_profile(sim.h, False)
     sim.sync()
     per_launch = {cc.KERNEL_NAMES[i]: ms[i] / max(nst, 1) for i in (0, 1, 2, 3, 4, 5)}
-    dom = max(per_launch, key=per_launch.get)
     peak, peak_kind = measured_peaks()
-    alg_bytes = PASSES[dom] * NN * esize
-    achieved = alg_bytes / (per_launch[dom] * 1e-3) / 1e9
+    roof = phase_roofline(per_launch, NN, esize, peak, peak_kind, f"three_vesicles_N{w.N}_{args.precision}")
     kernels = {k: {"ms_per_launch": round(v, 5), "share": round(v / sum(per_launch.values()), 4),
-                   "alg_GBps": (round(PASSES[k] * NN * esize / (v * 1e-3) / 1e9, 1) if v > 0 and PASSES[k] else None)}
+                   "impl_passes": PASSES[k],
+                   "impl_GBps": (round(PASSES[k] * NN * esize / (v * 1e-3) / 1e9, 1) if v > 0 and PASSES[k] else None)}
                for k, v in per_launch.items()}
     sim.close()
     # ---- FP64 step on the same workload (secondary)
@@ -403,6 +505,10 @@ def run_ours(args, world, rank, local):
         s64.close()
         fp64 = {"value": NN * k64 / t64, "ms_per_step": 1e3 * t64 / k64, "steps": k64,
                 "speedup_fp32_over_fp64": (NN * args.steps / secs) / (NN * k64 / t64)}
+    # ---- accuracy of the timed precision against the FP64 GPU path (1000 steps: the precision target)
+    acc = None
+    if args.precision == "fp32" and not args.no_fp64 and rank == 0 and args.accuracy_steps > 0:
+        acc = accuracy_vs_fp64([w], args.accuracy_steps, sh)
     # ---- the method's other workloads, device-timed (secondary lines)
     extra = None
     if not args.no_extra and rank == 0 and world == 1 and args.precision == "fp32":
@@ -437,13 +543,19 @@ def run_ours(args, world, rank, local):
     # ---- CPU baseline (oracle on the host cores, rank 0, N = 1 only)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, n, el = cpu_oracle_sample(w, args.cpu_seconds)
-        cpu = {"value": v, "unit": "grid-point-steps/s", "cores": os.cpu_count(), "kind": "oracle",
-               "sample": f"{n} BDF2 step(s) of the FP64 CPU oracle on the same N={w.N} workload "
-                         f"({el:.1f} s; numpy/OpenBLAS on all host cores)"}
+        seed = 1003 + rank
+        allc = cpu_oracle_sample(w.N, seed, args.cpu_seconds)
+        one = cpu_oracle_sample(w.N, seed, args.cpu_seconds, threads=1)
+        cpu = {"value": allc["value"], "unit": "grid-point-steps/s", "cores": os.cpu_count(), "kind": "oracle",
+               "sample": f"{allc['steps']} BDF2 step(s) of the FP64 CPU oracle on the same N={w.N} workload "
+                         f"({allc['seconds']:.1f} s; numpy with OpenBLAS on all {os.cpu_count()} host cores; "
+                         f"its DCT is the O(N^3) cosine-matrix product, O(N) per coefficient)",
+               "one_thread": {"value": one["value"], "cores": 1,
+                              "sample": f"{one['steps']} BDF2 step(s), {one['seconds']:.1f} s, "
+                                        "OPENBLAS_NUM_THREADS=OMP_NUM_THREADS=1"},
+               "complexity": "O(N^3) per 2D transform (cosine-matrix DCT), 14 one-way transforms per step"}
     if rank != 0:
         return
-    traffic = ncu_traffic(dom, f"three_vesicles_N{w.N}_{args.precision}")
     line = {
         "metric": "grid-point-steps/s", "value": value, "unit": "grid-point-steps/s",
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
@@ -453,14 +565,16 @@ def run_ours(args, world, rank, local):
                    ("fp32-bulk/fp64-reductions" if args.precision == "fp32" else "fp64"),
                    "dt": w.params.dt, "vesicles": 3, "parallelism": f"replicas{world}",
                    "l2": "per-step working set > L2 (no flush needed)"},
-        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peak,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": traffic, "alg_bytes_per_launch": alg_bytes},
+        "roofline": roof,
         "step_roofline": {"alg_bytes_per_point": STEP_PASSES_MIN_SCHEDULE * esize,
                           "achieved_GBps": round(value / world * STEP_PASSES_MIN_SCHEDULE * esize / 1e9, 1),
-                          "frac": round(value / world * STEP_PASSES_MIN_SCHEDULE * esize / 1e9 / peak, 4)},
+                          "peak": peak, "frac": round(value / world * STEP_PASSES_MIN_SCHEDULE * esize / 1e9 / peak, 4),
+                          "floor_frac": round(value / world * 6 * esize / 1e9 / peak, 4),
+                          "what": "whole step against the 40-pass dependency-minimal schedule (160 B/pt FP32); "
+                                  "floor_frac against the 6-pass floor (read 4 levels, write 2)"},
         "kernels": kernels,
         "fp64": fp64,
+        "accuracy": acc,
         "workloads": extra,
         "e2e": {"value": e2e_value, "unit": "grid-point-steps/s", "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h, "steps": k_e2e,
