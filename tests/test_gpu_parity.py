@@ -1,9 +1,14 @@
 """GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
 
 FP64: every field and SAV within 1e-12 relative to the oracle's max-norm
-(the target stated for the FP64 step); the FFT-based DCT, the spectral
-(Parseval) Gram sums and the oracle's cosine-matrix products and physical
-inner products round differently, so results are not bit-identical.
+(the target stated for the FP64 step) over short runs; the FFT-based DCT,
+the spectral (Parseval) Gram sums and the oracle's cosine-matrix products and
+physical inner products round differently, so results are not bit-identical.
+Over hundreds of steps this stiff system amplifies any change of rounding
+order: the oracle itself, with its DCT evaluated by scipy's FFT-based
+routine instead of the cosine matrix, moves by 3.8e-12 (N = 64, 200 steps).
+Long runs are therefore bounded by twice that measured spread of the oracle
+(rounding_spread below), never by less than 1e-12.
 FP32-bulk: within bounds derived from FP32 rounding (see each test).
 """
 import math
@@ -48,20 +53,48 @@ def rel(a, b):
     return float(np.abs(a - b).max() / max(np.abs(b).max(), 1e-300))
 
 
-def check_fp64(w, nsteps, tol=1e-12):
+def savs(s):
+    return np.array([s.V, s.U, s.W, s.Z, s.V_old, s.U_old, s.W_old, s.Z_old])
+
+
+def sav_err(sav, s):
+    """SAV differences on the scale of each SAV (U, a small difference of
+    O(A) quantities, on the scale of A)."""
+    scale = np.array([abs(s.V), abs(s.A), abs(s.W), abs(s.Z)] * 2)
+    return float((np.abs(np.asarray(sav) - savs(s)) / np.maximum(scale, 1e-300)).max())
+
+
+def rounding_spread(w, nsteps, s_ref):
+    """How far the oracle moves when only the rounding order of its DCT
+    changes: the same oracle run with scipy's FFT-based orthonormal DCT in
+    place of the cosine-matrix products.  Returns (phi, psi, sav) spreads."""
+    import scipy.fft as sfft
+    d2, i2 = O.dct2d, O.idct2d
+    try:
+        O.dct2d = lambda u: sfft.dctn(u, type=2, norm="ortho")
+        O.idct2d = lambda U: sfft.idctn(U, type=2, norm="ortho")
+        _, s2 = run_oracle(w, nsteps)
+    finally:
+        O.dct2d, O.idct2d = d2, i2
+    return rel(s2.phi, s_ref.phi), rel(s2.psi, s_ref.psi), sav_err(savs(s2), s_ref)
+
+
+def check_fp64(w, nsteps, tol=1e-12, spread=False):
+    """GPU FP64 against the oracle: fields and SAVs within tol relative to
+    the max-norm (SAVs on their own scale); with spread=True the bound of
+    each quantity is max(tol, 2 x the oracle's own rounding spread)."""
     sim, phi, psi, aux = run_gpu(w, nsteps)
     m, s = run_oracle(w, nsteps)
-    e_phi, e_psi = rel(phi, s.phi), rel(psi, s.psi)
-    sav_g = aux[:8]
-    sav_o = np.array([s.V, s.U, s.W, s.Z, s.V_old, s.U_old, s.W_old, s.Z_old])
-    e_sav = np.abs(sav_g - sav_o) / np.maximum(np.abs(sav_o), 1e-300)
-    scale = np.array([abs(s.V), abs(s.A), abs(s.W), abs(s.Z)] * 2)
-    e_sav_abs = np.abs(sav_g - sav_o) / np.maximum(scale, 1e-300)
-    msg = f"N={w.N} steps={nsteps} phi {e_phi:.3e} psi {e_psi:.3e} sav {e_sav_abs.max():.3e}"
+    e_phi, e_psi, e_sav = rel(phi, s.phi), rel(psi, s.psi), sav_err(aux[:8], s)
+    b_phi = b_psi = b_sav = tol
+    msg = f"N={w.N} steps={nsteps} phi {e_phi:.3e} psi {e_psi:.3e} sav {e_sav:.3e}"
+    if spread:
+        r_phi, r_psi, r_sav = rounding_spread(w, nsteps, s)
+        b_phi, b_psi, b_sav = max(tol, 2 * r_phi), max(tol, 2 * r_psi), max(tol, 2 * r_sav)
+        msg += f" | oracle rounding spread phi {r_phi:.3e} psi {r_psi:.3e} sav {r_sav:.3e}"
     print(msg)
-    assert e_phi <= tol and e_psi <= tol, msg
-    # U is a small difference of O(A) quantities: compare on the scale of A
-    assert e_sav_abs.max() <= 100 * tol, msg
+    assert e_phi <= b_phi and e_psi <= b_psi, msg
+    assert e_sav <= b_sav, msg
     assert aux[10] == nsteps
     sim.close()
     return e_phi, e_psi
@@ -80,10 +113,34 @@ def test_fp64_start_step_only():
 
 
 def test_fp64_one_vesicle_N64_200_steps():
-    """The small workload: one vesicle, N = 64, 200 steps at dt = 1e-4."""
+    """The small workload: one vesicle, N = 64, 200 steps at dt = 1e-4.
+    Measured on GB300: phi 3.0e-12, psi 4.0e-13 against the oracle, while
+    the oracle with another DCT rounding order moves by 3.8e-12 / 6.2e-13:
+    the bound is twice that spread."""
     w = I.workload("one_vesicle", N=64)
     assert w.params.dt == 1e-4 and w.steps == 200
-    check_fp64(w, 200, tol=1e-11)
+    check_fp64(w, 200, spread=True)
+
+
+@pytest.mark.slow
+def test_fp64_ellipse_N512_1000_steps():
+    """The shrinking-ellipse workload at full length: N = 512, 1000 steps at
+    dt = 1e-5 against the oracle, bounded by twice the oracle's own rounding
+    spread over the same run (measured on GB300: GPU phi 5.1e-11, psi
+    3.9e-11; the oracle takes about a minute per run on 16 Arm cores)."""
+    w = I.workload("ellipse_shrink", N=512)
+    assert w.params.dt == 1e-5 and w.steps == 1000
+    check_fp64(w, 1000, spread=True)
+
+
+@pytest.mark.slow
+def test_fp64_lattice_N8192_two_steps():
+    """The largest grid (sixteen vesicles, N = 8192, lines of 4096 complex
+    values in the block FFT): the start step and the first BDF2 step against
+    the oracle at every point, within 1e-12 (measured 6.4e-14; the oracle
+    takes about two minutes on 16 Arm cores)."""
+    w = I.workload("lattice16", N=8192)
+    check_fp64(w, 2)
 
 
 def test_fp64_ellipse_N256_30_steps():
@@ -278,14 +335,14 @@ def test_batched_graph_steps_match_single_runs(caller_stream):
     sim.close()
 
 
-@pytest.mark.slow
-def test_fp32_against_fp64_after_1000_steps_N2048():
-    """The precision form at full size: three vesicles, N = 2048, 1000 steps
-    at dt = 1e-5, FP32-bulk against the FP64 GPU path (itself within 1e-12 of
-    the oracle).  Measured: phi max 4.1e-5 / L2 1.9e-6, psi max 6.8e-6 / L2
-    2.6e-7 relative to the max-norm / RMS of the FP64 fields; the bounds
-    below leave about 2x room.  Stored mass of both paths within 5e-11 of the
-    initial mass."""
+_FP32_1000 = {}
+
+
+def fp32_vs_fp64_1000_steps():
+    """Errors of the FP32-bulk path against the FP64 path after 1000 steps
+    at N = 2048 (three vesicles, dt = 1e-5), computed once per session."""
+    if _FP32_1000:
+        return dict(_FP32_1000)
     w = I.workload("three_vesicles", N=2048)
     res = {}
     for prec in ("fp64", "fp32"):
@@ -301,10 +358,66 @@ def test_fp32_against_fp64_after_1000_steps_N2048():
          "phi_l2": float(np.sqrt(np.mean((p32 - p64) ** 2) / np.mean(p64 ** 2))),
          "psi_l2": float(np.sqrt(np.mean((q32 - q64) ** 2) / np.mean(q64 ** 2))),
          "mass32": abs(m32 - m0) / m0, "mass64": abs(m64 - m0) / m0}
+    _FP32_1000.update(e)
+    return dict(e)
+
+
+@pytest.mark.slow
+def test_fp32_against_fp64_after_1000_steps_N2048():
+    """The precision form at full size: three vesicles, N = 2048, 1000 steps
+    at dt = 1e-5, FP32-bulk against the FP64 GPU path (itself within 1e-12 of
+    the oracle).  Measured: phi max 4.1e-5 / L2 1.9e-6, psi max 6.8e-6 / L2
+    2.6e-7 relative to the max-norm / RMS of the FP64 fields; the bounds
+    below sit just above those values (regression bounds).  Stored mass of
+    both paths within 5e-11 of the initial mass."""
+    e = fp32_vs_fp64_1000_steps()
     print("fp32 vs fp64 after 1000 steps", e)
-    assert e["phi_l2"] < 5e-6 and e["psi_l2"] < 1e-6, e
-    assert e["phi_max"] < 1e-4 and e["psi_max"] < 2e-5, e
+    # regression bounds at the measured level (1.2 - 2x); the 1e-5 max-norm
+    # target itself is the strict xfail test below
+    assert e["phi_l2"] < 4e-6 and e["psi_l2"] < 5e-7, e
+    assert e["phi_max"] < 5e-5 and e["psi_max"] < 1e-5, e
     assert e["mass32"] < 5e-11 and e["mass64"] < 5e-11, e
+
+
+@pytest.mark.slow
+@pytest.mark.xfail(strict=True, reason="FP32-bulk phi max-norm error after 1000 steps at N = 2048 is 4.1e-5, "
+                                       "above the 1e-5 target (RMS error 1.8e-6 meets it)")
+def test_fp32_meets_1e5_max_norm_target_after_1000_steps_N2048():
+    """The precision target as stated: phi and psi within 1e-5 of the FP64
+    path in the max-norm after 1000 steps at N = 2048."""
+    e = fp32_vs_fp64_1000_steps()
+    assert e["phi_max"] <= 1e-5 and e["psi_max"] <= 1e-5, e
+
+
+@pytest.mark.slow
+def test_fp64_with_fp32_storage_after_1000_steps_N2048():
+    """What FP32 storage of the levels alone costs: the FP64 path with phi
+    and psi (both levels) rounded to FP32 after every step, through the
+    checkpoint calls (get_state / get_prev_state / get_aux, set_state_levels
+    / set_aux), against plain FP64.  Measured: phi max 1.0e-6, psi max
+    9.7e-7 -- 40x below the FP32-bulk path's phi error, so that error comes
+    from the FP32 arithmetic inside the step, not from storing the fields."""
+    w = I.workload("three_vesicles", N=2048)
+    f32 = lambda a: a.astype(np.float32).astype(np.float64)
+    ref = cc.Simulation(w.params, w.N, precision="fp64")
+    ref.set_state(f32(w.phi0), f32(w.psi0))
+    ref.step(1000)
+    p64, q64 = ref.state()
+    ref.close()
+    sim = cc.Simulation(w.params, w.N, precision="fp64")
+    sim.set_state(f32(w.phi0), f32(w.psi0))
+    for _ in range(1000):
+        sim.step(1)
+        a, b = sim.state()
+        c, d = sim.state(prev=True)
+        aux = sim.aux()
+        sim.set_levels(f32(a), f32(b), f32(c), f32(d))
+        sim.set_aux(aux)
+    p, q = sim.state()
+    sim.close()
+    e = (rel(p, p64), rel(q, q64))
+    print("fp64 with fp32 storage after 1000 steps", e)
+    assert max(e) < 3e-6, e
 
 
 def test_fp32_warp_path_N4096_against_fp64():
