@@ -2,25 +2,27 @@
 // of a caller-owned device field, computed without any allocation by the
 // library.
 //
-// Some callers cannot let a library allocate device memory: code running
-// while a stream is being captured into a CUDA graph (an allocation there
-// can force a synchronisation the capture forbids), services whose device
-// memory is reserved up front by a pooling allocator or capped by a
-// framework, and real-time loops that must not pay allocation latency or
-// fragment the heap.  For them this entry point takes its scratch (one FP64
-// partial sum per reduction block plus the final sum) from a fixed array
-// compiled into the library.  Every GPU that loads the library holds that
-// array (kScratchDoubles doubles, under 10 KB) until the process exits.
+// Some callers cannot let a library allocate device memory: services whose
+// device memory is reserved up front by a pooling allocator or capped by a
+// framework (a cudaMalloc there either fails or steals from the pool), and
+// real-time loops that must not pay allocation latency or fragment the heap.
+// For them this entry point takes its scratch (one FP64 partial sum per
+// reduction block plus the final sum) from a fixed array compiled into the
+// library.  Every GPU that loads the library holds that array
+// (kScratchDoubles doubles, under 10 KB, whatever N is) until the process
+// exits.
 //
 // The array's name, used in host code, is only a host-side stand-in for the
 // device symbol: a kernel handed it would fault or, where the GPU can reach
 // host memory, silently use the wrong memory.  So the first call on each
 // device looks up the real device address with cudaGetSymbolAddress (with
-// that device current) and caches it; that first call should therefore come
-// before any stream capture.  All calls share the array and it keeps the
-// last call's contents: every slot a call reads is written earlier in the
-// same call, so nothing needs clearing, but calls whose work overlaps on the
-// GPU (other streams, other host threads) race on it.
+// that device current) and keeps it for later calls on that device.  The
+// address belongs to the device's primary context: after cudaDeviceReset()
+// on a device, this entry point must not be called on it again in the same
+// process.  All calls share the array and it keeps the last call's contents:
+// every slot a call reads is written earlier in the same call, so nothing
+// needs clearing, but calls whose work overlaps on the GPU (other streams,
+// other host threads) race on it.
 #include <mutex>
 #include <cuda_runtime.h>
 #include "../../include/ccmsav.h"
@@ -94,13 +96,19 @@ extern "C" int ccmsav_mass_noalloc(const void* psi, int N, int precision, double
     const size_t n = (size_t)N * N;
     int nb = (int)((n + kThreads - 1) / kThreads);
     if (nb > kBlocks) nb = kBlocks;
-    if (precision == CCMSAV_FP64)
-        k_mass_partials<double><<<nb, kThreads, 0, st>>>(static_cast<const double*>(psi), n, scratch);
-    else
-        k_mass_partials<float><<<nb, kThreads, 0, st>>>(static_cast<const float*>(psi), n, scratch);
+    // cudaLaunchKernel returns this launch's own status (an error left over
+    // from earlier work of the caller is not taken for ours)
+    void* psi_arg = const_cast<void*>(psi);
+    size_t n_arg = n;
+    void* part_args[] = {&psi_arg, &n_arg, &scratch};
+    const void* kpart = precision == CCMSAV_FP64 ? (const void*)k_mass_partials<double>
+                                                 : (const void*)k_mass_partials<float>;
+    if (cudaLaunchKernel(kpart, dim3(nb), dim3(kThreads), part_args, 0, st) != cudaSuccess) return CCMSAV_ECUDA;
     const double h = L / N;
-    k_mass_final<<<1, kThreads, 0, st>>>(scratch, nb, h * h);
-    if (cudaGetLastError() != cudaSuccess) return CCMSAV_ECUDA;
+    double h2 = h * h;
+    void* fin_args[] = {&scratch, &nb, &h2};
+    if (cudaLaunchKernel((const void*)k_mass_final, dim3(1), dim3(kThreads), fin_args, 0, st) != cudaSuccess)
+        return CCMSAV_ECUDA;
     if (cudaMemcpyAsync(mass, scratch + kBlocks, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess)
         return CCMSAV_ECUDA;
     if (cudaStreamSynchronize(st) != cudaSuccess) return CCMSAV_ECUDA;

@@ -1,10 +1,14 @@
 """ccmsav_mass_noalloc: the allocation-free mass entry point, through the C
-ABI, against ccmsav_mass() on the same stored field, on two calls in a row.
+ABI, against ccmsav_mass() on the same stored field and against an exactly
+rounded host sum (math.fsum), on two calls in a row.
 
-Some callers cannot let the library allocate device memory (stream capture,
-pooled or capped device memory, real-time loops); this entry point serves
-them from a fixed scratch array inside the library.  The file is named so
-that pytest collects it last."""
+Some callers cannot let the library allocate device memory (device memory
+reserved up front by a pooling allocator or capped by a framework, real-time
+loops that must not pay allocation latency); this entry point serves them
+from a fixed scratch array inside the library.  The file is named so that
+pytest collects it last."""
+import math
+
 import numpy as np
 import pytest
 
@@ -38,6 +42,9 @@ def test_mass_noalloc_matches_ccmsav_mass(precision):
         got.append(m)
     assert got[0] == got[1]
     assert got[0] == pytest.approx(m_ref, rel=1e-12)
+    h = w.params.L / w.N
+    exact = h * h * math.fsum(psi.ravel().tolist())
+    assert got[0] == pytest.approx(exact, rel=1e-12)
     sim.close()
 
 
