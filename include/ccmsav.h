@@ -191,31 +191,91 @@ long long ccmsav_launch_count(ccmsav_t* h);
 int ccmsav_profile(ccmsav_t* h, int enable);
 int ccmsav_profile_read(ccmsav_t* h, int sim, double ms[8], long long* nsteps);
 
-/* Largest grid side accepted by ccmsav_mass_noalloc(). */
+/* Largest grid side accepted by ccmsav_mass_noalloc(): the largest grid a
+ * handle accepts.  The scratch does not grow with N (see below). */
 #define CCMSAV_NOALLOC_MAX_N 8192
 
 /* ccmsav_mass_noalloc -- h^2 * sum_ij psi_ij (h = L / N) of a caller-owned
  * device field, with no device or host allocation by the library.
  * The paper has no counterpart: this is a service for callers that cannot
- * let a library allocate, e.g. code running while a stream is captured into
- * a CUDA graph, services whose device memory is reserved up front by a
- * pooling allocator, or real-time loops that must not pay allocation
- * latency.  It computes what ccmsav_mass() computes for a handle's state,
- * but for any N x N field the caller holds.
+ * let a library allocate, e.g. services whose device memory is reserved up
+ * front by a pooling allocator or capped by a framework, or real-time loops
+ * that must not pay allocation latency.  It computes what ccmsav_mass()
+ * computes for a handle's state, but for any N x N field the caller holds.
  *   psi        device pointer, N*N values, FP64 (precision CCMSAV_FP64) or
  *              FP32 (CCMSAV_FP32_BULK); summed in FP64 in a fixed order
  *   N          1 <= N <= CCMSAV_NOALLOC_MAX_N, else CCMSAV_EINVAL
  *   L          domain side (> 0)
  *   mass       host pointer to one double (output)
- *   stream     cudaStream_t the work is queued on; the call synchronises it
- * Scratch is a fixed array of under 10 KB compiled into the library; every
- * GPU that loads the library holds it until the process exits.  The first
- * call on a device looks up that array's device address (with the device
- * current), so make the first call before any stream capture.  All calls
- * share the array: calls whose work overlaps on the GPU (different streams
- * or host threads) race and must be serialised by the caller. */
+ *   stream     cudaStream_t the work is queued on; the call copies the result
+ *              to *mass and synchronises that stream before it returns
+ * Returns CCMSAV_ECUDA if a launch, the copy or the synchronisation fails.
+ * Scratch is a fixed array of 1185 doubles (under 10 KB, whatever N is)
+ * compiled into the library; every GPU that loads the library holds it until
+ * the process exits.  The first call on a device looks up that array's
+ * device address (with the device current) and keeps it; after
+ * cudaDeviceReset() on that device the function must not be called there
+ * again in the same process.  All calls share the array: calls whose work
+ * overlaps on the GPU (different streams or host threads) race and must be
+ * serialised by the caller. */
 int ccmsav_mass_noalloc(const void* psi, int N, int precision, double L,
                         double* mass, void* stream);
+
+/* ---------------------------------------------------------------------------
+ * Standalone constant-coefficient spectral solver and initial-condition
+ * smoother.
+ *
+ * ccmsav_solver_solve computes u = (c0 - c1 Lap_h + c2 Lap_h^2)^{-1} f on an
+ * N x N cell-centred grid (h = L / N) with the 5-point Laplacian Lap_h and
+ * one of three boundary rules, by forward transform, division by the
+ * closed-form eigenvalues and inverse transform (Appendix C; the paper's
+ * closing remarks name the DST and the FFT as the fast solvers for Dirichlet
+ * and periodic boundaries):
+ *   CCMSAV_BC_NEUMANN    mirror ghosts (u_{-1} = u_0, Appendix D), DCT-II/III;
+ *   CCMSAV_BC_DIRICHLET  odd ghosts (u_{-1} = -u_0: u = 0 on the boundary
+ *                        faces), DST-II/III;
+ *   CCMSAV_BC_PERIODIC   wrapped ghosts (u_{-1} = u_{N-1}), complex FFT.
+ * ccmsav_solver_smooth runs the smoother of Appendix F in place on a device
+ * field phi: nsteps steps of the constant-mobility Cahn-Hilliard equation
+ * phi_t = Mob Lap((phi^3 - phi)/eps - eps Lap phi), semi-implicit first order
+ * (the nonlinear term explicit, the biharmonic term implicit):
+ *   (1/dt + Mob eps Lap_h^2) phi^{n+1} = phi^n/dt + Mob Lap_h((phi^n^3 - phi^n)/eps),
+ * each step one solve above, then phi <- max(-1, min(1, phi)).  The paper
+ * uses Mob = 0.01, dt = 1e-6 and ten steps (T = 1e-5) with Neumann ghosts.
+ *
+ * Device pointers f, u, phi hold N*N values of the solver's precision
+ * (FP64 or FP32), row-major, 16-byte aligned; f and u may be the same array.
+ * The calls are asynchronous on the solver's stream (ccmsav_solver_sync waits
+ * for it).  The solver owns its tables and one N x N scratch field (complex
+ * for periodic) and frees them in ccmsav_solver_destroy. */
+#define CCMSAV_BC_NEUMANN   0
+#define CCMSAV_BC_DIRICHLET 1
+#define CCMSAV_BC_PERIODIC  2
+
+typedef struct ccmsav_solver ccmsav_solver_t;   /* opaque solver handle */
+
+/* N a power of two in [8, 8192], L > 0, bc one of CCMSAV_BC_*, precision
+ * CCMSAV_FP64 or CCMSAV_FP32_BULK (FP32 fields and transforms), stream a
+ * cudaStream_t (NULL: a stream owned by the solver).  CCMSAV_EINVAL on a bad
+ * argument, CCMSAV_ENOMEM if device memory runs out. */
+int ccmsav_solver_create(ccmsav_solver_t** out, int N, double L, int bc, int precision, void* stream);
+
+/* coef = {c0, c1, c2}: finite, c1 >= 0, c2 >= 0 and c0 + c1 s + c2 s^2 > 0 at
+ * the smallest eigenvalue s of -Lap_h (0 for Neumann and periodic), else
+ * CCMSAV_EINVAL.  CCMSAV_ECUDA if a launch fails. */
+int ccmsav_solver_solve(ccmsav_solver_t* s, const double coef[3], const void* f, void* u);
+
+/* eps > 0, mobility >= 0, dt > 0, nsteps >= 0 (0: only the clamp). */
+int ccmsav_solver_smooth(ccmsav_solver_t* s, double eps, double mobility, double dt, int nsteps, void* phi);
+
+/* Wait for the solver's queued work. */
+int ccmsav_solver_sync(ccmsav_solver_t* s);
+
+/* Kernel launches queued by the solver since creation. */
+long long ccmsav_solver_launch_count(ccmsav_solver_t* s);
+
+/* Free the solver (synchronises its stream first).  NULL is accepted. */
+void ccmsav_solver_destroy(ccmsav_solver_t* s);
 
 /* Message for a status code (static storage). */
 const char* ccmsav_strerror(int status);

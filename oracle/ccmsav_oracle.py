@@ -596,3 +596,97 @@ def physical_energy(phi, psi, m: Model, A: float) -> Dict[str, float]:
     area = 0.5 * m.gamma_area * (surf - A) ** 2
     return {"surf": m.gamma_surf * surf, "bend": bend, "area": area, "osm": osm,
             "arc_length": surf, "total": m.gamma_surf * surf + bend + area + osm}
+
+
+# --------------------------------------------------------------------------
+# Other boundary rules for the constant-coefficient solve (the paper's closing
+# remarks: DST for Dirichlet, FFT for periodic boundaries) and the
+# initial-condition smoother (Appendix F)
+# --------------------------------------------------------------------------
+
+BCS = ("neumann", "dirichlet", "periodic")
+
+
+def ghost_bc(u: np.ndarray, bc: str) -> np.ndarray:
+    """One ghost layer by the boundary rule: mirror (u_{-1} = u_0), odd
+    (u_{-1} = -u_0, i.e. u = 0 on the boundary face) or periodic wrap."""
+    if bc == "neumann":
+        return np.pad(u, 1, mode="edge")
+    if bc == "dirichlet":
+        g = np.pad(u, 1, mode="edge")
+        g[0, :] *= -1.0
+        g[-1, :] *= -1.0
+        g[:, 0] *= -1.0
+        g[:, -1] *= -1.0
+        return g
+    if bc == "periodic":
+        return np.pad(u, 1, mode="wrap")
+    raise ValueError(bc)
+
+
+def lap_bc(u: np.ndarray, h: float, bc: str) -> np.ndarray:
+    """5-point Laplacian with the ghost layer of the boundary rule."""
+    g = ghost_bc(u, bc)
+    return (g[1:-1, 2:] + g[1:-1, :-2] + g[2:, 1:-1] + g[:-2, 1:-1] - 4.0 * u) / (h * h)
+
+
+def transform_matrix(N: int, bc: str) -> np.ndarray:
+    """Orthonormal (unitary) 1D transform that diagonalises the 1D Laplacian
+    of the boundary rule, written out from its defining sum: DCT-II
+    (Neumann), DST-II C[k, n] = c_k sin(pi (k+1)(2n+1)/(2N)) with
+    c_{N-1} = sqrt(1/N), c_k = sqrt(2/N) otherwise (Dirichlet), and the DFT
+    exp(-2 pi i k n / N)/sqrt(N) (periodic)."""
+    k = np.arange(N, dtype=np.float64)[:, None]
+    n = np.arange(N, dtype=np.float64)[None, :]
+    if bc == "neumann":
+        return dct_matrix(N)
+    if bc == "dirichlet":
+        S = np.sin(math.pi * (k + 1) * (2 * n + 1) / (2 * N))
+        S[:-1, :] *= math.sqrt(2.0 / N)
+        S[-1, :] *= math.sqrt(1.0 / N)
+        return S
+    if bc == "periodic":
+        return np.exp(-2j * math.pi * k * n / N) / math.sqrt(N)
+    raise ValueError(bc)
+
+
+def bc_eigenvalues(N: int, h: float, bc: str) -> np.ndarray:
+    """Eigenvalues of -Lap_h (1D) in the order of transform_matrix:
+    (4/h^2) sin^2(pi k/(2N)), sin^2(pi (k+1)/(2N)), sin^2(pi k/N)."""
+    k = np.arange(N, dtype=np.float64)
+    if bc == "neumann":
+        a = math.pi * k / (2 * N)
+    elif bc == "dirichlet":
+        a = math.pi * (k + 1) / (2 * N)
+    elif bc == "periodic":
+        a = math.pi * k / N
+    else:
+        raise ValueError(bc)
+    return 4.0 / (h * h) * np.sin(a) ** 2
+
+
+def spectral_solve_bc(f: np.ndarray, coef, h: float, bc: str) -> np.ndarray:
+    """u = (c0 - c1 Lap_h + c2 Lap_h^2)^{-1} f: forward transform along both
+    axes, division by c0 + c1 s + c2 s^2 (s = s_k + s_l), inverse transform."""
+    N = f.shape[0]
+    C = transform_matrix(N, bc)
+    e = bc_eigenvalues(N, h, bc)
+    s = e[:, None] + e[None, :]
+    F = C @ f @ C.T
+    U = F / (coef[0] + coef[1] * s + coef[2] * s * s)
+    u = C.conj().T @ U @ C.conj()
+    return np.real(u) if bc == "periodic" else u
+
+
+def smooth_initial(phi: np.ndarray, h: float, eps: float, mobility: float, dt: float,
+                   nsteps: int, bc: str = "neumann") -> np.ndarray:
+    """Appendix F: nsteps of the constant-mobility Cahn-Hilliard equation
+    phi_t = Mob Lap((phi^3 - phi)/eps - eps Lap phi), first order in time
+    with the nonlinear term explicit and the biharmonic term implicit,
+        (1/dt + Mob eps Lap_h^2) phi^{n+1} = phi^n/dt + Mob Lap_h((phi^n^3 - phi^n)/eps),
+    solved by the transform of the boundary rule; then phi is clamped to [-1, 1]."""
+    u = np.array(phi, dtype=np.float64)
+    for _ in range(nsteps):
+        rhs = u / dt + mobility * lap_bc((u ** 3 - u) / eps, h, bc)
+        u = spectral_solve_bc(rhs, (1.0 / dt, 0.0, mobility * eps), h, bc)
+    return np.clip(u, -1.0, 1.0)

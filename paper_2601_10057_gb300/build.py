@@ -1,7 +1,8 @@
 """Build the in-tree CUDA library ``libccmsav.so`` for sm_103a with nvcc.
 
-The three translation units (the C ABI, the FP32-bulk and the FP64
-instantiations) are compiled in parallel and linked into one shared object
+The translation units (the C ABI, the FP32-bulk and the FP64 instantiations
+of the step, the allocation-free mass and the standalone spectral solver) are
+compiled in parallel and linked into one shared object
 next to this file.  ``python -m paper_2601_10057_gb300.build`` runs it.
 """
 from __future__ import annotations
@@ -16,7 +17,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libccmsav.so")
-SOURCES = ["ccmsav_api.cu", "sim_f32.cu", "sim_f64.cu", "ccmsav_noalloc.cu"]
+SOURCES = ["ccmsav_api.cu", "sim_f32.cu", "sim_f64.cu", "ccmsav_noalloc.cu", "spectral_solve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
 

@@ -27,6 +27,10 @@ CCMSAV_ETIMEOUT = -6
 CCMSAV_FP64 = 0
 CCMSAV_FP32_BULK = 1
 CCMSAV_TRACK_ENERGY = 1
+CCMSAV_BC_NEUMANN = 0
+CCMSAV_BC_DIRICHLET = 1
+CCMSAV_BC_PERIODIC = 2
+BC_CODES = {"neumann": CCMSAV_BC_NEUMANN, "dirichlet": CCMSAV_BC_DIRICHLET, "periodic": CCMSAV_BC_PERIODIC}
 
 PARAM_FIELDS = ["gamma_surf", "gamma_bend", "gamma_area", "gamma_in", "gamma_out",
                 "psi_in", "psi_out", "beta_in", "beta_out", "eps", "M_phi", "M0",
@@ -84,6 +88,12 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "ccmsav_profile_read": (i, [vp, i, _DP, C.POINTER(C.c_longlong)]),
         "ccmsav_destroy": (None, [vp]),
         "ccmsav_mass_noalloc": (i, [vp, i, i, d, _DP, vp]),
+        "ccmsav_solver_create": (i, [C.POINTER(vp), i, d, i, i, vp]),
+        "ccmsav_solver_solve": (i, [vp, _DP, vp, vp]),
+        "ccmsav_solver_smooth": (i, [vp, d, d, d, i, vp]),
+        "ccmsav_solver_sync": (i, [vp]),
+        "ccmsav_solver_launch_count": (C.c_longlong, [vp]),
+        "ccmsav_solver_destroy": (None, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -224,6 +234,36 @@ def ccmsav_mass_noalloc(psi_ptr: int, N: int, precision: int, L: float, stream: 
     return st, float(out[0])
 
 
+def ccmsav_solver_create(N: int, L: float, bc: int, precision: int, stream: Optional[int] = None):
+    """Returns (status, solver handle)."""
+    h = C.c_void_p()
+    st = load().ccmsav_solver_create(C.byref(h), int(N), float(L), int(bc), int(precision),
+                                     C.c_void_p(stream) if stream else None)
+    return st, h
+
+
+def ccmsav_solver_solve(s, coef, f_ptr: int, u_ptr: int) -> int:
+    c = _f64(coef)
+    return load().ccmsav_solver_solve(s, _ptr(c), C.c_void_p(f_ptr), C.c_void_p(u_ptr))
+
+
+def ccmsav_solver_smooth(s, eps: float, mobility: float, dt: float, nsteps: int, phi_ptr: int) -> int:
+    return load().ccmsav_solver_smooth(s, float(eps), float(mobility), float(dt), int(nsteps), C.c_void_p(phi_ptr))
+
+
+def ccmsav_solver_sync(s) -> int:
+    return load().ccmsav_solver_sync(s)
+
+
+def ccmsav_solver_launch_count(s) -> int:
+    return int(load().ccmsav_solver_launch_count(s))
+
+
+def ccmsav_solver_destroy(s) -> None:
+    if s:
+        load().ccmsav_solver_destroy(s)
+
+
 # ---------------------------------------------------------------- wrapper
 
 class Simulation:
@@ -289,6 +329,61 @@ class Simulation:
     def close(self):
         if self.h:
             ccmsav_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class SpectralSolver:
+    """Owns one ccmsav_solver handle; fields are torch CUDA tensors of the
+    solver's precision (float64 or float32), N x N, contiguous."""
+
+    def __init__(self, N: int, L: float, bc: str = "neumann", precision: str = "fp64",
+                 stream: Optional[int] = None):
+        prec = CCMSAV_FP64 if precision == "fp64" else CCMSAV_FP32_BULK
+        st, h = ccmsav_solver_create(N, L, BC_CODES[bc], prec, stream)
+        if st != CCMSAV_OK:
+            raise CCMSAVError(st, "ccmsav_solver_create")
+        self.h, self.N, self.precision = h, int(N), precision
+
+    def _chk(self, t):
+        import torch
+        want = torch.float64 if self.precision == "fp64" else torch.float32
+        if t.dtype != want or not t.is_cuda or not t.is_contiguous() or t.numel() != self.N * self.N:
+            raise ValueError(f"expected a contiguous CUDA {want} tensor of {self.N} x {self.N} values")
+        return t.data_ptr()
+
+    def solve(self, coef, f, out=None):
+        """u = (c0 - c1 Lap_h + c2 Lap_h^2)^{-1} f (asynchronous on the solver's stream)."""
+        import torch
+        u = torch.empty_like(f) if out is None else out
+        st = ccmsav_solver_solve(self.h, coef, self._chk(f), self._chk(u))
+        if st != CCMSAV_OK:
+            raise CCMSAVError(st, "ccmsav_solver_solve")
+        return u
+
+    def smooth(self, phi, eps: float, mobility: float = 0.01, dt: float = 1e-6, nsteps: int = 10):
+        """The smoother of Appendix F in place on phi (then clamped to [-1, 1])."""
+        st = ccmsav_solver_smooth(self.h, eps, mobility, dt, nsteps, self._chk(phi))
+        if st != CCMSAV_OK:
+            raise CCMSAVError(st, "ccmsav_solver_smooth")
+        return phi
+
+    def sync(self):
+        st = ccmsav_solver_sync(self.h)
+        if st != CCMSAV_OK:
+            raise CCMSAVError(st, "ccmsav_solver_sync")
+
+    def launches(self) -> int:
+        return ccmsav_solver_launch_count(self.h)
+
+    def close(self):
+        if self.h:
+            ccmsav_solver_destroy(self.h)
             self.h = None
 
     def __del__(self):

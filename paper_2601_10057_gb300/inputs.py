@@ -33,6 +33,7 @@ import numpy as np
 __all__ = [
     "Params", "growth_params", "shrinkage_params", "Workload",
     "vesicle_phi", "concentration", "workload", "WORKLOADS",
+    "SHARP_SHAPES", "sharp_shape", "robustness_params",
 ]
 
 
@@ -324,3 +325,72 @@ def workload(name: str, N: Optional[int] = None, **kw) -> Workload:
     if name.startswith("lattice16"):
         return lattice_16(N=N or 8192, **kw)
     raise KeyError(name)
+
+
+# ---------------------------------------------------------------------------
+# Sharp initial shapes of the robustness runs (the paper names a triangle, a
+# star, an incomplete hexagon and a crescent but gives no dimensions; these
+# are this package's definitions).  phi = +1 at cell centres inside the
+# shape, -1 outside; the smoother of Appendix F turns them into diffuse
+# interfaces before a run.
+# ---------------------------------------------------------------------------
+
+SHARP_SHAPES = ("triangle", "star", "hexagon", "crescent")
+
+
+def _polygon_radius(theta, verts):
+    """Distance from the origin to the boundary of a polygon that is
+    star-shaped about the origin, along the rays at angles theta; verts are
+    (n, 2) vertices in counter-clockwise order of increasing angle."""
+    ang = np.mod(np.arctan2(verts[:, 1], verts[:, 0]), 2 * math.pi)
+    order = np.argsort(ang)
+    verts, ang = verts[order], ang[order]
+    th = np.mod(theta, 2 * math.pi)
+    k = np.searchsorted(ang, th, side="right") - 1          # edge k: vertex k -> k+1 (wrapping)
+    a = verts[k % len(verts)]
+    b = verts[(k + 1) % len(verts)]
+    d = b - a
+    ux, uy = np.cos(th), np.sin(th)
+    cross_ad = a[..., 0] * d[..., 1] - a[..., 1] * d[..., 0]
+    cross_ud = ux * d[..., 1] - uy * d[..., 0]
+    return cross_ad / cross_ud
+
+
+def sharp_shape(kind: str, N: int, L: float = 1.0, R: Optional[float] = None) -> np.ndarray:
+    """Sharp phase field of one centred shape of circumradius R (default
+    L/4): an equilateral triangle with a vertex up; a five-pointed star (inner
+    radius 0.45 R); a regular hexagon with one of its six sectors removed;
+    a crescent (a disc of radius R minus a disc of radius 0.8 R whose centre
+    is shifted by 0.45 R)."""
+    R = L / 4 if R is None else R
+    X, Y = _cell_centres(N, L)
+    x, y = X - L / 2, Y - L / 2
+    r, th = np.hypot(x, y), np.arctan2(y, x)
+    if kind == "triangle":
+        a = math.pi / 2 + 2 * math.pi * np.arange(3) / 3
+        inside = r < _polygon_radius(th, R * np.stack([np.cos(a), np.sin(a)], 1))
+    elif kind == "star":
+        a = math.pi / 2 + math.pi * np.arange(10) / 5
+        rad = np.where(np.arange(10) % 2 == 0, R, 0.45 * R)
+        inside = r < _polygon_radius(th, np.stack([rad * np.cos(a), rad * np.sin(a)], 1))
+    elif kind == "hexagon":
+        a = 2 * math.pi * np.arange(6) / 6
+        hexa = r < _polygon_radius(th, R * np.stack([np.cos(a), np.sin(a)], 1))
+        sector = (np.mod(th, 2 * math.pi) < 2 * math.pi / 6)   # the sector between vertices 0 and 1
+        inside = hexa & ~sector
+    elif kind == "crescent":
+        inside = (r < R) & (np.hypot(x - 0.45 * R, y) > 0.8 * R)
+    else:
+        raise KeyError(kind)
+    return np.where(inside, 1.0, -1.0)
+
+
+def robustness_params(grows: bool, N: int = 2048, L: float = 1.0, eps: float = 0.01,
+                      dt: float = 5e-6) -> Params:
+    """Parameters of the robustness runs: the table's growth or shrinkage
+    column with (gamma_bend, theta) = (0.05, 10) for growth and (0.1, 30)
+    for shrinkage, eps = 0.01, N = 2048, dt = 5e-6 on the unit square (about
+    twenty cells across the interface)."""
+    if grows:
+        return growth_params(gamma_bend=0.05, theta=10.0, eps=eps, dt=dt, L=L)
+    return shrinkage_params(gamma_bend=0.1, theta=30.0, eps=eps, dt=dt, L=L)

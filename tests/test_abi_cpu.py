@@ -66,3 +66,18 @@ def test_create_rejects_bad_precision_and_flags(lib):
     assert cc.ccmsav_create(I.growth_params(), [64], precision=7)[0] == cc.CCMSAV_EINVAL
     assert cc.ccmsav_create(I.growth_params(), [64], flags=8)[0] == cc.CCMSAV_EINVAL
     assert cc.ccmsav_create(I.growth_params(), [])[0] == cc.CCMSAV_EINVAL
+
+
+@pytest.mark.parametrize("N,bc,prec", [(4, 0, 0), (12, 0, 0), (16384, 0, 0), (64, 3, 0), (64, -1, 0), (64, 0, 5)])
+def test_solver_create_rejects_bad_arguments(lib, N, bc, prec):
+    st, h = cc.ccmsav_solver_create(N, 1.0, bc, prec)
+    assert st == cc.CCMSAV_EINVAL and not h.value
+
+
+def test_solver_calls_reject_null_handles(lib):
+    assert cc.ccmsav_solver_create(64, 0.0, 0, 0)[0] == cc.CCMSAV_EINVAL
+    assert cc.ccmsav_solver_solve(None, [1.0, 0.0, 0.0], 0, 0) == cc.CCMSAV_EINVAL
+    assert cc.ccmsav_solver_smooth(None, 0.1, 0.01, 1e-6, 10, 0) == cc.CCMSAV_EINVAL
+    assert cc.ccmsav_solver_sync(None) == cc.CCMSAV_EINVAL
+    assert cc.ccmsav_solver_launch_count(None) == 0
+    cc.ccmsav_solver_destroy(None)

@@ -605,3 +605,119 @@ def test_parameter_table_golden():
     w = I.workload("ellipse_shrink", N=16)
     sl, ic = gold["benchmark_profiles"]["shrinkage"]
     assert np.allclose(w.psi0, sl * w.phi0 + ic, atol=1e-15)
+
+
+# ------------------- other boundary rules and the smoother (Appendix C closing remarks, Appendix F)
+
+def dense_operator(N, h, bc, fn):
+    """Matrix of a linear grid operator, column by column from unit fields."""
+    A = np.zeros((N * N, N * N))
+    for q in range(N * N):
+        e = np.zeros(N * N)
+        e[q] = 1.0
+        A[:, q] = fn(e.reshape(N, N)).ravel()
+    return A
+
+
+@pytest.mark.parametrize("bc", O.BCS)
+def test_bc_transforms_against_libraries(bc):
+    """The written-out transforms are unitary and equal scipy's orthonormal
+    DCT-II / DST-II and numpy's FFT (scaled to be unitary)."""
+    N = 16
+    C = O.transform_matrix(N, bc)
+    assert np.abs(C @ C.conj().T - np.eye(N)).max() < 1e-13
+    u = np.random.default_rng(3).standard_normal((N, N))
+    got = C @ u @ C.T
+    ref = {"neumann": lambda: sfft.dctn(u, type=2, norm="ortho"),
+           "dirichlet": lambda: sfft.dstn(u, type=2, norm="ortho"),
+           "periodic": lambda: np.fft.fft2(u) / N}[bc]()
+    assert np.abs(got - ref).max() < 1e-13
+
+
+@pytest.mark.parametrize("bc", O.BCS)
+def test_bc_laplacian_ghost_rules_and_eigenvalues(bc):
+    """Lap_h with the boundary rule's ghosts, against explicit loops over
+    cells (mirror, odd, wrap), and the closed-form eigenvalues diagonalise it."""
+    N, h = 8, 0.41
+    u = np.random.default_rng(4).standard_normal((N, N))
+
+    def val(j, i):
+        if bc == "periodic":
+            return u[j % N, i % N]
+        sg = 1.0
+        if bc == "dirichlet" and (i < 0 or i >= N or j < 0 or j >= N):
+            sg = -1.0
+        return sg * u[min(max(j, 0), N - 1), min(max(i, 0), N - 1)]
+    ref = np.array([[(val(j, i + 1) + val(j, i - 1) + val(j + 1, i) + val(j - 1, i) - 4 * u[j, i]) / h ** 2
+                     for i in range(N)] for j in range(N)])
+    assert np.abs(O.lap_bc(u, h, bc) - ref).max() < 1e-12
+    C = O.transform_matrix(N, bc)
+    e = O.bc_eigenvalues(N, h, bc)
+    lhs = C @ O.lap_bc(u, h, bc) @ C.T
+    rhs = -(e[:, None] + e[None, :]) * (C @ u @ C.T)
+    assert np.abs(lhs - rhs).max() <= 1e-12 * np.abs(rhs).max()
+
+
+@pytest.mark.parametrize("bc", O.BCS)
+@pytest.mark.parametrize("N", [8, 16])
+def test_bc_spectral_solve_equals_dense_solve(bc, N):
+    """u = (c0 - c1 Lap_h + c2 Lap_h^2)^{-1} f by the transform equals the
+    dense solve with the operator assembled from unit fields."""
+    h = 0.23
+    c = (3.0, 0.7, 0.05) if bc != "dirichlet" else (0.0, 0.7, 0.05)
+    Lop = dense_operator(N, h, bc, lambda e: O.lap_bc(e, h, bc))
+    A = c[0] * np.eye(N * N) - c[1] * Lop + c[2] * Lop @ Lop
+    f = np.random.default_rng(N).standard_normal((N, N))
+    ref = np.linalg.solve(A, f.ravel()).reshape(N, N)
+    got = O.spectral_solve_bc(f, c, h, bc)
+    assert np.abs(got - ref).max() <= 1e-12 * np.abs(ref).max()
+
+
+def test_smoother_step_equals_dense_solve():
+    """One smoothing step of Appendix F (before the clamp) is the dense solve
+    of (I/dt + Mob eps L^2) phi1 = phi0/dt + Mob L (phi0^3 - phi0)/eps."""
+    N, h, eps, mob, dt = 8, 0.2, 0.3, 0.01, 1e-3
+    phi = np.random.default_rng(9).uniform(-0.9, 0.9, (N, N))
+    Lop = dense_operator(N, h, "neumann", lambda e: O.lap(e, h))
+    A = np.eye(N * N) / dt + mob * eps * Lop @ Lop
+    b = phi.ravel() / dt + mob * Lop @ ((phi ** 3 - phi) / eps).ravel()
+    ref = np.clip(np.linalg.solve(A, b).reshape(N, N), -1, 1)
+    assert np.abs(O.smooth_initial(phi, h, eps, mob, dt, 1) - ref).max() < 1e-12
+
+
+def test_smoother_conserves_mass_and_lowers_energy():
+    """Neumann Cahn-Hilliard conserves sum(phi) exactly (the zero mode of the
+    solve is phi^n/dt divided by 1/dt) and, at a small step, lowers the
+    Ginzburg-Landau energy int (g(phi)/eps + eps/2 |grad phi|^2); the clamp
+    changes nothing for a field already inside [-1, 1]."""
+    N, L, eps = 64, 2.0, 0.05
+    h = L / N
+    x = (np.arange(N) + 0.5) * h
+    X, Y = np.meshgrid(x, x)
+    sharp = np.where((np.abs(X - 1.0) < 0.45) & (np.abs(Y - 1.0) < 0.3), 1.0, -1.0)
+    sharp = 0.98 * sharp        # inside [-1, 1] throughout the run
+    m = model(N, eps=eps, L=L)
+
+    def energy(u):
+        return O.ip(O.g_dw(u), np.ones_like(u), h) / eps + 0.5 * eps * O.grad_norm2(u, h)
+    E0, prev = energy(sharp), sharp
+    for k in range(1, 6):
+        cur = O.smooth_initial(prev, h, eps, 0.01, 1e-6, 1)
+        assert abs(np.sum(cur) - np.sum(sharp)) <= 1e-12 * np.abs(sharp).sum()
+        assert energy(cur) < energy(prev)
+        prev = cur
+    assert energy(prev) < E0
+    assert m.N == N
+
+
+def test_smoother_keeps_a_relaxed_flat_profile():
+    """A flat interface phi = tanh(x/(sqrt2 eps)) is a steady state of the
+    continuous equation: ten smoothing steps move it by less than 1e-3 of
+    its range on a grid resolving eps by eight cells."""
+    N, L, eps = 256, 4.0, 0.125
+    h = L / N
+    x = (np.arange(N) + 0.5) * h
+    prof = np.tanh((x - L / 2) / (math.sqrt(2) * eps))
+    phi = np.tile(prof, (N, 1))
+    out = O.smooth_initial(phi, h, eps, 0.01, 1e-6, 10)
+    assert np.abs(out - phi).max() < 1e-3
