@@ -61,6 +61,12 @@ extern "C" {
                                    energy each BDF2 step (one extra reduction
                                    kernel per step); needed for E_mod in
                                    ccmsav_energy() */
+#define CCMSAV_BDF1_ALWAYS  2   /* every step is the first-order CC-MSAV-BDF1
+                                   scheme (Appendix B, remark on the BDF1
+                                   scheme: level n in place of the
+                                   extrapolations, 1/dt in place of 3/(2 dt),
+                                   phi^n/dt in place of (4 phi^n - phi^{n-1})/(2 dt),
+                                   SAV updates X^{n+1} = X^n + (F, phi^{n+1} - phi^n)) */
 
 /* Model and scheme parameters.  Symbols and default values are those of the
  * paper's parameter table (Appendix G): gamma_surf, gamma_bend, gamma_area
@@ -87,7 +93,7 @@ typedef struct ccmsav ccmsav_t;   /* opaque handle */
  *   params    parameters shared by all simulations; per_sim (may be NULL)
  *             gives one parameter set per simulation instead.
  *   precision CCMSAV_FP64 or CCMSAV_FP32_BULK.
- *   flags     0 or CCMSAV_TRACK_ENERGY.
+ *   flags     0 or a combination of CCMSAV_TRACK_ENERGY and CCMSAV_BDF1_ALWAYS.
  *   stream    a cudaStream_t (NULL: the legacy default stream).
  * Validates every parameter (eps, dt, L, lam, M_phi > 0; theta, beta,
  * gamma_* >= 0; 0 < M0 < 1) and returns CCMSAV_EINVAL otherwise.
@@ -129,7 +135,10 @@ int ccmsav_get_state(ccmsav_t* h, int sim, double* phi, double* psi);
 /* Diagnostics of simulation `sim` at the current level (synchronises):
  *   out[0] E_mod   modified discrete energy E^{n+1,n}_mod (eq.
  *                  modified_discrete_energy, discrete norms of Appendix D);
- *                  includes the lambda-sum only with CCMSAV_TRACK_ENERGY
+ *                  includes the lambda-sum only with CCMSAV_TRACK_ENERGY.
+ *                  With CCMSAV_BDF1_ALWAYS: the one-level energy of the BDF1
+ *                  scheme, c_b/2 ||Lap phi||^2 + (c_s - theta~)/2 ||grad phi||^2
+ *                  + c_beta/2 ||phi||^2 + the SAV terms at level n
  *   out[1] F_surf  gamma_surf * int f_surf
  *   out[2] F_bend  gamma_bend * int f_bend
  *   out[3] F_area  gamma_area/2 (int f_surf - A)^2

@@ -430,9 +430,11 @@ class StepInfo:
     bdf1: bool
 
 
-def step(s: State, m: Model, return_info: bool = False):
-    """One CC-MSAV step n -> n+1: BDF1 when s.n == 0, BDF2 afterwards."""
-    bdf1 = (s.n == 0)
+def step(s: State, m: Model, return_info: bool = False, bdf1: Optional[bool] = None):
+    """One CC-MSAV step n -> n+1: BDF1 when s.n == 0, BDF2 afterwards; with
+    bdf1=True every step is the CC-MSAV-BDF1 scheme (Appendix B, remark on
+    the BDF1 scheme)."""
+    bdf1 = (s.n == 0) if bdf1 is None else bool(bdf1)
     h = m.h
     # Stage 1: extrapolations (BDF1 uses level n).
     if bdf1:
@@ -518,9 +520,9 @@ def step(s: State, m: Model, return_info: bool = False):
     return out
 
 
-def run(s: State, m: Model, nsteps: int) -> State:
+def run(s: State, m: Model, nsteps: int, bdf1: Optional[bool] = None) -> State:
     for _ in range(nsteps):
-        s = step(s, m)
+        s = step(s, m, bdf1=bdf1)
     return s
 
 

@@ -27,6 +27,7 @@ CCMSAV_ETIMEOUT = -6
 CCMSAV_FP64 = 0
 CCMSAV_FP32_BULK = 1
 CCMSAV_TRACK_ENERGY = 1
+CCMSAV_BDF1_ALWAYS = 2
 CCMSAV_BC_NEUMANN = 0
 CCMSAV_BC_DIRICHLET = 1
 CCMSAV_BC_PERIODIC = 2
@@ -270,10 +271,10 @@ class Simulation:
     """Owns one handle for one or more simulations; raises on error codes."""
 
     def __init__(self, params, N, precision: str = "fp64", track_energy: bool = False,
-                 stream: Optional[int] = None, per_sim=None):
+                 stream: Optional[int] = None, per_sim=None, bdf1_always: bool = False):
         Ns = [int(N)] if np.isscalar(N) else [int(x) for x in N]
         prec = CCMSAV_FP64 if precision == "fp64" else CCMSAV_FP32_BULK
-        flags = CCMSAV_TRACK_ENERGY if track_energy else 0
+        flags = (CCMSAV_TRACK_ENERGY if track_energy else 0) | (CCMSAV_BDF1_ALWAYS if bdf1_always else 0)
         st, h = ccmsav_create(params, Ns, prec, flags, stream, per_sim)
         if st != CCMSAV_OK:
             raise CCMSAVError(st, "ccmsav_create")

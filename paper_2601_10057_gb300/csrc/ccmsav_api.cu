@@ -119,7 +119,7 @@ int ccmsav_create(ccmsav_t** out, const ccmsav_params* params, int n_sims, const
     *out = nullptr;
     if (n_sims < 1 || !N || (!params && !per_sim)) return CCMSAV_EINVAL;
     if (precision != CCMSAV_FP64 && precision != CCMSAV_FP32_BULK) return CCMSAV_EINVAL;
-    if (flags & ~CCMSAV_TRACK_ENERGY) return CCMSAV_EINVAL;
+    if (flags & ~(CCMSAV_TRACK_ENERGY | CCMSAV_BDF1_ALWAYS)) return CCMSAV_EINVAL;
     for (int s = 0; s < n_sims; ++s) {
         if (!valid_N(N[s])) return CCMSAV_EINVAL;
         if (!valid_params(per_sim ? per_sim[s] : *params)) return CCMSAV_EINVAL;

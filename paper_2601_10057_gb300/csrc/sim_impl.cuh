@@ -604,7 +604,7 @@ public:
     }
 
     int queue_one_step() {
-        const bool bdf1 = (steps_taken == 0);
+        const bool bdf1 = (steps_taken == 0) || (flags & CCMSAV_BDF1_ALWAYS);
         const double dt = p.dt;
         StencilCoef<T> c;
         c.bdf1 = bdf1 ? 1 : 0;
@@ -753,6 +753,13 @@ public:
         const double cs = p.gamma_surf * 3.0 * M_SQRT2 * p.eps / 4.0 + p.theta;
         const double cbeta = p.gamma_surf * 3.0 * M_SQRT2 * p.beta / (4.0 * p.eps);
         const double tt = theta_tilde();
+        if (flags & CCMSAV_BDF1_ALWAYS) {
+            // one-level energy of the first-order scheme (the BDF1 energy balance)
+            double E1 = 0.5 * cb * h2 * s[5] + 0.5 * (cs - tt) * h2 * s[4] + 0.5 * cbeta * h2 * s[9];
+            E1 += 0.5 * p.gamma_surf * 3.0 * M_SQRT2 / 2.0 * q.V * q.V + 0.5 * p.gamma_area * q.U * q.U;
+            E1 += 0.5 * p.gamma_bend * 3.0 * M_SQRT2 / (8.0 * p.eps) * q.W * q.W + 0.5 * q.Z * q.Z;
+            out[0] = E1;
+        }
         double E = 0.5 * cb * h2 * (s[5] + s[6]);
         E += 0.5 * cs * h2 * (s[4] + s[7]);
         E -= 0.5 * tt * h2 * (s[4] + s[7] - 2.0 * s[8]);
@@ -767,7 +774,8 @@ public:
         const double Fb = p.gamma_bend * 3.0 * M_SQRT2 / (16.0 * p.eps) * h2 * s[11];
         const double Fa = 0.5 * p.gamma_area * (arc - q.A) * (arc - q.A);
         const double Fo = h2 * s[12];
-        out[0] = E; out[1] = Fs; out[2] = Fb; out[3] = Fa; out[4] = Fo; out[5] = arc;
+        if (!(flags & CCMSAV_BDF1_ALWAYS)) out[0] = E;
+        out[1] = Fs; out[2] = Fb; out[3] = Fa; out[4] = Fo; out[5] = arc;
         out[6] = q.lamsum; out[7] = Fs + Fb + Fa + Fo;
         return CCMSAV_OK;
     }

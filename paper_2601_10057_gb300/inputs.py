@@ -394,3 +394,18 @@ def robustness_params(grows: bool, N: int = 2048, L: float = 1.0, eps: float = 0
     if grows:
         return growth_params(gamma_bend=0.05, theta=10.0, eps=eps, dt=dt, L=L)
     return shrinkage_params(gamma_bend=0.1, theta=30.0, eps=eps, dt=dt, L=L)
+
+
+def convergence_ellipse(N: int, L: float = 1.0, eps: float = 0.03125, dt: float = 1e-6,
+                        a: float = 0.3, b: float = 0.2) -> Workload:
+    """Smooth ellipse of the convergence studies (semi-axes a, b, centred in
+    the unit square; the paper's ellipse is not given): phi =
+    tanh((R(theta) - r)/(sqrt2 eps)), the shrinkage profile of psi, the
+    shrinkage column with the studies' moderate stiffness (gamma_in,
+    gamma_out, gamma_area) = (100, 100, 100) and eps fixed across grids."""
+    def radius(th):
+        return a * b / np.sqrt((b * np.cos(th)) ** 2 + (a * np.sin(th)) ** 2)
+    p = shrinkage_params(eps=eps, dt=dt, L=L, gamma_in=100.0, gamma_out=100.0, gamma_area=100.0)
+    phi = vesicle_phi(N, L, eps, (L / 2, L / 2), radius)
+    psi = concentration([phi], [0.8])
+    return Workload(f"convergence_ellipse_N{N}", N, p, phi, psi, 0, "fp64")

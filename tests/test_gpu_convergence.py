@@ -1,0 +1,33 @@
+"""Second-order convergence of the GPU step (Sec. 4.1 of the paper) through
+the C ABI: the refinement path dt = 0.002 h and the temporal Cauchy study on
+the smooth convergence ellipse, errors between levels with the fine solution
+restricted to the coarse centres by the 4-point cubic stencil."""
+import pytest
+
+from paper_2601_10057_gb300 import build as B
+from paper_2601_10057_gb300 import ccmsav as cc
+from paper_2601_10057_gb300 import convergence as CV
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    B.build()
+    return cc.load()
+
+
+def test_refinement_path_second_order_on_gpu():
+    """N = 128 .. 1024 with dt = 0.002 h, T = 5e-3 (the paper's path; its
+    combined rates are 1.83 - 2.53): every combined rate within 1.7 - 2.7."""
+    r = CV.study("refinement", "fp64", Ns=(128, 256, 512, 1024))
+    print(r)
+    assert all(1.7 < x < 2.7 for x in r["rate_combined"]), r
+
+
+def test_temporal_cauchy_second_order_on_gpu():
+    """Fixed N = 256, dt = 1e-5 / 2^k, T = 5e-3: Cauchy differences fall by
+    about 4x per halving (the paper's combined rates are 2.08 - 2.73)."""
+    r = CV.study("temporal", "fp64", N_time=256, dts=(1e-5, 5e-6, 2.5e-6, 1.25e-6))
+    print(r)
+    assert all(1.7 < x < 3.0 for x in r["rate_combined"]), r

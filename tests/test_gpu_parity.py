@@ -475,3 +475,36 @@ def test_async_aux_matches_synchronous_read():
     assert [int(b[10]) for b in bufs] == [1, 2, 3, 4, 5]
     assert np.array_equal(bufs[-1], sim.aux())
     sim.close()
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32", 2e-5)])
+def test_bdf1_mode_against_oracle(precision, tol):
+    """CCMSAV_BDF1_ALWAYS: every step is the CC-MSAV-BDF1 scheme (graph-
+    launched after the first); 10 steps at N = 128 against the oracle run
+    with bdf1=True, and the one-level BDF1 energy against its definition."""
+    w = I.workload("ellipse_shrink", N=128)
+    sim = cc.Simulation(w.params, w.N, precision=precision, bdf1_always=True)
+    sim.set_state(w.phi0, w.psi0)
+    sim.step(1)
+    sim.step(9)
+    phi, psi = sim.state()
+    aux = sim.aux()
+    E = sim.energy()
+    sim.close()
+    m = O.Model.from_params(w.N, w.params)
+    s = O.run(O.initial_state(w.phi0, w.psi0, m), m, 10, bdf1=True)
+    e = (rel(phi, s.phi), rel(psi, s.psi), sav_err(aux[:8], s))
+    print("bdf1 mode", precision, e)
+    assert max(e) <= tol, e
+    if precision == "fp64":
+        SQ2 = math.sqrt(2.0)
+        h = m.h
+        cb = m.gamma_bend * 3 * SQ2 * m.eps / 8
+        cs = m.gamma_surf * 3 * SQ2 * m.eps / 4 + m.theta
+        cbeta = m.gamma_surf * 3 * SQ2 * m.beta / (4 * m.eps)
+        La = O.lap(s.phi, h)
+        E1 = (0.5 * cb * O.ip(La, La, h) + 0.5 * (cs - m.theta_tilde) * O.grad_norm2(s.phi, h)
+              + 0.5 * cbeta * O.ip(s.phi, s.phi, h) + 0.5 * m.gamma_surf * 3 * SQ2 / 2 * s.V ** 2
+              + 0.5 * m.gamma_area * s.U ** 2 + 0.5 * m.gamma_bend * 3 * SQ2 / (8 * m.eps) * s.W ** 2
+              + 0.5 * s.Z ** 2)
+        assert E[0] == pytest.approx(E1, rel=1e-10)

@@ -721,3 +721,40 @@ def test_smoother_keeps_a_relaxed_flat_profile():
     phi = np.tile(prof, (N, 1))
     out = O.smooth_initial(phi, h, eps, 0.01, 1e-6, 10)
     assert np.abs(out - phi).max() < 1e-3
+
+
+# ------------------------------------------------ BDF1 product mode (Appendix B, remark on the BDF1 scheme)
+
+@pytest.mark.parametrize("wl", ["one_vesicle", "ellipse_shrink"])
+def test_bdf1_mode_energy_balance_every_step(wl):
+    """With every step BDF1, each step satisfies the first-order energy
+    balance (the identity of the BDF1 start step, applied at every level)."""
+    w = I.workload(wl, N=32, dt=1e-5)
+    m = O.Model.from_params(w.N, w.params)
+    s = O.initial_state(w.phi0, w.psi0, m)
+    for _ in range(5):
+        s1 = O.step(s, m, bdf1=True)
+        assert abs(bdf1_energy_residual(m, s, s1)) < 1e-12
+        s = s1
+    assert s.n == 5 and s.lam_sum == 0.0
+
+
+def test_bdf1_mode_is_first_order_in_time():
+    """Cauchy differences of the BDF1 mode fall by about 2x per dt halving
+    (against about 4x for the BDF2 scheme); moderate osmotic, area and
+    diffusion coefficients (100, 50, 100), with which the rate is already
+    asymptotic at these steps (with the table's 1e5 values it reaches 0.9
+    only below dt = 1e-6)."""
+    N, T = 16, 2e-4
+    sols = []
+    for dt in (1e-5, 5e-6, 2.5e-6, 1.25e-6):
+        w = I.workload("ellipse_shrink", N=N, dt=dt)
+        m = O.Model.from_params(w.N, w.params.replace(gamma_in=100.0, gamma_out=100.0, lam=100.0,
+                                                      gamma_area=50.0))
+        s = O.run(O.initial_state(w.phi0, w.psi0, m), m, int(round(T / dt)), bdf1=True)
+        sols.append((s.phi, s.psi))
+    h = m.h
+    e = [math.sqrt(O.ip(a[0] - b[0], a[0] - b[0], h) + O.ip(a[1] - b[1], a[1] - b[1], h))
+         for a, b in zip(sols[:-1], sols[1:])]
+    rates = [math.log2(e[k] / e[k + 1]) for k in range(len(e) - 1)]
+    assert all(0.8 < r < 1.3 for r in rates), rates
