@@ -430,10 +430,18 @@ class StepInfo:
     bdf1: bool
 
 
-def step(s: State, m: Model, return_info: bool = False, bdf1: Optional[bool] = None):
+def step(s: State, m: Model, return_info: bool = False, bdf1: Optional[bool] = None,
+         classical: bool = False):
     """One CC-MSAV step n -> n+1: BDF1 when s.n == 0, BDF2 afterwards; with
     bdf1=True every step is the CC-MSAV-BDF1 scheme (Appendix B, remark on
-    the BDF1 scheme)."""
+    the BDF1 scheme).  classical=True takes the classical MSAV scheme
+    instead (Appendix B, remarks on the Classical-MSAV-BDF2 / BDF1 schemes):
+    the Cahn-Hilliard stabilisation sits in the chemical potential, so
+    g = (4 psi^n - psi^{n-1})/(2 dt) + div(M_psi(phi*) grad nu~) with
+    nu~ = -lam psi* + a_Z P, and both Cahn-Hilliard solves use the
+    variable-coefficient operator 3/(2 dt) - lam div(M_psi(phi*) grad),
+    solved here by a sparse direct factorisation (the paper's
+    Classical+Direct baseline)."""
     bdf1 = (s.n == 0) if bdf1 is None else bool(bdf1)
     h = m.h
     # Stage 1: extrapolations (BDF1 uses level n).
@@ -475,7 +483,10 @@ def step(s: State, m: Model, return_info: bool = False, bdf1: Optional[bool] = N
                        + m.gamma_bend * 3 * SQ2 / (8 * m.eps) * aW * Q
                        + aZ * K)
     nu_tilde = aZ * P
-    g = g - m.lam * lap(psis, h) + div_mobility_grad(phis, nu_tilde, m)
+    if classical:
+        g = g + div_mobility_grad(phis, nu_tilde - m.lam * psis, m)
+    else:
+        g = g - m.lam * lap(psis, h) + div_mobility_grad(phis, nu_tilde, m)
     # Step 3: the seven constant-coefficient solves.
     sig = chi_spectrum(m, bdf1)
     tau = zeta_spectrum(m, bdf1)
@@ -484,8 +495,13 @@ def step(s: State, m: Model, return_info: bool = False, bdf1: Optional[bool] = N
     H_hat = solve_spectral(H, sig)
     Q_hat = solve_spectral(Q, sig)
     K_hat = solve_spectral(K, sig)
-    g_hat = solve_spectral(g, tau)
-    Lam_P = solve_spectral(div_mobility_grad(phis, P, m), tau)
+    if classical:
+        zeta_c = classical_zeta_matrix(phis, m, bdf1)
+        g_hat = sparse_solve(zeta_c, g)
+        Lam_P = sparse_solve(zeta_c, div_mobility_grad(phis, P, m))
+    else:
+        g_hat = solve_spectral(g, tau)
+        Lam_P = solve_spectral(div_mobility_grad(phis, P, m), tau)
     # Step 4: the 5x5 system for B, C, D, E, G.
     F = [S, H, Q, K]
     hats = [S_hat, H_hat, Q_hat, K_hat]
@@ -520,10 +536,45 @@ def step(s: State, m: Model, return_info: bool = False, bdf1: Optional[bool] = N
     return out
 
 
-def run(s: State, m: Model, nsteps: int, bdf1: Optional[bool] = None) -> State:
+def run(s: State, m: Model, nsteps: int, bdf1: Optional[bool] = None,
+        classical: bool = False) -> State:
     for _ in range(nsteps):
-        s = step(s, m, bdf1=bdf1)
+        s = step(s, m, bdf1=bdf1, classical=classical)
     return s
+
+
+def mobility_operator_matrix(phis: np.ndarray, m: Model):
+    """Sparse N^2 x N^2 matrix of nu -> div(M_psi(A phis) grad nu) (eq.
+    mobility_flux): each interior face couples its two cells with weight
+    M_face / h^2; boundary faces carry no flux (row-major cell index j N + i)."""
+    import scipy.sparse as sp
+    N, h = phis.shape[0], m.h
+    Mx = mobility(Ax(phis), m)[:, 1:-1] / (h * h)     # interior east-west faces, (N, N-1)
+    My = mobility(Ay(phis), m)[1:-1, :] / (h * h)     # interior north-south faces, (N-1, N)
+    idx = np.arange(N * N).reshape(N, N)
+    rows, cols, vals = [], [], []
+    for a, b, w in ((idx[:, :-1], idx[:, 1:], Mx), (idx[:-1, :], idx[1:, :], My)):
+        a, b, w = a.ravel(), b.ravel(), w.ravel()
+        rows += [a, b, a, b]
+        cols += [b, a, a, b]
+        vals += [w, w, -w, -w]
+    return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                         shape=(N * N, N * N))
+
+
+def classical_zeta_matrix(phis: np.ndarray, m: Model, bdf1: bool = False):
+    """The classical scheme's Cahn-Hilliard operator 3/(2 dt) - lam div(M grad)
+    (1/dt for BDF1) as a sparse matrix."""
+    import scipy.sparse as sp
+    a = 1.0 / m.dt if bdf1 else 1.5 / m.dt
+    N = phis.shape[0]
+    return (a * sp.identity(N * N, format="csr") - m.lam * mobility_operator_matrix(phis, m)).tocsc()
+
+
+def sparse_solve(A, rhs: np.ndarray) -> np.ndarray:
+    """Direct sparse solve (LU of scipy's SuperLU)."""
+    import scipy.sparse.linalg as spla
+    return spla.spsolve(A, rhs.ravel()).reshape(rhs.shape)
 
 
 # --------------------------------------------------------------------------

@@ -758,3 +758,46 @@ def test_bdf1_mode_is_first_order_in_time():
          for a, b in zip(sols[:-1], sols[1:])]
     rates = [math.log2(e[k] / e[k + 1]) for k in range(len(e) - 1)]
     assert all(0.8 < r < 1.3 for r in rates), rates
+
+
+# ------------------------------------------------ classical MSAV baseline (Appendix B remarks; Sec. 3.5.2)
+
+def test_classical_mobility_matrix_matches_flux():
+    """The assembled sparse div(M grad) equals the face-by-face flux form
+    (itself pinned by explicit loops above) and has zero column sums."""
+    w = I.workload("one_vesicle", N=32, dt=1e-5)
+    m = O.Model.from_params(w.N, w.params)
+    A = O.mobility_operator_matrix(w.phi0, m)
+    x = np.random.default_rng(0).standard_normal((32, 32))
+    assert np.abs(A @ x.ravel() - O.div_mobility_grad(w.phi0, x, m).ravel()).max() < 1e-12 * np.abs(A @ x.ravel()).max()
+    assert np.abs(np.asarray(A.sum(axis=0))).max() < 1e-9
+
+
+def test_classical_equals_cc_for_constant_mobility():
+    """With M0 = 0 the mobility is 1, div(M grad) = Lap_h, and the classical
+    scheme's lam div(M grad)(psi^{n+1} - psi*) is the CC scheme's
+    lam (Lap psi^{n+1} - Lap psi*): the two schemes coincide."""
+    w = I.workload("one_vesicle", N=32, dt=1e-5)
+    m = O.Model.from_params(w.N, w.params.replace(M0=0.0))
+    s = O.initial_state(w.phi0, w.psi0, m)
+    a, b = O.run(s, m, 4), O.run(s, m, 4, classical=True)
+    assert np.abs(a.phi - b.phi).max() < 1e-13 and np.abs(a.psi - b.psi).max() < 1e-13
+    assert abs(a.Z - b.Z) < 1e-13 * abs(a.Z)
+
+
+def test_classical_conserves_mass_and_approaches_cc():
+    """The classical scheme conserves h^2 sum psi (its operator has zero
+    column sums), and its difference to the CC scheme at a fixed time falls
+    about 4x per dt halving (both second-order consistent)."""
+    w = I.workload("ellipse_shrink", N=16, dt=1e-5)
+    T, diffs = 1e-4, []
+    for dt in (1e-5, 5e-6, 2.5e-6):
+        p = w.params.replace(dt=dt, gamma_in=100.0, gamma_out=100.0, lam=100.0, gamma_area=50.0)
+        m = O.Model.from_params(w.N, p)
+        s = O.initial_state(w.phi0, w.psi0, m)
+        n = int(round(T / dt))
+        a, b = O.run(s, m, n), O.run(s, m, n, classical=True)
+        assert abs(O.mass(b.psi, m) - O.mass(s.psi, m)) <= 1e-13 * abs(O.mass(s.psi, m))
+        diffs.append(math.sqrt(O.ip(a.phi - b.phi, a.phi - b.phi, m.h) + O.ip(a.psi - b.psi, a.psi - b.psi, m.h)))
+    rates = [math.log2(diffs[k] / diffs[k + 1]) for k in range(2)]
+    assert all(1.6 < r < 2.6 for r in rates), (rates, diffs)
