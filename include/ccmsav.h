@@ -61,6 +61,19 @@ extern "C" {
                                    energy each BDF2 step (one extra reduction
                                    kernel per step); needed for E_mod in
                                    ccmsav_energy() */
+#define CCMSAV_CLASSICAL    4   /* the classical MSAV scheme instead of CC-MSAV
+                                   (the paper's baseline, Sec. 3.5.2; Appendix B
+                                   remarks on the Classical-MSAV schemes): the
+                                   Cahn-Hilliard stabilisation inside the
+                                   chemical potential, so both Cahn-Hilliard
+                                   solves use 3/(2 dt) - lam div(M_psi(phi*) grad),
+                                   solved by DCT-preconditioned conjugate
+                                   gradients (the constant-coefficient
+                                   operator with the mean face mobility as
+                                   preconditioner); the Allen-Cahn part is the
+                                   CC-MSAV one.  Steps are launched directly
+                                   (no CUDA graphs): the host reads the
+                                   convergence flags every four iterations */
 #define CCMSAV_BDF1_ALWAYS  2   /* every step is the first-order CC-MSAV-BDF1
                                    scheme (Appendix B, remark on the BDF1
                                    scheme: level n in place of the
@@ -93,7 +106,8 @@ typedef struct ccmsav ccmsav_t;   /* opaque handle */
  *   params    parameters shared by all simulations; per_sim (may be NULL)
  *             gives one parameter set per simulation instead.
  *   precision CCMSAV_FP64 or CCMSAV_FP32_BULK.
- *   flags     0 or a combination of CCMSAV_TRACK_ENERGY and CCMSAV_BDF1_ALWAYS.
+ *   flags     0 or a combination of CCMSAV_TRACK_ENERGY, CCMSAV_BDF1_ALWAYS
+ *             and CCMSAV_CLASSICAL.
  *   stream    a cudaStream_t (NULL: the legacy default stream).
  * Validates every parameter (eps, dt, L, lam, M_phi > 0; theta, beta,
  * gamma_* >= 0; 0 < M0 < 1) and returns CCMSAV_EINVAL otherwise.
@@ -195,10 +209,24 @@ long long ccmsav_launch_count(ccmsav_t* h);
  *   [2] forward column DCT + Gram sums   [3] 5x5 solve + SAV update
  *   [4] recovery + inverse column DCT    [5] inverse row DCT
  *   [6] lambda-sum reduction (CCMSAV_TRACK_ENERGY only)
- *   [7] unused (0)
+ *   [7] the conjugate-gradient Cahn-Hilliard solves (CCMSAV_CLASSICAL only)
  * and in *nsteps the number of steps traced; it then resets the counters. */
 int ccmsav_profile(ccmsav_t* h, int enable);
 int ccmsav_profile_read(ccmsav_t* h, int sim, double ms[8], long long* nsteps);
+
+/* Conjugate-gradient settings of a CCMSAV_CLASSICAL handle (all its
+ * simulations): stop when ||r||_2 <= rtol ||b||_2 (rtol > 0; default 1e-10
+ * for FP64, 1e-6 for FP32) or after max_iter iterations (>= 1; default 200).
+ * CCMSAV_EINVAL on a bad value or a handle without CCMSAV_CLASSICAL. */
+int ccmsav_set_pcg(ccmsav_t* h, double rtol, int max_iter);
+
+/* Conjugate-gradient statistics of simulation `sim` (synchronises):
+ *   out[0] iterations of the last step (the larger of its two solves)
+ *   out[1] iterations of all steps since creation
+ *   out[2], out[3] final relative residuals ||r|| / ||b|| of the last step's
+ *          two solves (zeta_c^{-1} g0c and zeta_c^{-1} div(M grad P))
+ * CCMSAV_EINVAL for a handle without CCMSAV_CLASSICAL. */
+int ccmsav_pcg_stats(ccmsav_t* h, int sim, double out[4]);
 
 /* Largest grid side accepted by ccmsav_mass_noalloc(): the largest grid a
  * handle accepts.  The scratch does not grow with N (see below). */

@@ -28,6 +28,7 @@ CCMSAV_FP64 = 0
 CCMSAV_FP32_BULK = 1
 CCMSAV_TRACK_ENERGY = 1
 CCMSAV_BDF1_ALWAYS = 2
+CCMSAV_CLASSICAL = 4
 CCMSAV_BC_NEUMANN = 0
 CCMSAV_BC_DIRICHLET = 1
 CCMSAV_BC_PERIODIC = 2
@@ -89,6 +90,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "ccmsav_profile_read": (i, [vp, i, _DP, C.POINTER(C.c_longlong)]),
         "ccmsav_destroy": (None, [vp]),
         "ccmsav_mass_noalloc": (i, [vp, i, i, d, _DP, vp]),
+        "ccmsav_set_pcg": (i, [vp, d, i]),
+        "ccmsav_pcg_stats": (i, [vp, i, _DP]),
         "ccmsav_solver_create": (i, [C.POINTER(vp), i, d, i, i, vp]),
         "ccmsav_solver_solve": (i, [vp, _DP, vp, vp]),
         "ccmsav_solver_smooth": (i, [vp, d, d, d, i, vp]),
@@ -235,6 +238,18 @@ def ccmsav_mass_noalloc(psi_ptr: int, N: int, precision: int, L: float, stream: 
     return st, float(out[0])
 
 
+def ccmsav_set_pcg(h, rtol: float, max_iter: int) -> int:
+    return load().ccmsav_set_pcg(h, float(rtol), int(max_iter))
+
+
+def ccmsav_pcg_stats(h, sim: int = 0):
+    """Returns (status, [iterations of the last step, total iterations,
+    relative residual of solve 1, of solve 2])."""
+    out = np.zeros(4, np.float64)
+    st = load().ccmsav_pcg_stats(h, sim, _ptr(out))
+    return st, out
+
+
 def ccmsav_solver_create(N: int, L: float, bc: int, precision: int, stream: Optional[int] = None):
     """Returns (status, solver handle)."""
     h = C.c_void_p()
@@ -271,10 +286,12 @@ class Simulation:
     """Owns one handle for one or more simulations; raises on error codes."""
 
     def __init__(self, params, N, precision: str = "fp64", track_energy: bool = False,
-                 stream: Optional[int] = None, per_sim=None, bdf1_always: bool = False):
+                 stream: Optional[int] = None, per_sim=None, bdf1_always: bool = False,
+                 classical: bool = False):
         Ns = [int(N)] if np.isscalar(N) else [int(x) for x in N]
         prec = CCMSAV_FP64 if precision == "fp64" else CCMSAV_FP32_BULK
-        flags = (CCMSAV_TRACK_ENERGY if track_energy else 0) | (CCMSAV_BDF1_ALWAYS if bdf1_always else 0)
+        flags = ((CCMSAV_TRACK_ENERGY if track_energy else 0) | (CCMSAV_BDF1_ALWAYS if bdf1_always else 0)
+                 | (CCMSAV_CLASSICAL if classical else 0))
         st, h = ccmsav_create(params, Ns, prec, flags, stream, per_sim)
         if st != CCMSAV_OK:
             raise CCMSAVError(st, "ccmsav_create")
@@ -326,6 +343,14 @@ class Simulation:
 
     def launches(self) -> int:
         return ccmsav_launch_count(self.h)
+
+    def set_pcg(self, rtol: float, max_iter: int = 200):
+        self._check(ccmsav_set_pcg(self.h, rtol, max_iter), "ccmsav_set_pcg")
+
+    def pcg_stats(self, sim: int = 0):
+        st, out = ccmsav_pcg_stats(self.h, sim)
+        self._check(st, "ccmsav_pcg_stats")
+        return out
 
     def close(self):
         if self.h:

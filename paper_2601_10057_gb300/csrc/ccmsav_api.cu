@@ -119,7 +119,7 @@ int ccmsav_create(ccmsav_t** out, const ccmsav_params* params, int n_sims, const
     *out = nullptr;
     if (n_sims < 1 || !N || (!params && !per_sim)) return CCMSAV_EINVAL;
     if (precision != CCMSAV_FP64 && precision != CCMSAV_FP32_BULK) return CCMSAV_EINVAL;
-    if (flags & ~(CCMSAV_TRACK_ENERGY | CCMSAV_BDF1_ALWAYS)) return CCMSAV_EINVAL;
+    if (flags & ~(CCMSAV_TRACK_ENERGY | CCMSAV_BDF1_ALWAYS | CCMSAV_CLASSICAL)) return CCMSAV_EINVAL;
     for (int s = 0; s < n_sims; ++s) {
         if (!valid_N(N[s])) return CCMSAV_EINVAL;
         if (!valid_params(per_sim ? per_sim[s] : *params)) return CCMSAV_EINVAL;
@@ -237,6 +237,21 @@ int ccmsav_set_aux(ccmsav_t* h, int sim, const double aux[12]) {
     ccm::SimBase* s = get(h, sim);
     if (!s || !aux) return CCMSAV_EINVAL;
     return s->set_aux(aux);
+}
+
+int ccmsav_set_pcg(ccmsav_t* h, double rtol, int max_iter) {
+    if (!h || !(h->flags & CCMSAV_CLASSICAL)) return CCMSAV_EINVAL;
+    for (ccm::SimBase* s : h->sims) {
+        const int r = s->set_pcg(rtol, max_iter);
+        if (r) return r;
+    }
+    return CCMSAV_OK;
+}
+
+int ccmsav_pcg_stats(ccmsav_t* h, int sim, double out[4]) {
+    ccm::SimBase* s = get(h, sim);
+    if (!s || !out) return CCMSAV_EINVAL;
+    return s->pcg_stats(out);
 }
 
 int ccmsav_grid_size(ccmsav_t* h, int sim) {

@@ -33,6 +33,9 @@ public:
     virtual int queue_steps_captured(int n3) = 0;  // three steps as direct launches (for a
                                                    // stream capture); host counters unchanged
     virtual void count_steps(int n3) = 0;          // host counters after three batched steps
+    // classical MSAV (CCMSAV_CLASSICAL): conjugate-gradient settings and statistics
+    virtual int set_pcg(double rtol, int max_iter) = 0;
+    virtual int pcg_stats(double out[4]) = 0;
     int N = 0;
 };
 

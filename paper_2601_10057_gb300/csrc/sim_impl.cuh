@@ -22,6 +22,8 @@
 #include "sim.h"
 #include "diag_kernels.cuh"
 #include "warp_kernels.cuh"
+#include "spectral_kernels.cuh"
+#include "classical_kernels.cuh"
 #include <type_traits>
 
 namespace ccm {
@@ -98,6 +100,18 @@ public:
     size_t ev_used = 0;
     double prof_ms[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     long long prof_steps = 0;
+    // classical MSAV (CCMSAV_CLASSICAL): conjugate-gradient Cahn-Hilliard solves
+    bool classical = false;
+    T* cl = nullptr;                 // Mx My b1 (1 field each), x r p zq scratch (2 fields each)
+    PcgScalars* pcg = nullptr;
+    PcgScalars* pcg_host = nullptr;  // pinned
+    double* cl_red = nullptr;        // per-block partial sums
+    int cl_nb = 0;
+    ss::Geo cl_geo;
+    double pcg_rtol = 1e-10;
+    int pcg_max_it = 200;
+    double pcg_last[3] = {0, 0, 0};  // iterations, residuals of the last step
+    long long pcg_total = 0;
 
     ~SimImpl() override {
         if (st) cudaStreamSynchronize(st); else cudaDeviceSynchronize();
@@ -125,7 +139,7 @@ public:
     void count_steps(int n3) override { steps_taken += n3; nlaunch += n3 * launches_per_step(); }
     cudaStream_t stream() const override { return st; }
     int phase() const override { return cur; }
-    bool batchable() const override { return have_state && !poisoned && steps_taken > 0 && !prof; }
+    bool batchable() const override { return have_state && !poisoned && steps_taken > 0 && !prof && !classical; }
 
     // Captures three consecutive BDF2 steps starting at the current rotation
     // phase into this simulation's graph for that phase.
@@ -205,6 +219,9 @@ public:
         cudaFree(bufA); cudaFree(bufB); cudaFree(part1); cudaFree(part2); cudaFree(partd); cudaFree(part3);
         cudaFree(twM); cudaFree(twP); cudaFree(ev); cudaFree(sc); cudaFree(tmp64);
         cudaFree(tw2); cudaFree(evf); cudaFree(evp); cudaFree(twF); cudaFree(twI);
+        cudaFree(cl); cudaFree(pcg); cudaFree(cl_red);
+        if (pcg_host) cudaFreeHost(pcg_host);
+        cl = nullptr; pcg = nullptr; cl_red = nullptr; pcg_host = nullptr;
         tw2 = nullptr; evf = nullptr; evp = nullptr; twF = nullptr; twI = nullptr;
         if (sc_host) cudaFreeHost(sc_host);
         if (h_part) cudaFreeHost(h_part);
@@ -318,12 +335,113 @@ public:
         if (set_smem_limit((const void*)k_rowdct_T<T>, sm_rt) || set_smem_limit((const void*)k_coldct_gram<T>, sm_col) ||
             set_smem_limit((const void*)k_comb_icolT<T>, sm_comb) || set_smem_limit((const void*)k_irow<T>, sm_irow))
             return CCMSAV_ECUDA;
+        if (flags & CCMSAV_CLASSICAL) {
+            int r = init_classical();
+            if (r) return r;
+        }
         const char* force_block = std::getenv("CCMSAV_FORCE_BLOCK_FFT");   // test switch: block-FFT kernels only
         if (std::is_same<T, float>::value && M >= 64 && M <= 2048 && !(force_block && force_block[0] == '1')) {
             int r = init_warp_path();
             if (r) return r;
         }
         CCM_CUDA(cudaStreamSynchronize(st));
+        return CCMSAV_OK;
+    }
+
+    int init_classical() {
+        classical = true;
+        graphs_failed = true;            // the host reads convergence flags inside a step
+        pcg_rtol = std::is_same<T, float>::value ? 1e-6 : 1e-10;
+        if (cudaMalloc(&cl, 13 * NN * sizeof(T)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaMalloc(&pcg, sizeof(PcgScalars)) != cudaSuccess) return CCMSAV_ENOMEM;
+        if (cudaHostAlloc(&pcg_host, sizeof(PcgScalars), cudaHostAllocDefault) != cudaSuccess) return CCMSAV_ENOMEM;
+        CCM_CUDA(cudaMemsetAsync(pcg, 0, sizeof(PcgScalars), st));
+        const size_t nbw = (NN + kClThreads - 1) / kClThreads;
+        cl_nb = (int)(nbw < 1216 ? nbw : 1216);
+        if (cudaMalloc(&cl_red, (size_t)cl_nb * 2 * sizeof(double)) != cudaSuccess) return CCMSAV_ENOMEM;
+        cl_geo = ss::geometry<T>(N, false);
+        if (cl_geo.sm_fwd > kSmemMax || cl_geo.sm_col > kSmemMax || cl_geo.sm_inv > kSmemMax) return CCMSAV_EINVAL;
+        if (ss::optin_all<T>(cl_geo, false)) return CCMSAV_ECUDA;
+        return CCMSAV_OK;
+    }
+
+    // z = M^{-1} r for both systems (DCT solve of a - lam Mbar Lap_h with the
+    // coefficients on the device); converged systems are skipped.
+    void cl_precond(const T* r, T* z, T* scr) {
+        const dim3 g1(N / cl_geo.RT, 2), g2(N / cl_geo.RC, 2), b(cl_geo.threads);
+        // device addresses of the convergence flags and the coefficients
+        const int* conv = reinterpret_cast<const int*>(reinterpret_cast<const char*>(pcg) + offsetof(PcgScalars, conv));
+        const double* coef = reinterpret_cast<const double*>(reinterpret_cast<const char*>(pcg) + offsetof(PcgScalars, coef));
+        ss::k_ss_row_fwd<T, false><<<g1, b, cl_geo.sm_fwd, st>>>(r, scr, N, cl_geo.RT, cl_geo.lds, twM, twP, conv, NN);
+        ss::k_ss_col_solve<T><<<g2, b, cl_geo.sm_col, st>>>(scr, N, cl_geo.RC, twM, twP, ev, 0.0, 0.0, 0.0,
+                                                           coef, conv, NN);
+        ss::k_ss_row_inv<T, false><<<g1, b, cl_geo.sm_inv, st>>>(scr, z, N, cl_geo.RT, cl_geo.lds, twM, twP, conv, NN);
+        nlaunch += 3;
+    }
+
+    // The classical scheme's two Cahn-Hilliard solves y1 = zeta_c^{-1} g0c and
+    // y2 = zeta_c^{-1} LP by preconditioned CG, then (P, y1) and (P, y2).
+    // Reads the stencil's P and LP (bufA fields 5 and 7) before the column
+    // transforms overwrite bufA.
+    int queue_classical_ch(bool bdf1) {
+        T* Mx = cl;
+        T* My = cl + NN;
+        T* b1 = cl + 2 * NN;
+        T* x = cl + 3 * NN;
+        T* r = cl + 5 * NN;
+        T* pv = cl + 7 * NN;
+        T* zq = cl + 9 * NN;
+        T* scr = cl + 11 * NN;
+        const double a = bdf1 ? 1.0 / p.dt : 1.5 / p.dt;
+        const double h2i = 1.0 / (h() * h());
+        k_cl_prep<T><<<cl_nb, kClThreads, 0, st>>>(phi[cur], phi[prev], psi[cur], psi[prev], bdf1 ? 1 : 0, Mx, My, b1,
+                                                   cl_red, pcg, N, a, p.lam, p.M0, h2i, pcg_rtol);
+        k_cl_init<T><<<cl_nb, kClThreads, 0, st>>>(b1, bufA + 7 * NN, x, r, pv, cl_red, pcg, NN);
+        nlaunch += 2;
+        cl_precond(r, zq, scr);
+        k_cl_dot_rz<T><<<cl_nb, kClThreads, 0, st>>>(r, zq, cl_red, pcg, NN, 1);
+        k_cl_pupdate<T><<<cl_nb, kClThreads, 0, st>>>(zq, pv, pcg, NN);
+        nlaunch += 2;
+        for (int it = 1; it <= pcg_max_it; ++it) {
+            k_cl_apply<T><<<cl_nb, kClThreads, 0, st>>>(pv, Mx, My, zq, cl_red, pcg, N, a, p.lam * h2i);
+            k_cl_update<T><<<cl_nb, kClThreads, 0, st>>>(x, r, pv, zq, cl_red, pcg, NN);
+            nlaunch += 2;
+            cl_precond(r, zq, scr);
+            k_cl_dot_rz<T><<<cl_nb, kClThreads, 0, st>>>(r, zq, cl_red, pcg, NN, 0);
+            k_cl_pupdate<T><<<cl_nb, kClThreads, 0, st>>>(zq, pv, pcg, NN);
+            nlaunch += 2;
+            if (it % 4 == 0 || it == pcg_max_it) {
+                CCM_CUDA(cudaGetLastError());
+                CCM_CUDA(cudaMemcpyAsync(pcg_host, pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+                CCM_CUDA(cudaStreamSynchronize(st));
+                if (pcg_host->conv[0] && pcg_host->conv[1]) break;
+            }
+        }
+        k_cl_pdot<T><<<cl_nb, kClThreads, 0, st>>>(bufA + 5 * NN, x, cl_red, pcg, NN);
+        ++nlaunch;
+        CCM_CUDA(cudaGetLastError());
+        CCM_CUDA(cudaMemcpyAsync(pcg_host, pcg, sizeof(PcgScalars), cudaMemcpyDeviceToHost, st));
+        CCM_CUDA(cudaStreamSynchronize(st));
+        const int itmax = pcg_host->iters[0] > pcg_host->iters[1] ? pcg_host->iters[0] : pcg_host->iters[1];
+        pcg_last[0] = itmax;
+        for (int s = 0; s < 2; ++s)
+            pcg_last[1 + s] = pcg_host->rr0[s] > 0 ? std::sqrt(pcg_host->rr[s] / pcg_host->rr0[s]) : 0.0;
+        pcg_total += itmax;
+        return CCMSAV_OK;
+    }
+
+    int set_pcg(double rtol, int max_iter) override {
+        if (!classical) return CCMSAV_EINVAL;
+        if (!(std::isfinite(rtol) && rtol > 0.0) || max_iter < 1) return CCMSAV_EINVAL;
+        pcg_rtol = rtol;
+        pcg_max_it = max_iter;
+        return CCMSAV_OK;
+    }
+
+    int pcg_stats(double out[4]) override {
+        if (!classical) return CCMSAV_EINVAL;
+        CCM_CUDA(cudaStreamSynchronize(st));
+        out[0] = pcg_last[0]; out[1] = (double)pcg_total; out[2] = pcg_last[1]; out[3] = pcg_last[2];
         return CCMSAV_OK;
     }
 
@@ -640,6 +758,11 @@ public:
         mark(-1);
         k_stencil<T><<<g_st, b_st, stencil_smem_bytes<T>(), st>>>(phi[cur], phi[prev], psi[cur], psi[prev], bufA, part1, N, c);
         mark(0);
+        if (classical) {
+            int r = queue_classical_ch(bdf1);
+            if (r) return r;
+            mark(7);
+        }
         if (warp_path) {
             warp_forward(s, anchor);
             so.nb2 = N / wKC;
@@ -651,6 +774,10 @@ public:
         }
         {   // partial rows: FP64, or float pairs on the FP32 path
             using P = typename PartialOf<T>::type;
+            if (classical) {   // the psi entries from the conjugate-gradient solves
+                k_cl_inject<P><<<(so.nb2 + 255) / 256, 256, 0, st>>>(reinterpret_cast<P*>(part2), so.nb2, pcg);
+                ++nlaunch;
+            }
             k_solve<P><<<kSolveBlocks, kSolveThreads, 0, st>>>(reinterpret_cast<const P*>(part1), so.nb1,
                                                                reinterpret_cast<const P*>(part2), so.nb2, part3, sc, so);
         }
@@ -666,6 +793,10 @@ public:
             mark(5);
         }
         nlaunch += 6;
+        if (classical) {
+            k_cl_psi<T><<<cl_nb, kClThreads, 0, st>>>(psi[cur], psi[prev], cl + 3 * NN, sc, bdf1 ? 1 : 0, psi[spare], NN);
+            ++nlaunch;
+        }
         if (!bdf1 && (flags & CCMSAV_TRACK_ENERGY)) {
             k_dnorm<T><<<g_dg, 256, 0, st>>>(phi[cur], phi[prev], psi[spare], psi[cur], psi[prev], partd, N, p.M0);
             k_add_lamsum<<<1, 256, 0, st>>>(partd, nbd, 0.5 * dt * p.lam * p.lam, sc);

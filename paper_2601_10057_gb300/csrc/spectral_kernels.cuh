@@ -17,6 +17,11 @@
 // The paper names the DST and FFT solvers as the fast solvers for Dirichlet
 // and periodic boundaries (Sec. 5, limitations and scope).
 //
+// The DCT/DST kernels transform gridDim.y fields at once (field f at offset
+// f * fstride of every array); a field whose dskip[f] is set is left alone
+// (iterations of a solver that has converged), and dcoef, if given, holds
+// the coefficients c0, c1, c2 on the device.
+//
 // Data flow of one solve (three kernels):
 //   k_ss_row_fwd    transform along x of RT rows, written transposed (line kx
 //                   of the scratch holds the column-x spectra over y);
@@ -43,7 +48,11 @@ template <typename T> __device__ __forceinline__ T alt(int i) { return (i & 1) ?
 template <typename T, bool DST>
 __global__ void __launch_bounds__(512)
 k_ss_row_fwd(const T* __restrict__ in, T* __restrict__ out, int N, int RT, int lds,
-             const cplx<T>* __restrict__ twM, const PostTw<T>* __restrict__ twP) {
+             const cplx<T>* __restrict__ twM, const PostTw<T>* __restrict__ twP,
+             const int* __restrict__ dskip, size_t fstride) {
+    if (dskip && dskip[blockIdx.y]) return;
+    in += blockIdx.y * fstride;
+    out += blockIdx.y * fstride;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int M = N / 2, ldc = padded_len(M);
     const int E = M < 8 ? M : 8, G = M / E, P = blockDim.x / G;
@@ -92,7 +101,11 @@ template <typename T>
 __global__ void __launch_bounds__(512)
 k_ss_col_solve(T* __restrict__ data, int N, int RC, const cplx<T>* __restrict__ twM,
                const PostTw<T>* __restrict__ twP, const double* __restrict__ ev,
-               double c0, double c1, double c2) {
+               double c0, double c1, double c2, const double* __restrict__ dcoef,
+               const int* __restrict__ dskip, size_t fstride) {
+    if (dskip && dskip[blockIdx.y]) return;
+    data += blockIdx.y * fstride;
+    if (dcoef) { c0 = dcoef[0]; c1 = dcoef[1]; c2 = dcoef[2]; }   // coefficients formed on the device
     extern __shared__ __align__(16) unsigned char smraw[];
     const int M = N / 2, ldc = padded_len(M);
     const int E = M < 8 ? M : 8, G = M / E, P = blockDim.x / G;
@@ -141,7 +154,11 @@ k_ss_col_solve(T* __restrict__ data, int N, int RC, const cplx<T>* __restrict__ 
 template <typename T, bool DST>
 __global__ void __launch_bounds__(512)
 k_ss_row_inv(const T* __restrict__ in, T* __restrict__ out, int N, int RT, int lds,
-             const cplx<T>* __restrict__ twM, const PostTw<T>* __restrict__ twP) {
+             const cplx<T>* __restrict__ twM, const PostTw<T>* __restrict__ twP,
+             const int* __restrict__ dskip, size_t fstride) {
+    if (dskip && dskip[blockIdx.y]) return;
+    in += blockIdx.y * fstride;
+    out += blockIdx.y * fstride;
     extern __shared__ __align__(16) unsigned char smraw[];
     const int M = N / 2, ldc = padded_len(M);
     const int E = M < 8 ? M : 8, G = M / E, P = blockDim.x / G;
@@ -289,6 +306,82 @@ __global__ void k_smooth_rhs(const T* __restrict__ phi, T* __restrict__ r, int N
         const double lap = (g(i + 1, j) - gc) + (g(i - 1, j) - gc) + ((g(i, j + 1) - gc) + (g(i, j - 1) - gc));
         r[q] = (T)((double)phi[q] * inv_dt + mob_inv_h2 * lap);
     }
+}
+
+// ------------------------------------------------------------------ launch geometry
+// Threads per CTA, rows per CTA of the row kernels (RT), lines per CTA of the
+// column kernel (RC) and the dynamic shared memory of each, for N x N fields
+// of precision T (periodic: full-length complex lines).
+struct Geo {
+    int threads = 256, RT = 1, RC = 1, lds = 0;
+    size_t sm_fwd = 0, sm_col = 0, sm_inv = 0;
+};
+
+template <typename T> inline Geo geometry(int N, bool periodic) {
+    constexpr size_t cap = 200 * 1024;
+    Geo g;
+    const int M = periodic ? N : N / 2;                // complex line length
+    const int E = M < 8 ? M : 8, G = M / E;
+    g.threads = G > 256 ? G : 256;                     // <= 512 for DCT lines, <= 1024 periodic
+    const int P = g.threads / G;                       // lines transformed at once
+    const size_t line = (size_t)padded_len(M) * sizeof(cplx<T>);
+    if (periodic) {
+        int rt = 8;
+        while (rt > 1 && ((size_t)rt * line > cap || N % rt)) rt /= 2;
+        if (rt > N) rt = N;
+        g.RT = g.RC = rt;
+        g.sm_fwd = g.sm_col = g.sm_inv = (size_t)rt * line;
+    } else {
+        g.lds = N + 1;
+        auto rows_bytes = [&](int rt) {
+            return (((size_t)rt * g.lds * sizeof(T) + 15) & ~(size_t)15) + (size_t)(rt < P ? rt : P) * line;
+        };
+        int rt = 16;
+        while (rt > 1 && (rows_bytes(rt) > cap || N % rt)) rt /= 2;
+        if (rt > N) rt = N;
+        g.RT = rt;
+        g.sm_fwd = g.sm_inv = rows_bytes(rt);
+        int rc = P < 8 ? P : 8;
+        while (rc > 1 && ((size_t)rc * line > cap || N % rc)) rc /= 2;
+        g.RC = rc;
+        g.sm_col = (size_t)rc * line;
+    }
+    return g;
+}
+
+// Opt a kernel in to the largest dynamic shared memory a block can take (the
+// attribute is per kernel and process-wide, so it must not depend on one
+// grid size); fails if that is below `bytes`.
+inline int optin_smem(const void* fn, size_t bytes) {
+    int dev = 0, optin = 0;
+    cudaFuncAttributes fa;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
+        cudaFuncGetAttributes(&fa, fn) != cudaSuccess)
+        return -3;   // CCMSAV_ECUDA
+    const int lim = optin - (int)fa.sharedSizeBytes;
+    if (lim < 0 || (size_t)lim < bytes) return -1;   // CCMSAV_EINVAL
+    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess ? 0 : -3;
+}
+
+// Opt in every DCT/DST kernel of precision T (Neumann and Dirichlet) or every
+// periodic one.
+template <typename T> inline int optin_all(const Geo& g, bool periodic) {
+    int r = 0;
+    if (periodic) {
+        if ((r = optin_smem((const void*)k_ss_row_fwd_p<T>, g.sm_fwd)) ||
+            (r = optin_smem((const void*)k_ss_col_solve_p<T>, g.sm_col)) ||
+            (r = optin_smem((const void*)k_ss_row_inv_p<T>, g.sm_inv)))
+            return r;
+    } else {
+        if ((r = optin_smem((const void*)k_ss_row_fwd<T, false>, g.sm_fwd)) ||
+            (r = optin_smem((const void*)k_ss_row_fwd<T, true>, g.sm_fwd)) ||
+            (r = optin_smem((const void*)k_ss_col_solve<T>, g.sm_col)) ||
+            (r = optin_smem((const void*)k_ss_row_inv<T, false>, g.sm_inv)) ||
+            (r = optin_smem((const void*)k_ss_row_inv<T, true>, g.sm_inv)))
+            return r;
+    }
+    return 0;
 }
 
 // phi <- max(-1, min(1, phi)) (the final step of Appendix F)

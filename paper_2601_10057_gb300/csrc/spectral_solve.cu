@@ -31,72 +31,17 @@ using ccm::cplx;
 using ccm::PostTw;
 namespace ss = ccm::ss;
 
-constexpr size_t kSmemCap = 200 * 1024;
-
-// Opt a kernel in to the largest dynamic shared memory a block can take (the
-// attribute is per kernel and process-wide, so it must not depend on the N
-// of one solver); fails if that is below what this solver needs.
-template <typename T> int set_smem(const void* fn, size_t bytes) {
-    int dev = 0, optin = 0;
-    cudaFuncAttributes fa;
-    if (cudaGetDevice(&dev) != cudaSuccess ||
-        cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess ||
-        cudaFuncGetAttributes(&fa, fn) != cudaSuccess)
-        return CCMSAV_ECUDA;
-    const int lim = optin - (int)fa.sharedSizeBytes;
-    if (lim < 0 || (size_t)lim < bytes) return CCMSAV_EINVAL;
-    return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, lim) == cudaSuccess
-               ? CCMSAV_OK : CCMSAV_ECUDA;
-}
-
 // Launch geometry and tables of one solver (precision T).
 template <typename T> int setup(ccmsav_solver* s) {
     const int N = s->N;
     const double h = s->L / N;
     const bool per = s->bc == CCMSAV_BC_PERIODIC;
     const int M = per ? N : N / 2;                     // complex line length
-    const int E = M < 8 ? M : 8, G = M / E;
-    s->threads = G > 256 ? G : 256;     // <= 512 for DCT lines, <= 1024 for periodic ones
-    const int P = s->threads / G;                      // lines transformed at once
-    const size_t line = (size_t)ccm::padded_len(M) * sizeof(cplx<T>);
     const size_t NN = (size_t)N * N;
-    if (per) {
-        // every line of a CTA resident at once
-        int rt = 8;
-        while (rt > 1 && ((size_t)rt * line > kSmemCap || N % rt)) rt /= 2;
-        if (rt > N) rt = N;
-        s->RT = s->RC = rt;
-        s->sm_fwd = s->sm_col = s->sm_inv = (size_t)rt * line;
-    } else {
-        s->lds = N + 1;
-        auto rows_bytes = [&](int rt) {
-            return (((size_t)rt * s->lds * sizeof(T) + 15) & ~(size_t)15) + (size_t)(rt < P ? rt : P) * line;
-        };
-        int rt = 16;
-        while (rt > 1 && (rows_bytes(rt) > kSmemCap || N % rt)) rt /= 2;
-        if (rt > N) rt = N;
-        s->RT = rt;
-        s->sm_fwd = s->sm_inv = rows_bytes(rt);
-        int rc = P < 8 ? P : 8;
-        while (rc > 1 && ((size_t)rc * line > kSmemCap || N % rc)) rc /= 2;
-        s->RC = rc;
-        s->sm_col = (size_t)rc * line;
-    }
-    if (s->sm_fwd > kSmemCap || s->sm_col > kSmemCap || s->sm_inv > kSmemCap) return CCMSAV_EINVAL;
-    int r = CCMSAV_OK;
-    if (per) {
-        if ((r = set_smem<T>((const void*)ss::k_ss_row_fwd_p<T>, s->sm_fwd)) ||
-            (r = set_smem<T>((const void*)ss::k_ss_col_solve_p<T>, s->sm_col)) ||
-            (r = set_smem<T>((const void*)ss::k_ss_row_inv_p<T>, s->sm_inv)))
-            return r;
-    } else {
-        if ((r = set_smem<T>((const void*)ss::k_ss_row_fwd<T, false>, s->sm_fwd)) ||
-            (r = set_smem<T>((const void*)ss::k_ss_row_fwd<T, true>, s->sm_fwd)) ||
-            (r = set_smem<T>((const void*)ss::k_ss_col_solve<T>, s->sm_col)) ||
-            (r = set_smem<T>((const void*)ss::k_ss_row_inv<T, false>, s->sm_inv)) ||
-            (r = set_smem<T>((const void*)ss::k_ss_row_inv<T, true>, s->sm_inv)))
-            return r;
-    }
+    const ss::Geo g = ss::geometry<T>(N, per);
+    s->threads = g.threads; s->RT = g.RT; s->RC = g.RC; s->lds = g.lds;
+    s->sm_fwd = g.sm_fwd; s->sm_col = g.sm_col; s->sm_inv = g.sm_inv;
+    if (const int r = ss::optin_all<T>(g, per)) return r;
     // tables, computed on the host in FP64 and rounded to T
     std::vector<cplx<T>> hw(M);
     for (int t = 0; t < M; ++t) {
@@ -144,14 +89,15 @@ template <typename T> int solve(ccmsav_solver* s, const double c[3], const T* f,
         T* sc = static_cast<T*>(s->scratch);
         const PostTw<T>* tp = static_cast<const PostTw<T>*>(s->twP);
         if (s->bc == CCMSAV_BC_DIRICHLET)
-            ss::k_ss_row_fwd<T, true><<<N / s->RT, b, s->sm_fwd, s->st>>>(f, sc, N, s->RT, s->lds, tw, tp);
+            ss::k_ss_row_fwd<T, true><<<N / s->RT, b, s->sm_fwd, s->st>>>(f, sc, N, s->RT, s->lds, tw, tp, nullptr, 0);
         else
-            ss::k_ss_row_fwd<T, false><<<N / s->RT, b, s->sm_fwd, s->st>>>(f, sc, N, s->RT, s->lds, tw, tp);
-        ss::k_ss_col_solve<T><<<N / s->RC, b, s->sm_col, s->st>>>(sc, N, s->RC, tw, tp, s->ev, c[0], c[1], c[2]);
+            ss::k_ss_row_fwd<T, false><<<N / s->RT, b, s->sm_fwd, s->st>>>(f, sc, N, s->RT, s->lds, tw, tp, nullptr, 0);
+        ss::k_ss_col_solve<T><<<N / s->RC, b, s->sm_col, s->st>>>(sc, N, s->RC, tw, tp, s->ev, c[0], c[1], c[2],
+                                                                   nullptr, nullptr, 0);
         if (s->bc == CCMSAV_BC_DIRICHLET)
-            ss::k_ss_row_inv<T, true><<<N / s->RT, b, s->sm_inv, s->st>>>(sc, u, N, s->RT, s->lds, tw, tp);
+            ss::k_ss_row_inv<T, true><<<N / s->RT, b, s->sm_inv, s->st>>>(sc, u, N, s->RT, s->lds, tw, tp, nullptr, 0);
         else
-            ss::k_ss_row_inv<T, false><<<N / s->RT, b, s->sm_inv, s->st>>>(sc, u, N, s->RT, s->lds, tw, tp);
+            ss::k_ss_row_inv<T, false><<<N / s->RT, b, s->sm_inv, s->st>>>(sc, u, N, s->RT, s->lds, tw, tp, nullptr, 0);
     }
     s->launches += 3;
     return cudaPeekAtLastError() == cudaSuccess ? CCMSAV_OK : CCMSAV_ECUDA;
