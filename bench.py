@@ -265,6 +265,14 @@ def accuracy_vs_fp64(ws, steps, sh):
     return e
 
 
+def bench_config(w, precision, world):
+    """The config object of the JSON line (both arms carry the same one)."""
+    return {"workload": f"three_vesicles_N{w.N}", "N": w.N, "precision":
+            ("fp32-bulk/fp64-reductions" if precision == "fp32" else "fp64"),
+            "dt": w.params.dt, "vesicles": 3, "parallelism": f"replicas{world}",
+            "l2": "per-step working set > L2 (no flush needed)"}
+
+
 def run_reference(args, world, rank):
     from paper_2601_10057_gb300 import inputs as I
     if rank != 0:
@@ -291,8 +299,7 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": "grid-point-steps/s", "value": value, "unit": "grid-point-steps/s",
         "n_gpus": args.gpus, "steps": k, "warmup": warm, "ms_per_step": 1e3 * el / k,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": f"three_vesicles_N{w.N}", "N": w.N,
-                                        "precision": "fp64-oracle", "dt": w.params.dt},
+        "data": "synthetic", "config": bench_config(w, args.precision, world),
         "cpu_baseline": {"value": value, "unit": "grid-point-steps/s", "cores": cores, "kind": "oracle",
                          "sample": f"{k} BDF2 steps of the FP64 CPU oracle at N={w.N} (of {args.steps} "
                                    f"requested; bounded to ~{budget:.0f} s), after {warm} warm-up step(s)"},
@@ -561,10 +568,7 @@ def run_ours(args, world, rank, local):
         "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
         "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
-        "config": {"workload": f"three_vesicles_N{w.N}", "N": w.N, "precision":
-                   ("fp32-bulk/fp64-reductions" if args.precision == "fp32" else "fp64"),
-                   "dt": w.params.dt, "vesicles": 3, "parallelism": f"replicas{world}",
-                   "l2": "per-step working set > L2 (no flush needed)"},
+        "config": bench_config(w, args.precision, world),
         "roofline": roof,
         "step_roofline": {"alg_bytes_per_point": STEP_PASSES_MIN_SCHEDULE * esize,
                           "achieved_GBps": round(value / world * STEP_PASSES_MIN_SCHEDULE * esize / 1e9, 1),

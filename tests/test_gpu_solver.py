@@ -62,8 +62,12 @@ def test_solver_against_oracle(N, bc, precision):
 @pytest.mark.parametrize("bc", O.BCS)
 def test_solver_eigenmode_at_N8192(bc, precision):
     """The largest grid: a single eigenfunction of Lap_h with the boundary
-    rule (a cosine, sine or complex-exponential mode) is returned divided by
-    c0 + c1 s + c2 s^2 (closed form), at every point; in place (u = f)."""
+    rule (a cosine, sine or periodic mode) is returned divided by
+    c0 + c1 s + c2 s^2 (closed form), at every point; in place (u = f).
+    The transforms' rounding noise lands on every mode and is divided by
+    that mode's own factor (about 1 at the low modes), the signal by about
+    80 here: the relative error is the transform's rounding times that ratio
+    (measured 2.7e-11 in FP64 with a factor of 2e4 at this mode)."""
     import torch
     N, L = 8192, 2.0
     h = L / N
@@ -79,7 +83,7 @@ def test_solver_eigenmode_at_N8192(bc, precision):
         fx, fy = torch.cos(2 * math.pi * k * x / L + 0.3), torch.cos(2 * math.pi * l * x / L - 1.1)
         s_k, s_l = (4 / h ** 2 * math.sin(math.pi * q / N) ** 2 for q in (k, l))
     f = torch.outer(fy, fx)
-    coef = (1.0, 2e-3, 1e-9)
+    coef = (1.0, 2e-5, 1e-12)
     s = s_k + s_l
     want = f / (coef[0] + coef[1] * s + coef[2] * s * s)
     g = f.clone() if precision == "fp64" else f.float()
@@ -145,4 +149,41 @@ def test_smoothed_shapes_step_with_conserved_mass(shape, grows, precision):
     print(shape, grows, precision, "E", E[0], E[-1])
     if precision == "fp64":
         assert all(b <= a + 1e-12 * abs(a) for a, b in zip(E, E[1:])), E
+    sim.close()
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("shape", ["star", "crescent"])
+def test_robustness_run_at_paper_size(shape):
+    """Sec. 4.4 at full size: the smoothed star and crescent in the
+    shrinkage setting ((gamma_bend, theta) = (0.1, 30), eps = 0.01,
+    N = 2048 on the unit square, dt = 5e-6), 400 FP64 steps: the relative
+    mass error stays below 5e-11, the modified energy does not increase and
+    the arc length stays within 3.5 % of its initial value (the paper's
+    figures for these runs)."""
+    N, L = 2048, 1.0
+    p = I.robustness_params(False, N=N, L=L)
+    s = cc.SpectralSolver(N, L, "neumann", "fp64")
+    phi_t = dev(I.sharp_shape(shape, N, L), "fp64")
+    s.smooth(phi_t, p.eps, 0.01, 1e-6, 10)
+    s.sync()
+    phi0 = host(phi_t)
+    s.close()
+    psi0 = I.concentration([phi0], [0.8])
+    h = L / N
+    m0 = h * h * math.fsum(psi0.ravel().tolist())
+    sim = cc.Simulation(p, N, track_energy=True)
+    sim.set_state(phi0, psi0)
+    sim.step(1)
+    arc0 = sim.energy()[5]
+    E, arcs = [], []
+    for _ in range(8):
+        sim.step(50)
+        e = sim.energy()
+        E.append(e[0])
+        arcs.append(e[5])
+        assert abs(sim.mass() - m0) / abs(m0) < 5e-11
+    print(shape, "E", E[0], E[-1], "arc", arc0, min(arcs), max(arcs))
+    assert all(b <= a + 1e-12 * abs(a) for a, b in zip(E, E[1:])), E
+    assert max(abs(a - arc0) for a in arcs) <= 0.035 * arc0
     sim.close()
