@@ -214,6 +214,22 @@ long long ccmsav_launch_count(ccmsav_t* h);
 int ccmsav_profile(ccmsav_t* h, int enable);
 int ccmsav_profile_read(ccmsav_t* h, int sim, double ms[8], long long* nsteps);
 
+/* Autotuner of the line-transform schedule.  For every distinct grid size
+ * of the handle it times `steps` BDF2 steps (rounded up to a multiple of
+ * three, after three warm-up steps) of each candidate schedule from the
+ * simulation's current state, keeps the fastest and restores the state (the
+ * fields and scalars are unchanged afterwards).  Candidates (FP32): the
+ * warp-level four-step FFT kernels with a shared-memory carveout of 72, 58
+ * or 100 percent for the three 8-line transform kernels, and the CTA-level
+ * Stockham FFT kernels; FP64 has only the latter.  The choice is recorded
+ * for (N, precision) in a process-wide table: simulations of that size in
+ * this handle take it at once, handles created later start from it.
+ * report (may be NULL) receives 4 doubles per simulation: warp path (1/0),
+ * carveout, best ms/step, ms/step of the default schedule (0 when not timed).
+ * Needs set_state for every simulation (CCMSAV_ESTATE otherwise); steps in
+ * [1, 3000]; not for CCMSAV_CLASSICAL handles (CCMSAV_EINVAL).  Synchronises. */
+int ccmsav_autotune(ccmsav_t* h, int steps, double* report);
+
 /* Conjugate-gradient settings of a CCMSAV_CLASSICAL handle (all its
  * simulations): stop when ||r||_2 <= rtol ||b||_2 (rtol > 0; default 1e-10
  * for FP64, 1e-6 for FP32) or after max_iter iterations (>= 1; default 200).

@@ -91,6 +91,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "ccmsav_destroy": (None, [vp]),
         "ccmsav_mass_noalloc": (i, [vp, i, i, d, _DP, vp]),
         "ccmsav_set_pcg": (i, [vp, d, i]),
+        "ccmsav_autotune": (i, [vp, i, _DP]),
         "ccmsav_pcg_stats": (i, [vp, i, _DP]),
         "ccmsav_solver_create": (i, [C.POINTER(vp), i, d, i, i, vp]),
         "ccmsav_solver_solve": (i, [vp, _DP, vp, vp]),
@@ -238,6 +239,14 @@ def ccmsav_mass_noalloc(psi_ptr: int, N: int, precision: int, L: float, stream: 
     return st, float(out[0])
 
 
+def ccmsav_autotune(h, steps: int, n_sims: int):
+    """Returns (status, report[n_sims, 4]): warp path, carveout, best and
+    default ms/step per simulation."""
+    rep = np.zeros((n_sims, 4), np.float64)
+    st = load().ccmsav_autotune(h, int(steps), _ptr(rep))
+    return st, rep
+
+
 def ccmsav_set_pcg(h, rtol: float, max_iter: int) -> int:
     return load().ccmsav_set_pcg(h, float(rtol), int(max_iter))
 
@@ -343,6 +352,12 @@ class Simulation:
 
     def launches(self) -> int:
         return ccmsav_launch_count(self.h)
+
+    def autotune(self, steps: int = 12):
+        """Pick the fastest line-transform schedule per grid size (ccmsav_autotune)."""
+        st, rep = ccmsav_autotune(self.h, steps, len(self.N))
+        self._check(st, "ccmsav_autotune")
+        return rep
 
     def set_pcg(self, rtol: float, max_iter: int = 200):
         self._check(ccmsav_set_pcg(self.h, rtol, max_iter), "ccmsav_set_pcg")

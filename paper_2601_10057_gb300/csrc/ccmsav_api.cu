@@ -254,6 +254,34 @@ int ccmsav_pcg_stats(ccmsav_t* h, int sim, double out[4]) {
     return s->pcg_stats(out);
 }
 
+int ccmsav_autotune(ccmsav_t* h, int steps, double* report) {
+    if (!h || steps < 1 || steps > 3000) return CCMSAV_EINVAL;
+    if (h->flags & CCMSAV_CLASSICAL) return CCMSAV_EINVAL;
+    int r = ccmsav_sync(h);
+    if (r) return r;
+    std::vector<int> done_N;
+    std::vector<double> row(4);
+    for (size_t k = 0; k < h->sims.size(); ++k) {
+        ccm::SimBase* s = h->sims[k];
+        if (!s->has_state()) return CCMSAV_ESTATE;
+        bool seen = false;
+        for (int n : done_N) seen = seen || n == s->N;
+        if (!seen) {
+            if ((r = s->autotune(steps, row.data()))) return r;
+            done_N.push_back(s->N);
+            // the other simulations of this size take the same schedule
+            for (size_t j = k + 1; j < h->sims.size(); ++j)
+                if (h->sims[j]->N == s->N && (r = h->sims[j]->autotune_apply_cached())) return r;
+        }
+        if (report) {
+            const int rr = s->autotune_report(report + 4 * k);
+            if (rr) return rr;
+        }
+    }
+    for (int i = 0; i < 3; ++i) if (h->bexec[i]) { cudaGraphExecDestroy(h->bexec[i]); h->bexec[i] = nullptr; }
+    return CCMSAV_OK;
+}
+
 int ccmsav_grid_size(ccmsav_t* h, int sim) {
     ccm::SimBase* s = get(h, sim);
     if (!s) return CCMSAV_EINVAL;

@@ -36,6 +36,10 @@ public:
     // classical MSAV (CCMSAV_CLASSICAL): conjugate-gradient settings and statistics
     virtual int set_pcg(double rtol, int max_iter) = 0;
     virtual int pcg_stats(double out[4]) = 0;
+    // autotuner of the line-transform schedule (see ccmsav_autotune)
+    virtual int autotune(int k, double out[4]) = 0;
+    virtual int autotune_apply_cached() = 0;       // take this N's recorded schedule
+    virtual int autotune_report(double out[4]) = 0; // {warp path, carveout, best ms, default ms}
     int N = 0;
 };
 

@@ -25,8 +25,20 @@
 #include "spectral_kernels.cuh"
 #include "classical_kernels.cuh"
 #include <type_traits>
+#include <map>
+#include <mutex>
 
 namespace ccm {
+
+// Schedule chosen by the autotuner for one (grid size, precision): the FFT
+// path of the line transforms (warp-level four-step FFT or CTA-level Stockham
+// FFT) and the shared-memory carveout of the three 8-line warp-FFT kernels.
+// Process-wide, so handles created later with the same N start from it.
+struct TuneChoice { int warp = 1; int carveout = 72; double ms = 0.0, ms_default = 0.0; };
+template <typename T> struct TuneTable {
+    static std::mutex& mu() { static std::mutex m; return m; }
+    static std::map<int, TuneChoice>& table() { static std::map<int, TuneChoice> t; return t; }
+};
 
 #define CCM_CUDA(call)                                  \
     do {                                                \
@@ -438,6 +450,136 @@ public:
         return CCMSAV_OK;
     }
 
+    // ---- autotuner --------------------------------------------------------
+    template <int MM> int apply_carveout_M(int c) {
+        if (cudaFuncSetAttribute((const void*)kw_rowdct_T<MM>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess ||
+            cudaFuncSetAttribute((const void*)kw_coldct_gram<MM>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess ||
+            cudaFuncSetAttribute((const void*)kw_comb_icolT<MM>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess)
+            return CCMSAV_ECUDA;
+        return CCMSAV_OK;
+    }
+    int apply_carveout(int c) {
+        if constexpr (std::is_same<T, float>::value) {
+            switch (M) {
+                case 64: return apply_carveout_M<64>(c);
+                case 128: return apply_carveout_M<128>(c);
+                case 256: return apply_carveout_M<256>(c);
+                case 512: return apply_carveout_M<512>(c);
+                case 1024: return apply_carveout_M<1024>(c);
+                case 2048: return apply_carveout_M<2048>(c);
+            }
+        }
+        return CCMSAV_OK;
+    }
+    void drop_graphs() {
+        if (st) cudaStreamSynchronize(st);
+        for (int i = 0; i < 3; ++i) {
+            if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
+            if (gexec1[i]) cudaGraphExecDestroy(gexec1[i]);
+            gexec[i] = gexec1[i] = nullptr;
+        }
+    }
+    // Apply a schedule (the warp path only where it was set up).
+    int apply_choice(const TuneChoice& c) {
+        drop_graphs();
+        warp_path = have_warp && c.warp;
+        return have_warp ? apply_carveout(c.carveout) : CCMSAV_OK;
+    }
+    bool have_warp = false;
+
+    // Times `k` steps (a multiple of three, after three warm-up steps that
+    // capture the graphs) of each candidate schedule from the same saved
+    // state, keeps the fastest, restores the state and records the choice for
+    // this (N, precision).  out = {warp, carveout, best ms/step, ms/step of
+    // the default schedule}.
+    int autotune(int k, double out[4]) override {
+        if (!have_state || poisoned || classical) return CCMSAV_ESTATE;
+        if (k < 3) k = 3;
+        k = (k + 2) / 3 * 3;
+        std::vector<TuneChoice> cand;
+        if (have_warp)
+            for (int c : {72, 58, 100}) { TuneChoice t; t.warp = 1; t.carveout = c; cand.push_back(t); }
+        { TuneChoice t; t.warp = 0; t.carveout = 72; cand.push_back(t); }
+        // save the state: four levels, the scalars, the host counters
+        T* snap = nullptr;
+        if (cudaMalloc(&snap, 4 * NN * sizeof(T)) != cudaSuccess) return CCMSAV_ENOMEM;
+        DevScalars sc0;
+        const int c0 = cur, p0 = prev, s0 = spare;
+        const long long st0 = steps_taken;
+        T* lv[4] = {phi[cur], psi[cur], phi[prev], psi[prev]};
+        int r = CCMSAV_OK;
+        for (int q = 0; q < 4 && !r; ++q)
+            if (cudaMemcpyAsync(snap + q * NN, lv[q], NN * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess) r = CCMSAV_ECUDA;
+        if (!r && cudaMemcpyAsync(&sc0, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st) != cudaSuccess) r = CCMSAV_ECUDA;
+        if (!r && cudaStreamSynchronize(st) != cudaSuccess) r = CCMSAV_ECUDA;
+        auto restore = [&]() -> int {
+            cur = c0; prev = p0; spare = s0; steps_taken = st0;
+            T* dst[4] = {phi[cur], psi[cur], phi[prev], psi[prev]};
+            for (int q = 0; q < 4; ++q)
+                if (cudaMemcpyAsync(dst[q], snap + q * NN, NN * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                    return CCMSAV_ECUDA;
+            if (cudaMemcpyAsync(sc, &sc0, sizeof(DevScalars), cudaMemcpyHostToDevice, st) != cudaSuccess) return CCMSAV_ECUDA;
+            return cudaStreamSynchronize(st) == cudaSuccess ? CCMSAV_OK : CCMSAV_ECUDA;
+        };
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (!r && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) r = CCMSAV_ECUDA;
+        double best = 1e300, dflt = 0.0;
+        size_t bi = 0;
+        for (size_t i = 0; i < cand.size() && !r; ++i) {
+            if ((r = apply_choice(cand[i])) || (r = restore())) break;
+            if (steps_taken == 0) { if ((r = queue_steps(1))) break; }   // start step outside the timing
+            if ((r = queue_steps(3))) break;
+            if (cudaEventRecord(e0, st) != cudaSuccess) { r = CCMSAV_ECUDA; break; }
+            if ((r = queue_steps(k))) break;
+            if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { r = CCMSAV_ECUDA; break; }
+            if ((r = device_status())) break;
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            const double per = ms / k;
+            if (i == 0) dflt = per;
+            if (per < best) { best = per; bi = i; }
+        }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        TuneChoice ch = cand[bi];
+        ch.ms = best; ch.ms_default = dflt;
+        if (!r) r = apply_choice(ch);
+        const int r2 = restore();
+        cudaFree(snap);
+        poisoned = false;
+        if (r) return r;
+        if (r2) return r2;
+        {
+            std::lock_guard<std::mutex> lk(TuneTable<T>::mu());
+            TuneTable<T>::table()[N] = ch;
+        }
+        out[0] = ch.warp && have_warp ? 1.0 : 0.0; out[1] = ch.carveout; out[2] = ch.ms; out[3] = ch.ms_default;
+        return CCMSAV_OK;
+    }
+
+    int autotune_apply_cached() override {
+        TuneChoice c;
+        {
+            std::lock_guard<std::mutex> lk(TuneTable<T>::mu());
+            auto it = TuneTable<T>::table().find(N);
+            if (it == TuneTable<T>::table().end()) return CCMSAV_OK;
+            c = it->second;
+        }
+        return apply_choice(c);
+    }
+
+    int autotune_report(double out[4]) override {
+        TuneChoice c;
+        c.carveout = kRowCarveout;
+        {
+            std::lock_guard<std::mutex> lk(TuneTable<T>::mu());
+            auto it = TuneTable<T>::table().find(N);
+            if (it != TuneTable<T>::table().end()) c = it->second;
+        }
+        out[0] = warp_path ? 1.0 : 0.0; out[1] = c.carveout; out[2] = c.ms; out[3] = c.ms_default;
+        return CCMSAV_OK;
+    }
+
     int pcg_stats(double out[4]) override {
         if (!classical) return CCMSAV_EINVAL;
         CCM_CUDA(cudaStreamSynchronize(st));
@@ -553,7 +695,15 @@ public:
             case 1024: r = setup_warp<1024>(); break;
             case 2048: r = setup_warp<2048>(); break;
         }
-        if (r == CCMSAV_OK) warp_path = true;
+        if (r == CCMSAV_OK) warp_path = have_warp = true;
+        if (r == CCMSAV_OK) {   // a schedule the autotuner chose for this N
+            std::lock_guard<std::mutex> lk(TuneTable<T>::mu());
+            auto it = TuneTable<T>::table().find(N);
+            if (it != TuneTable<T>::table().end()) {
+                warp_path = it->second.warp != 0;
+                r = apply_carveout(it->second.carveout);
+            }
+        }
         return r;
     }
 

@@ -508,3 +508,39 @@ def test_bdf1_mode_against_oracle(precision, tol):
               + 0.5 * m.gamma_area * s.U ** 2 + 0.5 * m.gamma_bend * 3 * SQ2 / (8 * m.eps) * s.W ** 2
               + 0.5 * s.Z ** 2)
         assert E[0] == pytest.approx(E1, rel=1e-10)
+
+
+def test_autotune_keeps_state_and_records_schedule():
+    """ccmsav_autotune times the candidate schedules from the current state
+    and restores it: the fields and scalars after tuning are bit-identical to
+    those before, the report names a schedule per simulation (sizes tuned
+    once), and stepping on agrees with an untuned run (FP32: the warp and
+    block paths round differently, within 5e-6)."""
+    ws = [I.workload("one_vesicle", N=128, dt=1e-5), I.workload("ellipse_shrink", N=256),
+          I.workload("one_vesicle", N=128, dt=2e-5)]
+    sim = cc.Simulation(None, [w.N for w in ws], per_sim=[w.params for w in ws], precision="fp32")
+    for k, w in enumerate(ws):
+        sim.set_state(w.phi0, w.psi0, sim=k)
+    sim.step(4)
+    before = [(*sim.state(sim=k), sim.state(sim=k, prev=True), sim.aux(sim=k)) for k in range(3)]
+    rep = sim.autotune(6)
+    print("autotune report", rep)
+    for k in range(3):
+        phi, psi = sim.state(sim=k)
+        prev = sim.state(sim=k, prev=True)
+        assert np.array_equal(phi, before[k][0]) and np.array_equal(psi, before[k][1])
+        assert np.array_equal(prev[0], before[k][2][0]) and np.array_equal(prev[1], before[k][2][1])
+        assert np.array_equal(sim.aux(sim=k)[:10], before[k][3][:10])
+    assert rep.shape == (3, 4) and all(r[1] in (58, 72, 100) for r in rep)
+    assert rep[0][0] == rep[2][0] and rep[0][1] == rep[2][1]          # same size, same schedule
+    assert all(r[2] > 0 and r[3] > 0 for r in rep[:2])
+    sim.step(5)
+    for k, w in enumerate(ws):
+        ref = cc.Simulation(w.params, w.N, precision="fp32")
+        ref.set_state(w.phi0, w.psi0)
+        ref.step(9)
+        a, b = ref.state()
+        ref.close()
+        phi, psi = sim.state(sim=k)
+        assert max(rel(phi, a), rel(psi, b)) <= 5e-6
+    sim.close()
