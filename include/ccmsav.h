@@ -230,6 +230,16 @@ int ccmsav_profile_read(ccmsav_t* h, int sim, double ms[8], long long* nsteps);
  * [1, 3000]; not for CCMSAV_CLASSICAL handles (CCMSAV_EINVAL).  Synchronises. */
 int ccmsav_autotune(ccmsav_t* h, int steps, double* report);
 
+/* Index checks of a library built with -DCCMSAV_BOUNDS (a separate
+ * libccmsav_bounds.so, for testing): the step kernels check every element
+ * index of their field, spectrum and level accesses against the array's
+ * size; an index outside sets bit 1 (a load, redirected to element 0) or
+ * bit 2 (a store, dropped) of a device flag.  Returns the flags raised by
+ * the kernels of the handle's precisions since the last call (0: none) and
+ * clears them; synchronises.  CCMSAV_EINVAL in a library built without the
+ * checks. */
+int ccmsav_bounds_flag(ccmsav_t* h);
+
 /* Conjugate-gradient settings of a CCMSAV_CLASSICAL handle (all its
  * simulations): stop when ||r||_2 <= rtol ||b||_2 (rtol > 0; default 1e-10
  * for FP64, 1e-6 for FP32) or after max_iter iterations (>= 1; default 200).

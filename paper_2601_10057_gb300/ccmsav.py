@@ -16,6 +16,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libccmsav.so")
+LIB_BOUNDS_PATH = os.path.join(HERE, "libccmsav_bounds.so")   # index-checked test build
 
 CCMSAV_OK = 0
 CCMSAV_EINVAL = -1
@@ -92,6 +93,7 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "ccmsav_mass_noalloc": (i, [vp, i, i, d, _DP, vp]),
         "ccmsav_set_pcg": (i, [vp, d, i]),
         "ccmsav_autotune": (i, [vp, i, _DP]),
+        "ccmsav_bounds_flag": (i, [vp]),
         "ccmsav_pcg_stats": (i, [vp, i, _DP]),
         "ccmsav_solver_create": (i, [C.POINTER(vp), i, d, i, i, vp]),
         "ccmsav_solver_solve": (i, [vp, _DP, vp, vp]),
@@ -237,6 +239,10 @@ def ccmsav_mass_noalloc(psi_ptr: int, N: int, precision: int, L: float, stream: 
     st = load().ccmsav_mass_noalloc(C.c_void_p(psi_ptr), int(N), int(precision), float(L), _ptr(out),
                                     C.c_void_p(stream) if stream else None)
     return st, float(out[0])
+
+
+def ccmsav_bounds_flag(h) -> int:
+    return load().ccmsav_bounds_flag(h)
 
 
 def ccmsav_autotune(h, steps: int, n_sims: int):

@@ -282,6 +282,17 @@ int ccmsav_autotune(ccmsav_t* h, int steps, double* report) {
     return CCMSAV_OK;
 }
 
+int ccmsav_bounds_flag(ccmsav_t* h) {
+    if (!h) return CCMSAV_EINVAL;
+    int acc = 0;
+    for (ccm::SimBase* s : h->sims) {
+        const int r = s->bounds_flag();
+        if (r < 0) return r;
+        acc |= r;
+    }
+    return acc;
+}
+
 int ccmsav_grid_size(ccmsav_t* h, int sim) {
     ccm::SimBase* s = get(h, sim);
     if (!s) return CCMSAV_EINVAL;

@@ -40,6 +40,8 @@ public:
     virtual int autotune(int k, double out[4]) = 0;
     virtual int autotune_apply_cached() = 0;       // take this N's recorded schedule
     virtual int autotune_report(double out[4]) = 0; // {warp path, carveout, best ms, default ms}
+    // index-check flag of a bounds-checked build (-DCCMSAV_BOUNDS), read and cleared
+    virtual int bounds_flag() = 0;
     int N = 0;
 };
 

@@ -580,6 +580,18 @@ public:
         return CCMSAV_OK;
     }
 
+    int bounds_flag() override {
+#ifdef CCMSAV_BOUNDS
+        unsigned v = 0, z = 0;
+        CCM_CUDA(cudaStreamSynchronize(st));
+        CCM_CUDA(cudaMemcpyFromSymbol(&v, g_oob_flag, sizeof(v)));
+        CCM_CUDA(cudaMemcpyToSymbol(g_oob_flag, &z, sizeof(z)));
+        return (int)v;
+#else
+        return CCMSAV_EINVAL;
+#endif
+    }
+
     int pcg_stats(double out[4]) override {
         if (!classical) return CCMSAV_EINVAL;
         CCM_CUDA(cudaStreamSynchronize(st));

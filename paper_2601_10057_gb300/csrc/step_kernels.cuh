@@ -45,6 +45,7 @@
 #pragma once
 #include <type_traits>
 #include "dct_device.cuh"
+#include "bounds.cuh"
 
 namespace ccm {
 
@@ -410,11 +411,11 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
                 if (u < NI && (!ex || ex_on)) {
                     const int lj = ex ? ex_r : ty + TY * u, li = ex ? ex_c : cx;
                     const size_t g = (size_t)reflect(j0 + lj - 2, N) * N + (ex ? gxe : gxc);
-                    ra[b] = phn[g];
-                    rb[b] = pho[g];
+                    ra[b] = phn[CCM_IX(g, NN)];
+                    rb[b] = pho[CCM_IX(g, NN)];
                     if (lj >= 1 && lj <= TYB + 2 && li >= 1 && li <= TX + 2) {
-                        rc[b] = psn[g];
-                        rd[b] = pso[g];
+                        rc[b] = psn[CCM_IX(g, NN)];
+                        rd[b] = pso[CCM_IX(g, NN)];
                     }
                 }
             }
@@ -458,7 +459,8 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
         sincospi_<T>((T)0.5 * ph, &sp, &cp);
         sP[q] = (T)0.5 * (c.gin * ((T)1 + sp) * (ps - c.psin) + c.gout * ((T)1 - sp) * (ps - c.psout));
         const int gi = i0 + li1 - 1, gj = j0 + lj1 - 1;
-        if (lj1 >= 1 && lj1 <= TYB && li1 >= 1 && li1 <= TX && gi < N && gj < N) {
+        if (lj1 >= 1 && lj1 <= TYB && li1 >= 1 && li1 <= TX && gi < N && gj < N &&
+            CCM_OK(4 * NN + (size_t)gj * N + gi, 8 * NN)) {
             const T fin = c.hgin * (ps - c.psin) * (ps - c.psin) + c.bin;
             const T fout = c.hgout * (ps - c.psout) * (ps - c.psout) + c.bout;
             out[4 * NN + (size_t)gj * N + gi] = (T)0.5 * ((T)1.5707963267948966192 * cp) * (fin - fout);
@@ -500,7 +502,7 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
         const T bC = sbar[(lj + 1) * W2 + li + 1];
         const T f0 = c.C2 * lbC - c.C3 * lap2b - c.Mth * lapp - c.betap * bC;
         const T g0 = c.lam * lapd;
-        if (inside) {
+        if (inside && CCM_OK(7 * NN + g, 8 * NN)) {
             out[0 * NN + g] = f0;
             out[1 * NN + g] = Snum;
             out[2 * NN + g] = Hv;
@@ -613,7 +615,7 @@ k_rowdct_T(const T* __restrict__ in, T* __restrict__ out, int N, int RT, int lds
         // pack nr rows
         for (int q = threadIdx.x; q < nr * (M / 2); q += blockDim.x) {
             const int r = q / (M / 2), m = q % (M / 2);
-            pack4(fb + (size_t)r * ldc, M, m, ld4(src + (size_t)(y0 + r0 + r) * N + 4 * m));
+            pack4(fb + (size_t)r * ldc, M, m, ld4(src + CCM_IXW((size_t)(y0 + r0 + r) * N + 4 * m, 4, NN)));
         }
         __syncthreads();
         fft_lines<T, false>(fb, ldc, nr, M, twM);
@@ -631,7 +633,7 @@ k_rowdct_T(const T* __restrict__ in, T* __restrict__ out, int N, int RT, int lds
     T* dst = out + f * NN;
     for (int q = threadIdx.x; q < RT * N; q += blockDim.x) {
         const int r = q % RT, kx = q / RT;
-        dst[(size_t)kx * N + y0 + r] = stage[(size_t)r * lds + kx];
+        if (CCM_OK((size_t)kx * N + y0 + r, NN)) dst[(size_t)kx * N + y0 + r] = stage[(size_t)r * lds + kx];
     }
 }
 
@@ -671,7 +673,7 @@ k_coldct_gram(const T* __restrict__ in, T* __restrict__ spec, double* __restrict
     for (int fg0 = 0; fg0 < NF; fg0 += FG) {
         for (int q = threadIdx.x; q < FG * (M / 2); q += blockDim.x) {
             const int f = q / (M / 2), m = q % (M / 2);
-            pack4(fb + (size_t)f * ldc, M, m, ld4(in + (fg0 + f) * NN + (size_t)kx * N + 4 * m));
+            pack4(fb + (size_t)f * ldc, M, m, ld4(in + CCM_IXW((fg0 + f) * NN + (size_t)kx * N + 4 * m, 4, NF * NN)));
         }
         __syncthreads();
         fft_lines<T, false>(fb, ldc, FG, M, twM);
@@ -696,13 +698,14 @@ k_coldct_gram(const T* __restrict__ in, T* __restrict__ spec, double* __restrict
                     const size_t o = (size_t)kx * N + ky;
 #pragma unroll
                     for (int f = 0; f < NF; ++f)
-                        if (f != 5) spec[f * NN + o] = v[f];
+                        if (f != 5 && CCM_OK(f * NN + o, NF * NN)) spec[f * NN + o] = v[f];
                 }
             }
         } else {
             for (int q = threadIdx.x; q < FG * (M / 2 + 1); q += blockDim.x) {
                 const int f = q / (M / 2 + 1), k = q % (M / 2 + 1);
                 Quad<T> X = post_forward(fb + (size_t)f * ldc, M, k, twP[k], cn0, cn);
+                if (!CCM_OK((fg0 + f) * NN + (size_t)kx * N + (M + k < N ? M + k : N - 1), NF * NN)) continue;
                 T* row = spec + (fg0 + f) * NN + (size_t)kx * N;
                 row[k] = X.xk;
                 if (pair_mode_valid(1, k, M)) row[N - k] = X.xNk;
@@ -720,7 +723,7 @@ k_coldct_gram(const T* __restrict__ in, T* __restrict__ spec, double* __restrict
             const T itau = (T)(1.0 / (sc.Ct + sc.lam * s));
             T v[NF];
 #pragma unroll
-            for (int f = 0; f < NF; ++f) v[f] = spec[f * NN + (size_t)kx * N + ky];
+            for (int f = 0; f < NF; ++f) v[f] = spec[CCM_IX(f * NN + (size_t)kx * N + ky, NF * NN)];
             gram_accumulate(acc, v, isig, itau);
         }
     }
@@ -991,7 +994,7 @@ k_comb_icolT(const T* __restrict__ spec, T* __restrict__ out, int N, int RT, int
                 int ky = kys[u];
                 if (u == 1 && k == 0) { vals[u] = 0; continue; }
                 const double s = evx + ev[ky];
-                const size_t o = (size_t)kx * N + ky;
+                const size_t o = CCM_IX((size_t)kx * N + ky, NN);
                 if (f == 0) {
                     const T isig = (T)(1.0 / (sc.C1 + sc.C2 * s + sc.C3 * s * s));
                     vals[u] = (spec[0 * NN + o] - aS * spec[1 * NN + o] - aH * spec[2 * NN + o]
@@ -1025,7 +1028,8 @@ k_comb_icolT(const T* __restrict__ spec, T* __restrict__ out, int N, int RT, int
     for (int q = threadIdx.x; q < 2 * RT * N; q += blockDim.x) {
         const int r = q % RT, rest = q / RT;
         const int y = rest % N, f = rest / N;
-        out[f * NN + (size_t)y * N + kx0 + r] = stage[(size_t)(f * RT + r) * lds + y];
+        if (CCM_OK(f * NN + (size_t)y * N + kx0 + r, 2 * NN))
+            out[f * NN + (size_t)y * N + kx0 + r] = stage[(size_t)(f * RT + r) * lds + y];
     }
 }
 
@@ -1053,7 +1057,7 @@ k_irow(const T* __restrict__ in, T* __restrict__ phi_new, T* __restrict__ psi_ne
         for (int q = threadIdx.x; q < nl * (M / 2 + 1); q += blockDim.x) {
             const int l = l0 + q / (M / 2 + 1), k = q % (M / 2 + 1);
             const int r = l >> 1, f = l & 1;
-            const T* row = in + f * NN + (size_t)(y0 + r) * N;
+            const T* row = in + CCM_IXW(f * NN + (size_t)(y0 + r) * N, N, 2 * NN);
             Quad<T> X{row[k], k > 0 ? row[N - k] : (T)0, row[M - k], row[M + k]};
             cplx<T> zk, zMk;
             pre_inverse(X, k, twP[k], inv0, inv, zk, zMk);
@@ -1066,7 +1070,7 @@ k_irow(const T* __restrict__ in, T* __restrict__ phi_new, T* __restrict__ psi_ne
         for (int q = threadIdx.x; q < nl * (M / 2); q += blockDim.x) {
             const int l = l0 + q / (M / 2), m = q % (M / 2);
             const int r = l >> 1, f = l & 1;
-            const size_t off = (size_t)(y0 + r) * N + 4 * m;
+            const size_t off = CCM_IXW((size_t)(y0 + r) * N + 4 * m, 4, NN);
             vec4<T> v = unpack4(fb + (size_t)(l - l0) * ldc, M, m);
             const vec4<T> a = ld4((f == 0 ? phn : psn) + off), b = ld4((f == 0 ? pho : pso) + off);
             const T an = (f == 1) ? anc : (T)0;

@@ -75,7 +75,7 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
     cplx<float>* buf = bufs + (size_t)slot * Gm::BUF;
     {
         cplx<float> v[E];
-        wf::pack_fwd_global<M>(in + f * NN + (size_t)(y0 + slot) * N, v, n2);
+        wf::pack_fwd_global<M>(in + CCM_IXW(f * NN + (size_t)(y0 + slot) * N, N, NF * NN), v, n2);
         wf::fourstep<float, M, false, true>(v, buf, tw2, n2);
     }
     // DCT post-process in place, one pair at a time: pair k reads the complex
@@ -120,6 +120,8 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
         const float2* sp = stage + (size_t)(4 * r4) * BC + j;
         const float2 v0 = sp[0], v1 = sp[BC], v2 = sp[2 * BC], v3 = sp[3 * BC];
         const int mb = j == 0 ? M : N - j;
+        if (!CCM_OKW(f * NN + y0 + (size_t)j * N + 4 * r4, 4, NF * NN) ||
+            !CCM_OKW(f * NN + y0 + (size_t)mb * N + 4 * r4, 4, NF * NN)) continue;
         *reinterpret_cast<float4*>(dst + (size_t)j * N + 4 * r4) = make_float4(v0.x, v1.x, v2.x, v3.x);
         *reinterpret_cast<float4*>(dst + (size_t)mb * N + 4 * r4) = make_float4(v0.y, v1.y, v2.y, v3.y);
     }
@@ -143,7 +145,7 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
     const int kc = slot / NF, f = slot % NF;
     {
         cplx<float> v[E];
-        wf::pack_fwd_global<M>(in + f * NN + (size_t)(kx0 + kc) * N, v, n2);
+        wf::pack_fwd_global<M>(in + CCM_IXW(f * NN + (size_t)(kx0 + kc) * N, N, NF * NN), v, n2);
         wf::fourstep<float, M, false, true>(v, bufs + (size_t)slot * Gm::BUF, tw2, n2);
     }
     __syncthreads();
@@ -211,6 +213,8 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
 #pragma unroll
         for (int g = 0; g < NF; ++g) {
             if (g == 5) continue;
+            if (!CCM_OKW((size_t)kx * SpecRow<M>::KS + 4 * k + (size_t)(g < 5 ? g : g - 1) * SpecRow<M>::FO, 4,
+                         (size_t)N * SpecRow<M>::KS)) continue;
             float4 o = make_float4(X[g].xk, k == 0 ? 0.f : X[g].xNk, X[g].xMk, X[g].xMpk);
             if (k == 0) o.w = o.z;
             *reinterpret_cast<float4*>(dst + (size_t)(g < 5 ? g : g - 1) * SpecRow<M>::FO) = o;
@@ -250,7 +254,8 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
         const int kx = kx0 + r;
         const float evx = evf[kx];
         const float4 e4 = evp[k];
-        const float* src = spec + (size_t)kx * SpecRow<M>::KS + 4 * k;
+        const float* src = spec + CCM_IXW((size_t)kx * SpecRow<M>::KS + 4 * k, 6 * SpecRow<M>::FO + 4,
+                                          (size_t)N * SpecRow<M>::KS);
         constexpr size_t FS = SpecRow<M>::FO;
         const float4 f0 = __ldg(reinterpret_cast<const float4*>(src));
         const float4 f1 = __ldg(reinterpret_cast<const float4*>(src + FS));
@@ -321,6 +326,7 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
         const float2* sp = stage + (size_t)(8 * r4 + fld) * BC;
         const float2 a0 = sp[m], a1 = sp[2 * BC + m], a2 = sp[4 * BC + m], a3 = sp[6 * BC + m];
         const float2 b0 = sp[M - 1 - m], b1 = sp[2 * BC + M - 1 - m], b2 = sp[4 * BC + M - 1 - m], b3 = sp[6 * BC + M - 1 - m];
+        if (!CCM_OKW(fld * NN + (size_t)(4 * m + 3) * N + kx0 + 4 * r4, 4, 2 * NN)) continue;
         float* d = out + fld * NN + (size_t)(4 * m) * N + kx0 + 4 * r4;
         *reinterpret_cast<float4*>(d) = make_float4(a0.x, a1.x, a2.x, a3.x);
         *reinterpret_cast<float4*>(d + N) = make_float4(b0.y, b1.y, b2.y, b3.y);
@@ -374,7 +380,7 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
         const int l = q / PAIRS, k = q % PAIRS;
         const int gl = l0 + l;
         if (gl >= 2 * N) continue;
-        const float* row = in + (gl & 1) * NN + (size_t)(gl >> 1) * N;
+        const float* row = in + CCM_IXW((gl & 1) * NN + (size_t)(gl >> 1) * N, N, 2 * NN);
         const Quad<float> X{__ldg(row + k), k > 0 ? __ldg(row + N - k) : 0.f, __ldg(row + M - k), __ldg(row + M + k)};
         cplx<float> zk, zMk;
         wf::pre_pair_lean(X, wf::load_pair_tw<true>(twI, k), zk, zMk);
@@ -434,6 +440,7 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
         const int m = n2 + G * i;
         const cplx<float> a = buf[m], b = buf[M - 1 - m];
         if (!valid) continue;
+        if (!CCM_OKW(roff + 4 * m, 4, NN)) continue;
         const float4 p = __ldg(un + m), q = __ldg(uo + m);
         float4 o;
         if (psi_line) {

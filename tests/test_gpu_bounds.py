@@ -1,0 +1,61 @@
+"""The step with every field, spectrum and level access index-checked: the
+library built with -DCCMSAV_BOUNDS (libccmsav_bounds.so) runs the small and
+ragged grids (N = 8 ... 256, FP64 and FP32, block- and warp-FFT paths, start
+and BDF2 steps, graph-launched steps, the classical and BDF1 modes) in a
+child process; no access may leave its array (ccmsav_bounds_flag() = 0) and
+the results stay those of the oracle.  compute-sanitizer is not available
+for this purpose, so the checks are compiled into the kernels."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+from paper_2601_10057_gb300 import build as B
+
+pytestmark = pytest.mark.gpu
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+CHILD = r"""
+import json, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_2601_10057_gb300 import ccmsav as cc
+from paper_2601_10057_gb300 import inputs as I
+from oracle import ccmsav_oracle as O
+cc.load(cc.LIB_BOUNDS_PATH)
+out = []
+cases = [(N, prec, mode) for N in (8, 16, 32, 64, 128, 256) for prec in ("fp64", "fp32")
+         for mode in ("cc", "bdf1", "classical")]
+for N, prec, mode in cases:
+    w = I.workload("one_vesicle", N=N, dt=1e-5)
+    sim = cc.Simulation(w.params, N, precision=prec, bdf1_always=(mode == "bdf1"), classical=(mode == "classical"))
+    if mode == "classical":
+        sim.set_pcg(1e-13 if prec == "fp64" else 1e-6, 400)
+    sim.set_state(w.phi0, w.psi0)
+    sim.step(1)
+    sim.step(7)          # graph-launched BDF2 steps (direct for the classical mode)
+    phi, psi = sim.state()
+    flag = cc.ccmsav_bounds_flag(sim.h)
+    sim.close()
+    m = O.Model.from_params(N, w.params)
+    s = O.run(O.initial_state(w.phi0, w.psi0, m), m, 8, bdf1=(True if mode == "bdf1" else None),
+              classical=(mode == "classical"))
+    e = max(float(np.abs(phi - s.phi).max() / np.abs(s.phi).max()), float(np.abs(psi - s.psi).max() / np.abs(s.psi).max()))
+    out.append({"N": N, "precision": prec, "mode": mode, "flag": flag, "err": e})
+print(json.dumps(out))
+"""
+
+
+def test_bounds_checked_build_small_grids():
+    B.build(bounds=True)
+    r = subprocess.run([sys.executable, "-c", CHILD, ROOT], capture_output=True, text=True, timeout=900)
+    assert r.returncode == 0, r.stderr[-3000:]
+    res = json.loads(r.stdout.strip().splitlines()[-1])
+    for c in res:
+        print(c)
+    assert all(c["flag"] == 0 for c in res), [c for c in res if c["flag"]]
+    tol = {"fp64": 1e-11, "fp32": 2e-5}
+    bad = [c for c in res if c["err"] > tol[c["precision"]]]
+    assert not bad, bad
