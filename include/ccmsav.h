@@ -217,7 +217,8 @@ int ccmsav_profile_read(ccmsav_t* h, int sim, double ms[8], long long* nsteps);
 /* Autotuner of the line-transform schedule.  For every distinct grid size
  * of the handle it times `steps` BDF2 steps (rounded up to a multiple of
  * three, after three warm-up steps) of each candidate schedule from the
- * simulation's current state, keeps the fastest and restores the state (the
+ * simulation's current state, keeps the fastest (the default schedule unless
+ * another is at least 2 % faster) and restores the state (the
  * fields and scalars are unchanged afterwards).  Candidates (FP32): the
  * warp-level four-step FFT kernels with a shared-memory carveout of 72, 58
  * or 100 percent for the three 8-line transform kernels, and the CTA-level

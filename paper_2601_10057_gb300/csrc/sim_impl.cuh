@@ -486,6 +486,7 @@ public:
         return have_warp ? apply_carveout(c.carveout) : CCMSAV_OK;
     }
     bool have_warp = false;
+    static constexpr double kTuneMargin = 0.02;
 
     // Times `k` steps (a multiple of three, after three warm-up steps that
     // capture the graphs) of each candidate schedule from the same saved
@@ -541,6 +542,9 @@ public:
         }
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
+        // keep the default unless another schedule is clearly faster (the
+        // timing of a few steps varies by about a percent)
+        if (bi != 0 && best > (1.0 - kTuneMargin) * dflt) { bi = 0; best = dflt; }
         TuneChoice ch = cand[bi];
         ch.ms = best; ch.ms_default = dflt;
         if (!r) r = apply_choice(ch);
