@@ -214,11 +214,13 @@ long long ccmsav_launch_count(ccmsav_t* h);
 int ccmsav_profile(ccmsav_t* h, int enable);
 int ccmsav_profile_read(ccmsav_t* h, int sim, double ms[8], long long* nsteps);
 
-/* Autotuner of the line-transform schedule.  For every distinct grid size
- * of the handle it times `steps` BDF2 steps (rounded up to a multiple of
- * three, after three warm-up steps) of each candidate schedule from the
- * simulation's current state, keeps the fastest (the default schedule unless
- * another is at least 2 % faster) and restores the state (the
+/* Autotuner of the line-transform schedule.  It times `steps` BDF2 steps
+ * (rounded up to a multiple of three, after three warm-up steps) of each
+ * candidate schedule from the current state -- for a handle of one
+ * simulation that simulation alone, for several simulations the handle's
+ * batched step with the candidate applied to all of them (what the handle
+ * runs) -- keeps the fastest (the default schedule unless another is at
+ * least 2 % faster) and restores the state (the
  * fields and scalars are unchanged afterwards).  Candidates (FP32): the
  * warp-level four-step FFT kernels with a shared-memory carveout of 72, 58
  * or 100 percent for the three 8-line transform kernels, and the CTA-level

@@ -259,26 +259,63 @@ int ccmsav_autotune(ccmsav_t* h, int steps, double* report) {
     if (h->flags & CCMSAV_CLASSICAL) return CCMSAV_EINVAL;
     int r = ccmsav_sync(h);
     if (r) return r;
-    std::vector<int> done_N;
-    std::vector<double> row(4);
-    for (size_t k = 0; k < h->sims.size(); ++k) {
-        ccm::SimBase* s = h->sims[k];
+    for (ccm::SimBase* s : h->sims)
         if (!s->has_state()) return CCMSAV_ESTATE;
-        bool seen = false;
-        for (int n : done_N) seen = seen || n == s->N;
-        if (!seen) {
-            if ((r = s->autotune(steps, row.data()))) return r;
-            done_N.push_back(s->N);
-            // the other simulations of this size take the same schedule
-            for (size_t j = k + 1; j < h->sims.size(); ++j)
-                if (h->sims[j]->N == s->N && (r = h->sims[j]->autotune_apply_cached())) return r;
-        }
-        if (report) {
-            const int rr = s->autotune_report(report + 4 * k);
-            if (rr) return rr;
-        }
+    if (!batched(h)) {
+        double row[4];
+        if ((r = h->sims[0]->autotune(steps, row))) return r;
+        if (report) for (int i = 0; i < 4; ++i) report[i] = row[i];
+        return CCMSAV_OK;
     }
-    for (int i = 0; i < 3; ++i) if (h->bexec[i]) { cudaGraphExecDestroy(h->bexec[i]); h->bexec[i] = nullptr; }
+    // Several simulations: every candidate schedule is applied to all of
+    // them and the batched step of the whole handle is timed, since that is
+    // what the handle runs (a schedule that is faster for one simulation
+    // alone can be slower when the simulations share the GPU).
+    const int k = (steps < 3 ? 3 : steps + 2) / 3 * 3;
+    bool any_warp = false;
+    for (ccm::SimBase* s : h->sims) {
+        if ((r = s->tune_save())) return r;
+        any_warp = any_warp || s->tune_has_warp();
+    }
+    const std::vector<ccm::TuneChoice> cand = ccm::tune_candidates(any_warp);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = CCMSAV_ECUDA;
+    double best = 1e300, dflt = 0.0;
+    size_t bi = 0;
+    auto drop_batch = [&]() {
+        for (int i = 0; i < 3; ++i) if (h->bexec[i]) { cudaGraphExecDestroy(h->bexec[i]); h->bexec[i] = nullptr; }
+    };
+    for (size_t i = 0; i < cand.size() && !r; ++i) {
+        for (ccm::SimBase* s : h->sims) {
+            if ((r = s->tune_apply(cand[i].warp, cand[i].carveout)) || (r = s->tune_load())) break;
+        }
+        if (r) break;
+        drop_batch();
+        if ((r = ccmsav_step(h, 3))) break;
+        if (cudaEventRecord(e0, h->stream) != cudaSuccess) { r = CCMSAV_ECUDA; break; }
+        if ((r = ccmsav_step(h, k))) break;
+        if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { r = CCMSAV_ECUDA; break; }
+        if ((r = ccmsav_sync(h))) break;
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double per = ms / k;
+        if (i == 0) dflt = per;
+        if (per < best) { best = per; bi = i; }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (bi != 0 && best > 0.98 * dflt) { bi = 0; best = dflt; }
+    for (ccm::SimBase* s : h->sims) {
+        int e = r ? CCMSAV_OK : s->tune_record(cand[bi].warp, cand[bi].carveout, best, dflt);
+        const int e2 = s->tune_load();
+        s->tune_free();
+        if (!r) r = e ? e : e2;
+    }
+    drop_batch();
+    if (r) return r;
+    if (report)
+        for (size_t q = 0; q < h->sims.size(); ++q)
+            if ((r = h->sims[q]->autotune_report(report + 4 * q))) return r;
     return CCMSAV_OK;
 }
 

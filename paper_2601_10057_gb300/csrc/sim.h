@@ -2,9 +2,25 @@
 // per-precision implementations of one simulation.
 #pragma once
 #include <cuda_runtime.h>
+#include <vector>
 #include "../../include/ccmsav.h"
 
 namespace ccm {
+
+// Schedule chosen by the autotuner for one (grid size, precision): the FFT
+// path of the line transforms (warp-level four-step FFT or CTA-level Stockham
+// FFT) and the shared-memory carveout of the three 8-line warp-FFT kernels.
+// Process-wide, so handles created later with the same N start from it.
+struct TuneChoice { int warp = 1; int carveout = 72; double ms = 0.0, ms_default = 0.0; };
+// Candidate schedules, the default first: warp-FFT kernels at carveouts of
+// 72, 58 and 100 percent (where the warp path exists), then the block FFT.
+inline std::vector<TuneChoice> tune_candidates(bool have_warp) {
+    std::vector<TuneChoice> c;
+    if (have_warp)
+        for (int cv : {72, 58, 100}) { TuneChoice t; t.warp = 1; t.carveout = cv; c.push_back(t); }
+    TuneChoice b; b.warp = 0; b.carveout = 72; c.push_back(b);
+    return c;
+}
 
 class SimBase {
 public:
@@ -38,6 +54,12 @@ public:
     virtual int pcg_stats(double out[4]) = 0;
     // autotuner of the line-transform schedule (see ccmsav_autotune)
     virtual int autotune(int k, double out[4]) = 0;
+    virtual int tune_save() = 0;                   // keep the state while schedules are timed
+    virtual int tune_load() = 0;                   // back to the kept state
+    virtual void tune_free() = 0;
+    virtual bool tune_has_warp() const = 0;
+    virtual int tune_apply(int warp, int carveout) = 0;
+    virtual int tune_record(int warp, int carveout, double ms, double ms_default) = 0;
     virtual int autotune_apply_cached() = 0;       // take this N's recorded schedule
     virtual int autotune_report(double out[4]) = 0; // {warp path, carveout, best ms, default ms}
     // index-check flag of a bounds-checked build (-DCCMSAV_BOUNDS), read and cleared

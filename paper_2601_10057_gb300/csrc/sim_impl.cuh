@@ -30,11 +30,6 @@
 
 namespace ccm {
 
-// Schedule chosen by the autotuner for one (grid size, precision): the FFT
-// path of the line transforms (warp-level four-step FFT or CTA-level Stockham
-// FFT) and the shared-memory carveout of the three 8-line warp-FFT kernels.
-// Process-wide, so handles created later with the same N start from it.
-struct TuneChoice { int warp = 1; int carveout = 72; double ms = 0.0, ms_default = 0.0; };
 template <typename T> struct TuneTable {
     static std::mutex& mu() { static std::mutex m; return m; }
     static std::map<int, TuneChoice>& table() { static std::map<int, TuneChoice> t; return t; }
@@ -127,6 +122,7 @@ public:
 
     ~SimImpl() override {
         if (st) cudaStreamSynchronize(st); else cudaDeviceSynchronize();
+        cudaFree(tune_snap);
         for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
         for (int i = 0; i < 3; ++i) if (gexec[i]) cudaGraphExecDestroy(gexec[i]);
         for (int i = 0; i < 3; ++i) if (gexec1[i]) cudaGraphExecDestroy(gexec1[i]);
@@ -488,46 +484,77 @@ public:
     bool have_warp = false;
     static constexpr double kTuneMargin = 0.02;
 
-    // Times `k` steps (a multiple of three, after three warm-up steps that
-    // capture the graphs) of each candidate schedule from the same saved
-    // state, keeps the fastest, restores the state and records the choice for
-    // this (N, precision).  out = {warp, carveout, best ms/step, ms/step of
-    // the default schedule}.
-    int autotune(int k, double out[4]) override {
+    // State saved while the autotuner times candidate schedules: the four
+    // levels, the scalars and the host counters.
+    T* tune_snap = nullptr;
+    DevScalars tune_sc{};
+    int tune_cur = 0, tune_prev = 1, tune_spare = 2;
+    long long tune_steps = 0;
+
+    int tune_save() override {
         if (!have_state || poisoned || classical) return CCMSAV_ESTATE;
+        if (!tune_snap && cudaMalloc(&tune_snap, 4 * NN * sizeof(T)) != cudaSuccess) return CCMSAV_ENOMEM;
+        tune_cur = cur; tune_prev = prev; tune_spare = spare; tune_steps = steps_taken;
+        T* lv[4] = {phi[cur], psi[cur], phi[prev], psi[prev]};
+        for (int q = 0; q < 4; ++q)
+            CCM_CUDA(cudaMemcpyAsync(tune_snap + q * NN, lv[q], NN * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        CCM_CUDA(cudaMemcpyAsync(&tune_sc, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st));
+        CCM_CUDA(cudaStreamSynchronize(st));
+        return CCMSAV_OK;
+    }
+
+    int tune_load() override {
+        if (!tune_snap) return CCMSAV_ESTATE;
+        cur = tune_cur; prev = tune_prev; spare = tune_spare; steps_taken = tune_steps;
+        T* dst[4] = {phi[cur], psi[cur], phi[prev], psi[prev]};
+        for (int q = 0; q < 4; ++q)
+            CCM_CUDA(cudaMemcpyAsync(dst[q], tune_snap + q * NN, NN * sizeof(T), cudaMemcpyDeviceToDevice, st));
+        CCM_CUDA(cudaMemcpyAsync(sc, &tune_sc, sizeof(DevScalars), cudaMemcpyHostToDevice, st));
+        CCM_CUDA(cudaStreamSynchronize(st));
+        poisoned = false;
+        return CCMSAV_OK;
+    }
+
+    void tune_free() override {
+        cudaFree(tune_snap);
+        tune_snap = nullptr;
+    }
+
+    bool tune_has_warp() const override { return have_warp; }
+
+    int tune_apply(int warp, int carveout) override {
+        TuneChoice c;
+        c.warp = warp; c.carveout = carveout;
+        return apply_choice(c);
+    }
+
+    int tune_record(int warp, int carveout, double ms, double ms_default) override {
+        TuneChoice c;
+        c.warp = warp; c.carveout = carveout; c.ms = ms; c.ms_default = ms_default;
+        int r = apply_choice(c);
+        std::lock_guard<std::mutex> lk(TuneTable<T>::mu());
+        TuneTable<T>::table()[N] = c;
+        return r;
+    }
+
+    // Times `k` steps (a multiple of three, after three warm-up steps that
+    // capture the graphs) of each candidate schedule of this simulation
+    // alone, from the same saved state; keeps the fastest (the default unless
+    // another is kTuneMargin faster), restores the state and records the
+    // choice for this (N, precision).  out = {warp, carveout, best ms/step,
+    // ms/step of the default schedule}.
+    int autotune(int k, double out[4]) override {
         if (k < 3) k = 3;
         k = (k + 2) / 3 * 3;
-        std::vector<TuneChoice> cand;
-        if (have_warp)
-            for (int c : {72, 58, 100}) { TuneChoice t; t.warp = 1; t.carveout = c; cand.push_back(t); }
-        { TuneChoice t; t.warp = 0; t.carveout = 72; cand.push_back(t); }
-        // save the state: four levels, the scalars, the host counters
-        T* snap = nullptr;
-        if (cudaMalloc(&snap, 4 * NN * sizeof(T)) != cudaSuccess) return CCMSAV_ENOMEM;
-        DevScalars sc0;
-        const int c0 = cur, p0 = prev, s0 = spare;
-        const long long st0 = steps_taken;
-        T* lv[4] = {phi[cur], psi[cur], phi[prev], psi[prev]};
-        int r = CCMSAV_OK;
-        for (int q = 0; q < 4 && !r; ++q)
-            if (cudaMemcpyAsync(snap + q * NN, lv[q], NN * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess) r = CCMSAV_ECUDA;
-        if (!r && cudaMemcpyAsync(&sc0, sc, sizeof(DevScalars), cudaMemcpyDeviceToHost, st) != cudaSuccess) r = CCMSAV_ECUDA;
-        if (!r && cudaStreamSynchronize(st) != cudaSuccess) r = CCMSAV_ECUDA;
-        auto restore = [&]() -> int {
-            cur = c0; prev = p0; spare = s0; steps_taken = st0;
-            T* dst[4] = {phi[cur], psi[cur], phi[prev], psi[prev]};
-            for (int q = 0; q < 4; ++q)
-                if (cudaMemcpyAsync(dst[q], snap + q * NN, NN * sizeof(T), cudaMemcpyDeviceToDevice, st) != cudaSuccess)
-                    return CCMSAV_ECUDA;
-            if (cudaMemcpyAsync(sc, &sc0, sizeof(DevScalars), cudaMemcpyHostToDevice, st) != cudaSuccess) return CCMSAV_ECUDA;
-            return cudaStreamSynchronize(st) == cudaSuccess ? CCMSAV_OK : CCMSAV_ECUDA;
-        };
+        int r = tune_save();
+        if (r) return r;
+        const std::vector<TuneChoice> cand = tune_candidates(have_warp);
         cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (!r && (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)) r = CCMSAV_ECUDA;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = CCMSAV_ECUDA;
         double best = 1e300, dflt = 0.0;
         size_t bi = 0;
         for (size_t i = 0; i < cand.size() && !r; ++i) {
-            if ((r = apply_choice(cand[i])) || (r = restore())) break;
+            if ((r = tune_apply(cand[i].warp, cand[i].carveout)) || (r = tune_load())) break;
             if (steps_taken == 0) { if ((r = queue_steps(1))) break; }   // start step outside the timing
             if ((r = queue_steps(3))) break;
             if (cudaEventRecord(e0, st) != cudaSuccess) { r = CCMSAV_ECUDA; break; }
@@ -542,22 +569,13 @@ public:
         }
         if (e0) cudaEventDestroy(e0);
         if (e1) cudaEventDestroy(e1);
-        // keep the default unless another schedule is clearly faster (the
-        // timing of a few steps varies by about a percent)
         if (bi != 0 && best > (1.0 - kTuneMargin) * dflt) { bi = 0; best = dflt; }
-        TuneChoice ch = cand[bi];
-        ch.ms = best; ch.ms_default = dflt;
-        if (!r) r = apply_choice(ch);
-        const int r2 = restore();
-        cudaFree(snap);
-        poisoned = false;
+        if (!r) r = tune_record(cand[bi].warp, cand[bi].carveout, best, dflt);
+        const int r2 = tune_load();
+        tune_free();
         if (r) return r;
         if (r2) return r2;
-        {
-            std::lock_guard<std::mutex> lk(TuneTable<T>::mu());
-            TuneTable<T>::table()[N] = ch;
-        }
-        out[0] = ch.warp && have_warp ? 1.0 : 0.0; out[1] = ch.carveout; out[2] = ch.ms; out[3] = ch.ms_default;
+        out[0] = cand[bi].warp && have_warp ? 1.0 : 0.0; out[1] = cand[bi].carveout; out[2] = best; out[3] = dflt;
         return CCMSAV_OK;
     }
 

@@ -544,3 +544,19 @@ def test_autotune_keeps_state_and_records_schedule():
         phi, psi = sim.state(sim=k)
         assert max(rel(phi, a), rel(psi, b)) <= 5e-6
     sim.close()
+
+
+def test_autotune_single_simulation():
+    """One simulation: its candidate schedules timed alone; state kept."""
+    w = I.workload("ellipse_shrink", N=256)
+    sim = cc.Simulation(w.params, w.N, precision="fp32")
+    sim.set_state(w.phi0, w.psi0)
+    sim.step(2)
+    phi0, psi0 = sim.state()
+    rep = sim.autotune(6)
+    phi1, psi1 = sim.state()
+    assert np.array_equal(phi0, phi1) and np.array_equal(psi0, psi1)
+    assert rep.shape == (1, 4) and rep[0][1] in (58, 72, 100) and rep[0][2] > 0 and rep[0][3] > 0
+    sim.step(3)
+    sim.sync()
+    sim.close()
