@@ -225,8 +225,8 @@ int ccmsav_profile_read(ccmsav_t* h, int sim, double ms[8], long long* nsteps);
  * warp-level four-step FFT kernels with a shared-memory carveout of 72, 58
  * or 100 percent for the three 8-line transform kernels, and the CTA-level
  * Stockham FFT kernels; FP64 has only the latter.  The choice is recorded
- * for (N, precision) in a process-wide table: simulations of that size in
- * this handle take it at once, handles created later start from it.
+ * for each (N, precision) of the handle in a process-wide table, from which
+ * handles created later start.
  * report (may be NULL) receives 4 doubles per simulation: warp path (1/0),
  * carveout, best ms/step, ms/step of the default schedule (0 when not timed).
  * Needs set_state for every simulation (CCMSAV_ESTATE otherwise); steps in
