@@ -50,9 +50,14 @@ PHASES = {
     "K5 inverse row DCT": (("k_irow",), 4),
 }
 STEP_PASSES_MIN_SCHEDULE = sum(p for _, p in PHASES.values())   # 40
-# Files whose code sets the step kernels' DRAM traffic (launch geometry included)
-KERNEL_SOURCES = ("dct_device.cuh", "diag_kernels.cuh", "sim.h", "sim_f32.cu", "sim_f64.cu",
-                  "sim_impl.cuh", "step_kernels.cuh", "warp_fft.cuh", "warp_kernels.cuh")
+# FP64 step at N = 2048: FP64 operations per grid point and step (2 DFMA + DADD
+# + DMUL thread instructions of the six step kernels, one ncu capture) and the
+# nominal FP64 peak, 152 SMs x 2 FP64 FMA/clock x 2 x 2.07 GHz
+FP64_FLOP_PER_POINT_N2048 = 1042.0
+FP64_PEAK_TFLOPS = 1.25
+# Files holding the step kernels' device code (the DRAM traffic of a
+# committed ncu capture stays valid while these are unchanged)
+KERNEL_SOURCES = ("bounds.cuh", "dct_device.cuh", "step_kernels.cuh", "warp_fft.cuh", "warp_kernels.cuh")
 
 
 def parse():
@@ -560,6 +565,13 @@ def run_ours(args, world, rank, local):
         s64.close()
         fp64 = {"value": NN * k64 / t64, "ms_per_step": 1e3 * t64 / k64, "steps": k64,
                 "speedup_fp32_over_fp64": (NN * args.steps / secs) / (NN * k64 / t64)}
+        if w.N == 2048:
+            ach = FP64_FLOP_PER_POINT_N2048 * NN / t64 / 1e12
+            fp64["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": round(ach, 3),
+                                "peak": FP64_PEAK_TFLOPS, "peak_kind": "nominal FP64 (152 SMs x 2 DFMA/clk x 2 x 2.07 GHz)",
+                                "frac": round(ach / FP64_PEAK_TFLOPS, 3),
+                                "flop_per_point": FP64_FLOP_PER_POINT_N2048,
+                                "hbm_frac": round(2289e6 / t64 / 1e9 / measured_peaks()[0], 4)}
     # ---- accuracy of the timed precision against the FP64 GPU path (1000 steps: the precision target)
     acc = None
     if args.precision == "fp32" and not args.no_fp64 and rank == 0 and args.accuracy_steps > 0:

@@ -108,6 +108,53 @@ k_dnorm(const T* __restrict__ phn, const T* __restrict__ pho, const T* __restric
     block_sum_store<1, double>(v, part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x), sred);
 }
 
+// The five sums set_state needs for the initial SAVs and the arc length
+// (columns 0-4 of k_diag; the other columns are written as 0) for FP32
+// fields, in the FP32 arithmetic of the step's own stencil (sin/cos by the
+// same polynomials) with double-float accumulation per thread.  k_diag
+// evaluates every cell in FP64, whose issue rate on GB300 makes it a
+// millisecond at N = 2048; this pass costs about as much as reading the two
+// fields.
+struct InitCoefF { float inv_h, eps, inv_eps, beta, gin, gout, psin, psout, bin, bout; };
+
+static __global__ void __launch_bounds__(256)
+k_init_sums_f32(const float* __restrict__ a, const float* __restrict__ psi, double* __restrict__ part, int N,
+                InitCoefF c) {
+    __shared__ double sred[8 * NDIAG];
+    const int i = blockIdx.x * 32 + (threadIdx.x & 31);
+    float hi[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, lo[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+    auto ld = [&](int ii, int jj) {
+        ii = ii < 0 ? 0 : (ii >= N ? N - 1 : ii);
+        jj = jj < 0 ? 0 : (jj >= N ? N - 1 : jj);
+        return a[(size_t)jj * N + ii];
+    };
+    for (int rr = 0; rr < kDiagRows; ++rr) {
+        const int j = blockIdx.y * 8 * kDiagRows + 8 * rr + (threadIdx.x >> 5);
+        if (i < N && j < N) {
+            const float aC = ld(i, j), aE = ld(i + 1, j), aW = ld(i - 1, j), aN = ld(i, j + 1), aS = ld(i, j - 1);
+            const float gE = (aE - aC) * c.inv_h, gW = (aC - aW) * c.inv_h, gN = (aN - aC) * c.inv_h, gS = (aC - aS) * c.inv_h;
+            const float gbar = 0.5f * (gE * gE + gW * gW) + 0.5f * (gN * gN + gS * gS);
+            const float a2 = aC * aC, vv = a2 - 1.0f - c.beta, a3 = aC * (a2 - 1.0f);
+            const float ps = psi[(size_t)j * N + i];
+            float sp, cp;
+            sincospi_<float>(0.5f * aC, &sp, &cp);
+            const float fin = 0.5f * c.gin * (ps - c.psin) * (ps - c.psin) + c.bin;
+            const float fout = 0.5f * c.gout * (ps - c.psout) * (ps - c.psout) + c.bout;
+            float face = 0.f;
+            if (i + 1 < N) face += gE * gE;
+            if (j + 1 < N) face += gN * gN;
+            const float v[5] = {vv * vv * 0.25f * c.inv_eps, 6.0f * a2 * gbar + a3 * a3 * c.inv_eps * c.inv_eps,
+                                (1.0f + sp) * fin + (1.0f - sp) * fout, 0.25f * (a2 - 1.0f) * (a2 - 1.0f), face};
+#pragma unroll
+            for (int q = 0; q < 5; ++q) df_add(hi[q], lo[q], v[q]);
+        }
+    }
+    double v[NDIAG];
+#pragma unroll
+    for (int q = 0; q < NDIAG; ++q) v[q] = q < 5 ? (double)hi[q] + (double)lo[q] : 0.0;
+    block_sum_store<NDIAG, double>(v, part + (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * NDIAG, sred);
+}
+
 // lamsum += scale * sum(part[0..nb)) in a fixed order (one block).
 static __global__ void __launch_bounds__(256)
 k_add_lamsum(const double* __restrict__ part, int nb, double scale, DevScalars* sc) {

@@ -859,7 +859,23 @@ public:
 
     int init_scalars_from_fields(double psi_sum_fp64) {
         double s[NDIAG];
-        int r = diag_sums(phi[cur], phi[cur], psi[cur], s);
+        int r = CCMSAV_OK;
+        if constexpr (std::is_same<T, float>::value) {
+            // FP32 fields: the five sums in the step's FP32 arithmetic
+            const double hh = h();
+            InitCoefF ic{(float)(1.0 / hh), (float)p.eps, (float)(1.0 / p.eps), (float)p.beta, (float)p.gamma_in,
+                         (float)p.gamma_out, (float)p.psi_in, (float)p.psi_out, (float)p.beta_in, (float)p.beta_out};
+            k_init_sums_f32<<<g_dg, 256, 0, st>>>(phi[cur], psi[cur], partd, N, ic);
+            ++nlaunch;
+            CCM_CUDA(cudaGetLastError());
+            CCM_CUDA(cudaMemcpyAsync(h_part, partd, (size_t)nbd * NDIAG * sizeof(double), cudaMemcpyDeviceToHost, st));
+            CCM_CUDA(cudaStreamSynchronize(st));
+            for (int q = 0; q < NDIAG; ++q) s[q] = 0.0;
+            for (int bk = 0; bk < nbd; ++bk)
+                for (int q = 0; q < 5; ++q) s[q] += h_part[(size_t)bk * NDIAG + q];
+        } else {
+            r = diag_sums(phi[cur], phi[cur], psi[cur], s);
+        }
         if (r) return r;
         const double h2 = h() * h();
         std::memset(sc_host, 0, sizeof(DevScalars));
