@@ -566,12 +566,12 @@ def run_ours(args, world, rank, local):
         fp64 = {"value": NN * k64 / t64, "ms_per_step": 1e3 * t64 / k64, "steps": k64,
                 "speedup_fp32_over_fp64": (NN * args.steps / secs) / (NN * k64 / t64)}
         if w.N == 2048:
-            ach = FP64_FLOP_PER_POINT_N2048 * NN / t64 / 1e12
+            ach = FP64_FLOP_PER_POINT_N2048 * NN * k64 / t64 / 1e12     # t64: seconds for k64 steps
             fp64["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "achieved": round(ach, 3),
                                 "peak": FP64_PEAK_TFLOPS, "peak_kind": "nominal FP64 (152 SMs x 2 DFMA/clk x 2 x 2.07 GHz)",
                                 "frac": round(ach / FP64_PEAK_TFLOPS, 3),
                                 "flop_per_point": FP64_FLOP_PER_POINT_N2048,
-                                "hbm_frac": round(2289e6 / t64 / 1e9 / measured_peaks()[0], 4)}
+                                "hbm_frac": round(2289e6 * k64 / t64 / 1e9 / measured_peaks()[0], 4)}
     # ---- accuracy of the timed precision against the FP64 GPU path (1000 steps: the precision target)
     acc = None
     if args.precision == "fp32" and not args.no_fp64 and rank == 0 and args.accuracy_steps > 0:

@@ -3,7 +3,9 @@ library built with -DCCMSAV_BOUNDS (libccmsav_bounds.so) runs the small and
 ragged grids (N = 8 ... 256, FP64 and FP32, block- and warp-FFT paths, start
 and BDF2 steps, graph-launched steps, the classical and BDF1 modes) in a
 child process; no access may leave its array (ccmsav_bounds_flag() = 0) and
-the results stay those of the oracle.  compute-sanitizer is not available
+the results stay those of the oracle (the shrinking ellipse: the single
+perturbed circle at N = 256 amplifies a 1e-10 perturbation to 1e-5 within
+50 steps, too sensitive for an FP32 comparison).  compute-sanitizer is not available
 for this purpose, so the checks are compiled into the kernels."""
 import json
 import os
@@ -29,7 +31,7 @@ out = []
 cases = [(N, prec, mode) for N in (8, 16, 32, 64, 128, 256) for prec in ("fp64", "fp32")
          for mode in ("cc", "bdf1", "classical")]
 for N, prec, mode in cases:
-    w = I.workload("one_vesicle", N=N, dt=1e-5)
+    w = I.workload("ellipse_shrink", N=N)
     sim = cc.Simulation(w.params, N, precision=prec, bdf1_always=(mode == "bdf1"), classical=(mode == "classical"))
     if mode == "classical":
         sim.set_pcg(1e-13 if prec == "fp64" else 1e-6, 400)
