@@ -348,7 +348,7 @@ public:
             if (r) return r;
         }
         const char* force_block = std::getenv("CCMSAV_FORCE_BLOCK_FFT");   // test switch: block-FFT kernels only
-        if (std::is_same<T, float>::value && M >= 64 && M <= 2048 && !(force_block && force_block[0] == '1')) {
+        if (std::is_same<T, float>::value && M >= 64 && M <= 4096 && !(force_block && force_block[0] == '1')) {
             int r = init_warp_path();
             if (r) return r;
         }
@@ -447,9 +447,13 @@ public:
     }
 
     // ---- autotuner --------------------------------------------------------
+    template <int MM> static const void* coldct_fn() {
+        if constexpr (MM == 4096) return (const void*)kw_coldct_gram_split<MM>;
+        else return (const void*)kw_coldct_gram<MM>;
+    }
     template <int MM> int apply_carveout_M(int c) {
         if (cudaFuncSetAttribute((const void*)kw_rowdct_T<MM>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess ||
-            cudaFuncSetAttribute((const void*)kw_coldct_gram<MM>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess ||
+            cudaFuncSetAttribute(coldct_fn<MM>(), cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess ||
             cudaFuncSetAttribute((const void*)kw_comb_icolT<MM>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess)
             return CCMSAV_ECUDA;
         return CCMSAV_OK;
@@ -463,6 +467,7 @@ public:
                 case 512: return apply_carveout_M<512>(c);
                 case 1024: return apply_carveout_M<1024>(c);
                 case 2048: return apply_carveout_M<2048>(c);
+                case 4096: return apply_carveout_M<4096>(c);
             }
         }
         return CCMSAV_OK;
@@ -644,9 +649,13 @@ public:
         const size_t bb = Gm::buf_bytes();
         wRT = Gm::SLOTS; wsm_rt = bb;
         wKC = Gm::SLOTS / NF; wsm_col = bb;
+        if constexpr (MM == 4096) {      // column pass split into the two field groups, one column per CTA
+            wKC = 1;
+            wsm_col = (size_t)5 * Gm::BUF * sizeof(cplx<float>);
+        }
         wRT4 = Gm::SLOTS / 2; wsm_comb = Gm::bufp_bytes();
         wsm_irow = InvGeo<MM>::smem_bytes();
-        if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt, kRowCarveout) || set_smem_limit((const void*)kw_coldct_gram<MM>, wsm_col, kColCarveout) ||
+        if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt, kRowCarveout) || set_smem_limit(coldct_fn<MM>(), wsm_col, kColCarveout) ||
             set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb, kCombCarveout) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
             return CCMSAV_ECUDA;
         // L2 prefetch one residency ahead only where few CTAs fit per SM (one
@@ -728,6 +737,7 @@ public:
             case 512: r = setup_warp<512>(); break;
             case 1024: r = setup_warp<1024>(); break;
             case 2048: r = setup_warp<2048>(); break;
+            case 4096: r = setup_warp<4096>(); break;
         }
         if (r == CCMSAV_OK) warp_path = have_warp = true;
         if (r == CCMSAV_OK) {   // a schedule the autotuner chose for this N
@@ -750,7 +760,11 @@ public:
         const cplx<float>* t2 = tw2;
         kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, t2, pair_tab(twF), ahead_rt);
         mark(1);
-        kw_coldct_gram<MM><<<N / wKC, kWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2, t2, pair_tab(twF), evf, evp, sf);
+        if constexpr (MM == 4096)
+            kw_coldct_gram_split<MM><<<dim3(N, 2), kSplitWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2,
+                                                                                  t2, pair_tab(twF), evf, evp, sf);
+        else
+            kw_coldct_gram<MM><<<N / wKC, kWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2, t2, pair_tab(twF), evf, evp, sf);
         mark(2);
     }
     int bdf1_launch = 0;
@@ -776,7 +790,8 @@ public:
             case 256: launch_warp_ffts<256>(s, anchor); break;
             case 512: launch_warp_ffts<512>(s, anchor); break;
             case 1024: launch_warp_ffts<1024>(s, anchor); break;
-            default: launch_warp_ffts<2048>(s, anchor); break;
+            case 2048: launch_warp_ffts<2048>(s, anchor); break;
+            default: launch_warp_ffts<4096>(s, anchor); break;
         }
     }
     void warp_inverse(const SpecCoef& s, int anchor) {
@@ -787,7 +802,8 @@ public:
             case 256: launch_warp_inverse<256>(s, anchor); break;
             case 512: launch_warp_inverse<512>(s, anchor); break;
             case 1024: launch_warp_inverse<1024>(s, anchor); break;
-            default: launch_warp_inverse<2048>(s, anchor); break;
+            case 2048: launch_warp_inverse<2048>(s, anchor); break;
+            default: launch_warp_inverse<4096>(s, anchor); break;
         }
     }
 

@@ -11,8 +11,10 @@
 //      written to the buffer in natural order.
 // One smem round trip per stage pair instead of one per radix-8 stage, no
 // block barriers (only __syncwarp), and 32 independent values per lane.
-// Supported lines: M in {64, ..., 2048} (N = 2M in 128 .. 4096);
-// G = 2^floor(log2(M)/2) <= 32, E = M / G <= 64.
+// Supported lines: M in {64, ..., 4096} (N = 2M in 128 .. 8192);
+// G = 2^floor(log2(M)/2), E = M / G <= 64.  A group of G = 64 lanes spans
+// two warps (M = 4096): its lanes synchronise through a named barrier of the
+// line (id 1 + line slot, 64 threads) instead of __syncwarp.
 #pragma once
 #include <type_traits>
 #include "dct_device.cuh"
@@ -178,6 +180,32 @@ template <> struct Shape<256>  { static constexpr int E = 16, G = 16; };
 template <> struct Shape<512>  { static constexpr int E = 32, G = 16; };
 template <> struct Shape<1024> { static constexpr int E = 32, G = 32; };
 template <> struct Shape<2048> { static constexpr int E = 64, G = 32; };
+template <> struct Shape<4096> { static constexpr int E = 64, G = 64; };
+
+// Lane n2 of its line's group and the line's slot in the CTA: G <= 32 puts
+// 32 / G lines in a warp; G = 64 spreads a line over two consecutive warps.
+template <int M> __device__ __forceinline__ void lane_geo(int& n2, int& slot) {
+    constexpr int G = Shape<M>::G;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if constexpr (G <= 32) {
+        n2 = lane % G;
+        slot = warp * (32 / G) + lane / G;
+    } else {
+        n2 = lane + 32 * (warp % (G / 32));
+        slot = warp / (G / 32);
+    }
+}
+
+// Barrier of one line's lane group: the warp's own lanes for G <= 32, the
+// two warps of the line (named barrier 1 + slot; every one of their 64
+// threads arrives) for G = 64.
+template <int G> __device__ __forceinline__ void line_sync(int slot) {
+    if constexpr (G <= 32) {
+        __syncwarp();
+    } else {
+        asm volatile("bar.sync %0, %1;" :: "r"(1 + slot), "r"(G) : "memory");
+    }
+}
 
 // Per-line buffer length (complex values) for the transpose and the
 // natural-order result.  Padded (SWZ = false): rows of G + 1 values; + 2 so
@@ -205,7 +233,7 @@ template <int M, bool SWZ> __device__ __forceinline__ int tpos(int R, int c) {
 // Steps 1-4.  v: this lane's E values in four-step order.  buf: this line's
 // buffer.  On return buf[k] = Z[k], k = 0..M-1 (visible to the warp).
 template <typename T, int M, bool INV, bool SWZ = false>
-__device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>* __restrict__ tw2, int n2) {
+__device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>* __restrict__ tw2, int n2, int slot) {
     constexpr int E = Shape<M>::E, G = Shape<M>::G, J = E / G;
     DIF<T, E, INV, 0>::run(v);
     if constexpr (!INV) {
@@ -228,7 +256,7 @@ __device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>
             buf[tpos<M, SWZ>(k1, n2)] = cmulc(v[r], tw2[k1 * G + n2]);
         }
     }
-    __syncwarp();
+    line_sync<G>(slot);
     if constexpr (SWZ && wide_reads<M>() && std::is_same<T, float>::value) {
 #pragma unroll
         for (int j = 0; j < J; ++j)
@@ -244,7 +272,7 @@ __device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>
 #pragma unroll
             for (int m = 0; m < G; ++m) v[j * G + m] = buf[tpos<M, SWZ>(n2 * J + j, m)];
     }
-    __syncwarp();
+    line_sync<G>(slot);
 #pragma unroll
     for (int j = 0; j < J; ++j) {
         if (j == 0) DIF<T, G, INV, 0>::run(v);
@@ -254,7 +282,7 @@ __device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>
     for (int j = 0; j < J; ++j)
 #pragma unroll
         for (int r = 0; r < G; ++r) buf[(n2 * J + j) + E * bitrev<G>(r)] = v[j * G + r];
-    __syncwarp();
+    line_sync<G>(slot);
 }
 
 // Forward pack from a real line x in global memory (16-byte aligned):
@@ -267,9 +295,15 @@ __device__ __forceinline__ void pack_fwd_global(const float* __restrict__ x, cpl
     for (int n1 = 0; n1 < E / 2; ++n1) {
         const float4 q = __ldcg(reinterpret_cast<const float4*>(x) + (G * n1 + n2));   // L2 only: keeps L1 for the tables
         v[n1] = mk(q.x, q.z);
-        const float ox = __shfl_xor_sync(0xffffffffu, q.w, G - 1);
-        const float oy = __shfl_xor_sync(0xffffffffu, q.y, G - 1);
-        v[E - 1 - n1] = mk(ox, oy);
+        if constexpr (G <= 32) {
+            const float ox = __shfl_xor_sync(0xffffffffu, q.w, G - 1);
+            const float oy = __shfl_xor_sync(0xffffffffu, q.y, G - 1);
+            v[E - 1 - n1] = mk(ox, oy);
+        } else {
+            // the partner lane G - 1 - n2 sits in the other warp: load its quad too
+            const float4 p = __ldg(reinterpret_cast<const float4*>(x) + (G * n1 + (G - 1 - n2)));
+            v[E - 1 - n1] = mk(p.w, p.y);
+        }
     }
 }
 

@@ -21,6 +21,26 @@ struct SpecCoefF {        // FP32 copy of SpecCoef for the FP32 spectral kernels
 
 constexpr int kWarps = 8;
 
+// Exact (double-float) sum over the G lanes of one line: inside the warp for
+// G <= 32; for G = 64 each warp sums its half, the halves go through `sm`
+// (two float2 per line slot) and both warps add them in the same order.
+template <int G>
+__device__ __forceinline__ double line_sum_exact(float hi, float lo, int slot, float2* sm) {
+    if constexpr (G <= 32) {
+        return group_sum_exact<G>(hi, lo);
+    } else {
+        const float2 h = group_sum_df<32>(hi, lo);
+        const int half = (threadIdx.x >> 5) & 1;
+        if ((threadIdx.x & 31) == 0) sm[2 * slot + half] = h;
+        wf::line_sync<G>(slot);
+        float2 a = sm[2 * slot];
+        const float2 b = sm[2 * slot + 1];
+        wf::line_sync<G>(slot);        // the two slots may be written again by a later call
+        df_add2(a.x, a.y, b.x, b.y);
+        return (double)a.x + (double)a.y;
+    }
+}
+
 
 
 // Pair-ordered spectra of the warp path: for each spectral row kx and each
@@ -38,8 +58,9 @@ template <int M> struct SpecRow {
 
 template <int M> struct WGeo {
     static constexpr int E = wf::Shape<M>::E, G = wf::Shape<M>::G;
-    static constexpr int LPW = 32 / G;                  // lines per warp
-    static constexpr int SLOTS = kWarps * LPW;          // line buffers per CTA
+    static constexpr int WPL = G > 32 ? G / 32 : 1;     // warps per line
+    static constexpr int LPW = G > 32 ? 1 : 32 / G;     // lines per warp (one line spans WPL warps)
+    static constexpr int SLOTS = kWarps * LPW / WPL;    // line buffers per CTA
     // complex per buffer: unpadded, XOR-swizzled transpose (M + 2), so that
     // three 8-line CTAs of the forward kernels fit the 196 KB shared-memory
     // configuration; padded rows (G + 1 values) for the recovery kernel (two
@@ -69,14 +90,13 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
         if (ahead > 0 && t < (int)(gridDim.x * gridDim.y) && threadIdx.x < RT)
             prefetch_l2(in + (t / gridDim.x) * NN + (size_t)((t % gridDim.x) * RT + threadIdx.x) * N, N * sizeof(float));
     }
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = lane / G, n2 = lane % G;
-    const int slot = warp * Gm::LPW + grp;
+    int n2, slot;
+    wf::lane_geo<M>(n2, slot);
     cplx<float>* buf = bufs + (size_t)slot * Gm::BUF;
     {
         cplx<float> v[E];
         wf::pack_fwd_global<M>(in + CCM_IXW(f * NN + (size_t)(y0 + slot) * N, N, NF * NN), v, n2);
-        wf::fourstep<float, M, false, true>(v, buf, tw2, n2);
+        wf::fourstep<float, M, false, true>(v, buf, tw2, n2, slot);
     }
     // DCT post-process in place, one pair at a time: pair k reads the complex
     // slots k and M-k and writes its four modes back into them (slot k: modes
@@ -139,14 +159,15 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
     const int kx0 = blockIdx.x * KC;
+    static_assert(G <= 32, "lines of one warp at most; longer lines take kw_coldct_gram_split");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = lane / G, n2 = lane % G;
-    const int slot = warp * Gm::LPW + grp;               // line = (kc, field)
+    int n2, slot;                                        // line = (kc, field)
+    wf::lane_geo<M>(n2, slot);
     const int kc = slot / NF, f = slot % NF;
     {
         cplx<float> v[E];
         wf::pack_fwd_global<M>(in + CCM_IXW(f * NN + (size_t)(kx0 + kc) * N, N, NF * NN), v, n2);
-        wf::fourstep<float, M, false, true>(v, bufs + (size_t)slot * Gm::BUF, tw2, n2);
+        wf::fourstep<float, M, false, true>(v, bufs + (size_t)slot * Gm::BUF, tw2, n2, slot);
     }
     __syncthreads();
     float acc[NRED2];
@@ -225,6 +246,102 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
                                        reinterpret_cast<double*>(smraw));
 }
 
+// ------------------------------------------------------------------ kw_coldct_gram_split
+// The column pass for lines too long to keep all eight fields of a column on
+// chip (M = 4096: 32 KB per line).  The Gram sums have no terms across the
+// two groups {f0', S, H, Q, K} (the 15 chi entries) and {P, g0', LP} (the
+// two zeta entries), so one CTA per (column kx, group): blockIdx.y = 0 takes
+// the five fields (ten warps, two per line), blockIdx.y = 1 the three (six
+// warps; its other four warps only join the block barriers).  Each writes its
+// own columns of the column's partial row and its fields' spectra (P is not
+// stored).
+constexpr int kSplitWarps = 10;
+
+template <int M>
+__global__ void __launch_bounds__(kSplitWarps * 32, 1)
+kw_coldct_gram_split(const float* __restrict__ in, float* __restrict__ spec, double* __restrict__ part,
+                     const cplx<float>* __restrict__ tw2, wf::PairTwTab twF,
+                     const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc) {
+    using Gm = WGeo<M>;
+    constexpr int N = 2 * M, G = Gm::G, E = Gm::E;
+    static_assert(G == 64, "two warps per line");
+    extern __shared__ __align__(16) unsigned char smraw[];
+    cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
+    const size_t NN = (size_t)N * N;
+    const int kx = blockIdx.x, grp = blockIdx.y;
+    const int nf = grp == 0 ? 5 : 3, f0 = grp == 0 ? 0 : 5;
+    int n2, slot;
+    wf::lane_geo<M>(n2, slot);                           // slot 0 .. 4
+    if (slot < nf) {                                     // both warps of a line take the same branch
+        cplx<float> v[E];
+        wf::pack_fwd_global<M>(in + CCM_IXW((f0 + slot) * NN + (size_t)kx * N, N, NF * NN), v, n2);
+        wf::fourstep<float, M, false, true>(v, bufs + (size_t)slot * Gm::BUF, tw2, n2, slot);
+    }
+    __syncthreads();
+    float acc[NRED2];
+#pragma unroll
+    for (int i = 0; i < NRED2; ++i) acc[i] = 0.f;
+    const float evx = evf[kx];
+    for (int k = threadIdx.x; k <= M / 2; k += blockDim.x) {
+        const wf::PairTw tw = wf::load_pair_tw<false>(twF, k);
+        Quad<float> X[5];
+#pragma unroll
+        for (int g = 0; g < 5; ++g) {
+            if (g >= nf) continue;
+            const cplx<float>* b = bufs + (size_t)g * Gm::BUF;
+            X[g] = wf::post_pair_lean(b[k], b[(M - k) & (M - 1)], tw);
+        }
+        const float4 e4 = evp[k];
+        const float ev_u[4] = {e4.x, e4.y, e4.z, e4.w};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (!pair_mode_valid(u, k, M)) continue;
+            const float s = evx + ev_u[u];
+            const float isig = __frcp_rn(sc.C1 + s * (sc.C2 + sc.C3 * s));
+            const float itau = __frcp_rn(sc.Ct + sc.lam * s);
+            float v[NF];
+#pragma unroll
+            for (int g = 0; g < NF; ++g) v[g] = 0.f;
+#pragma unroll
+            for (int g = 0; g < 5; ++g) {
+                if (g >= nf) continue;
+                const float x = (u == 0) ? X[g].xk : (u == 1) ? X[g].xNk : (u == 2) ? X[g].xMk : X[g].xMpk;
+                v[f0 + g] = x;
+            }
+            gram_accumulate(acc, v, isig, itau);
+        }
+        // spectra in pair order (the layout of kw_coldct_gram)
+        float* dst = spec + (size_t)kx * SpecRow<M>::KS + 4 * k;
+#pragma unroll
+        for (int g = 0; g < 5; ++g) {
+            if (g >= nf) continue;
+            const int f = f0 + g;
+            if (f == 5) continue;
+            const size_t o = (size_t)kx * SpecRow<M>::KS + 4 * k + (size_t)(f < 5 ? f : f - 1) * SpecRow<M>::FO;
+            if (!CCM_OKW(o, 4, (size_t)N * SpecRow<M>::KS)) continue;
+            float4 w = make_float4(X[g].xk, k == 0 ? 0.f : X[g].xNk, X[g].xMk, X[g].xMpk);
+            if (k == 0) w.w = w.z;
+            *reinterpret_cast<float4*>(dst + (size_t)(f < 5 ? f : f - 1) * SpecRow<M>::FO) = w;
+        }
+    }
+    __syncthreads();       // the line buffers are free: their start holds the block reduction
+    // block sums of this group's Gram columns (float pairs, as block_sum_store_part)
+    float* smf = reinterpret_cast<float*>(smraw);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int i = 0; i < NRED2; ++i) {
+        const float sw = warp_sum(acc[i]);
+        if (lane == 0) smf[warp * NRED2 + i] = sw;
+    }
+    __syncthreads();
+    const int c0 = grp == 0 ? 0 : 15, c1 = grp == 0 ? 15 : NRED2;
+    if (threadIdx.x >= c0 && threadIdx.x < c1) {
+        float hi = 0.f, lo = 0.f;
+        for (int w = 0; w < kSplitWarps; ++w) df_add(hi, lo, smf[w * NRED2 + threadIdx.x]);
+        reinterpret_cast<float2*>(part)[(size_t)kx * NRED2 + threadIdx.x] = make_float2(hi, lo);
+    }
+}
+
 // ------------------------------------------------------------------ kw_comb_icolT
 // RT = SLOTS/2 spectral rows per CTA, two lines (d_phi^, d_psi^) per row.
 // Phase 1 (all threads): gather the spectra, combine, divide, pre-process
@@ -290,16 +407,16 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
         if (k > 0) b[M - k] = zMk;
     }
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = lane / G, n2 = lane % G;
-    const int slot = warp * Gm::LPW + grp;              // line = slot: row slot/2, field slot%2
+    __shared__ float2 lsum[2 * Gm::SLOTS];
+    int n2, slot;                                        // line = slot: row slot/2, field slot%2
+    wf::lane_geo<M>(n2, slot);
     cplx<float>* buf = bufs + (size_t)slot * Gm::BUFP;
     {
         cplx<float> v[E];
 #pragma unroll
         for (int n1 = 0; n1 < E; ++n1) v[n1] = buf[G * n1 + n2];
-        __syncwarp();
-        wf::fourstep<float, M, true>(v, buf, tw2, n2);
+        wf::line_sync<G>(slot);
+        wf::fourstep<float, M, true>(v, buf, tw2, n2, slot);
     }
     float dhi = 0.f, dlo = 0.f;
 #pragma unroll
@@ -310,7 +427,7 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
     }
     // FP32 path: the zero-mean psi increment's kx = 0 column should sum to 0
     // over y; record what the FP32 transform left (removed in kw_irow)
-    const double dsum = group_sum_exact<G>(dhi, dlo);
+    const double dsum = line_sum_exact<G>(dhi, dlo, slot, lsum);
     if (anchor_mass && (slot & 1) == 1 && kx0 + (slot >> 1) == 0 && n2 == 0) dsc->dc_col = dsum;
     __syncthreads();
     // transposed write straight from the line buffers: after the inverse
@@ -318,6 +435,23 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
     // samples y = 4m+3, 4m+1 (the even/odd reordering undone in the indexing)
     const float2* stage = reinterpret_cast<const float2*>(bufs);
     constexpr int BC = Gm::BUFP;                     // float2 per line buffer
+    if constexpr (RT < 4) {
+        // two rows per CTA (4096-point lines): 8-byte stores of the row pair
+        static_assert(RT == 2, "two or a multiple of four rows per CTA");
+        for (int q = threadIdx.x; q < 2 * (M / 2); q += blockDim.x) {
+            const int m = q % (M / 2), fld = q / (M / 2);
+            const float2* sp = stage + (size_t)fld * BC;       // row 0: buffer fld, row 1: buffer 2 + fld
+            const float2 a0 = sp[m], a1 = sp[2 * BC + m];
+            const float2 b0 = sp[M - 1 - m], b1 = sp[2 * BC + M - 1 - m];
+            if (!CCM_OKW(fld * NN + (size_t)(4 * m + 3) * N + kx0, 2, 2 * NN)) continue;
+            float* d = out + fld * NN + (size_t)(4 * m) * N + kx0;
+            *reinterpret_cast<float2*>(d) = make_float2(a0.x, a1.x);
+            *reinterpret_cast<float2*>(d + N) = make_float2(b0.y, b1.y);
+            *reinterpret_cast<float2*>(d + 2 * (size_t)N) = make_float2(a0.y, a1.y);
+            *reinterpret_cast<float2*>(d + 3 * (size_t)N) = make_float2(b0.x, b1.x);
+        }
+        return;
+    }
     constexpr int R4 = RT / 4;
     for (int q = threadIdx.x; q < 2 * R4 * (M / 2); q += blockDim.x) {
         const int m = q % (M / 2), rest = q / (M / 2);
@@ -354,7 +488,7 @@ template <int M> __host__ __device__ constexpr int inv_min_ctas() {
 
 template <int M> struct InvGeo {
     static constexpr int WARPS = inv_warps<M>();
-    static constexpr int LINES = WARPS * WGeo<M>::LPW;          // lines per CTA
+    static constexpr int LINES = WARPS * WGeo<M>::LPW / WGeo<M>::WPL;   // lines per CTA
     static constexpr int BUF = wf::buf_len<M, true>();         // unpadded, swizzled transpose
     static constexpr size_t smem_bytes() { return (size_t)LINES * BUF * sizeof(cplx<float>); }
 };
@@ -389,9 +523,9 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
         if (k > 0) b[M - k] = zMk;
     }
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int grp = lane / G, n2 = lane % G;
-    const int slot = warp * Gm::LPW + grp;
+    __shared__ float2 lsum[2 * L];
+    int n2, slot;
+    wf::lane_geo<M>(n2, slot);
     const int gl = l0 + slot;
     const bool valid = gl < 2 * N;                       // the last CTA has fewer lines
     const int fld = gl & 1;
@@ -400,8 +534,8 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
         cplx<float> v[E];
 #pragma unroll
         for (int n1 = 0; n1 < E; ++n1) v[n1] = buf[G * n1 + n2];
-        __syncwarp();
-        wf::fourstep<float, M, true, true>(v, buf, tw2, n2);
+        wf::line_sync<G>(slot);
+        wf::fourstep<float, M, true, true>(v, buf, tw2, n2, slot);
     }
     const size_t roff = valid ? (size_t)(gl >> 1) * N : 0;
     // FP32 path, psi: the row's increments should sum to sqrt(N) x0 (x0 the
@@ -417,7 +551,7 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
             const cplx<float> a = buf[m], b = buf[M - 1 - m];
             df_add(rhi, rlo, a.x); df_add(rhi, rlo, b.y); df_add(rhi, rlo, a.y); df_add(rhi, rlo, b.x);
         }
-    const double rsum = group_sum_exact<G>(rhi, rlo);
+    const double rsum = line_sum_exact<G>(rhi, rlo, slot, lsum);
     float an = 0.f;
     if (psi_line) {
         const double x0 = (double)__ldg(in + fld * NN + roff);
@@ -457,7 +591,7 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
         if (i == 0) first = o.x;
         *reinterpret_cast<float4*>(dst + 4 * m) = o;
     }
-    const double rest = group_sum_exact<G>(carry, 0.f);
+    const double rest = line_sum_exact<G>(carry, 0.f, slot, lsum);
     if (psi_line && n2 == 0) dst[0] = dither_round(first, (float)rest, dither_key(step, (uint32_t)roff) | 1u);
 }
 

@@ -46,6 +46,20 @@ for N, prec, mode in cases:
               classical=(mode == "classical"))
     e = max(float(np.abs(phi - s.phi).max() / np.abs(s.phi).max()), float(np.abs(psi - s.psi).max() / np.abs(s.psi).max()))
     out.append({"N": N, "precision": prec, "mode": mode, "flag": flag, "err": e})
+# the largest grid on the FP32 warp path (two warps per 4096-point line), against FP64 on the GPU
+w = I.lattice_16(N=8192)
+res = {}
+for prec in ("fp64", "fp32"):
+    sim = cc.Simulation(w.params, 8192, precision=prec)
+    sim.set_state(w.phi0, w.psi0)
+    sim.step(1)
+    sim.step(3)
+    res[prec] = sim.state()
+    flag = cc.ccmsav_bounds_flag(sim.h) if prec == "fp32" else 0
+    sim.close()
+e = max(float(np.abs(res["fp32"][0] - res["fp64"][0]).max() / np.abs(res["fp64"][0]).max()),
+        float(np.abs(res["fp32"][1] - res["fp64"][1]).max() / np.abs(res["fp64"][1]).max()))
+out.append({"N": 8192, "precision": "fp32", "mode": "cc-vs-fp64", "flag": flag, "err": e})
 print(json.dumps(out))
 """
 
@@ -58,6 +72,6 @@ def test_bounds_checked_build_small_grids():
     for c in res:
         print(c)
     assert all(c["flag"] == 0 for c in res), [c for c in res if c["flag"]]
-    tol = {"fp64": 1e-11, "fp32": 2e-5}
+    tol = {"fp64": 1e-11, "fp32": 2e-5}      # N = 8192: FP32 against FP64 after 4 steps
     bad = [c for c in res if c["err"] > tol[c["precision"]]]
     assert not bad, bad
