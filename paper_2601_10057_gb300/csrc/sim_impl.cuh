@@ -448,7 +448,7 @@ public:
 
     // ---- autotuner --------------------------------------------------------
     template <int MM> static const void* coldct_fn() {
-        if constexpr (MM == 4096) return (const void*)kw_coldct_gram_split<MM>;
+        if constexpr (WGeo<MM>::WPL > 1) return (const void*)kw_coldct_gram_split<MM>;
         else return (const void*)kw_coldct_gram<MM>;
     }
     template <int MM> int apply_carveout_M(int c) {
@@ -649,7 +649,7 @@ public:
         const size_t bb = Gm::buf_bytes();
         wRT = Gm::SLOTS; wsm_rt = bb;
         wKC = Gm::SLOTS / NF; wsm_col = bb;
-        if constexpr (MM == 4096) {      // column pass split into the two field groups, one column per CTA
+        if constexpr (Gm::WPL > 1) {     // two-warp lines: column pass split into the two field groups, one column per CTA
             wKC = 1;
             wsm_col = (size_t)5 * Gm::BUF * sizeof(cplx<float>);
         }
@@ -760,7 +760,7 @@ public:
         const cplx<float>* t2 = tw2;
         kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, t2, pair_tab(twF), ahead_rt);
         mark(1);
-        if constexpr (MM == 4096)
+        if constexpr (WGeo<MM>::WPL > 1)
             kw_coldct_gram_split<MM><<<dim3(N, 2), kSplitWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2,
                                                                                   t2, pair_tab(twF), evf, evp, sf);
         else
