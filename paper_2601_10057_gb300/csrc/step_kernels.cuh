@@ -359,7 +359,18 @@ __device__ __forceinline__ double bar_add(double a, double b, double du, double 
 // two-cell halo (for Lap^2 phi_bar), and phi*, psi* (overwritten in place by
 // the P numerator), psi_bar - psi* and Lap phi_bar with a one-cell halo.  Partial sums are
 // accumulated per thread over its cells, then reduced once per block.
+//
+// FP32 fields: phi_bar = phi^n + (phi^n - phi^{n-1})/3 is kept as an
+// unevaluated pair hi + lo (hi the FMA-rounded value, lo its exact residual,
+// the same pair the final update u^{n+1} = u_bar + du forms), and lo enters
+// Lap phi_bar, Lap^2 phi_bar and the beta' phi_bar term of f0'.  The linear
+// part of f0' (C2 Lap - C3 Lap^2 - beta') phi_bar is nearly cancelled by the
+// implicit operator in the recovery; with phi_bar rounded to FP32 here but
+// not in the final update, the mismatch was fed back into phi every step
+// (measured: 4.0e-5 max-norm deviation from the FP64 path after 1000 steps
+// at N = 2048 with the rounded phi_bar, 2.6e-6 with phi_bar exact in f0').
 constexpr int TX = 64, TY = 4, TYB = 32;
+template <typename T> constexpr bool kBarLo = std::is_same<T, float>::value;
 
 template <typename T>
 __global__ void __launch_bounds__(TX * TY)
@@ -374,6 +385,7 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
     T* sP = sps;              // the P numerator replaces psi* in the one-halo pass
     T* sdq = sps + H1 * W1;
     T* slb = sdq + H1 * W1;
+    T* slo = slb + H1 * W1;   // FP32 only: [TYB+4][W2] low parts of phi_bar
     __shared__ double sred[(TX * TY / 32) * 4];
     __shared__ double smean[2][TX * TY / 32];
     __shared__ T smin[TX * TY / 32];
@@ -426,7 +438,13 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
                 if (u < NI && (!ex || ex_on)) {
                     const int lj = ex ? ex_r : ty + TY * u, li = ex ? ex_c : cx;
                     const T a = ra[b], da = a - rb[b];
-                    sbar[lj * W2 + li] = a + kbar * da;
+                    if constexpr (kBarLo<T>) {
+                        const T t1 = fmaf(da, kbar, a);
+                        sbar[lj * W2 + li] = t1;
+                        slo[lj * W2 + li] = fmaf(da, kbar, a - t1);
+                    } else {
+                        sbar[lj * W2 + li] = a + kbar * da;
+                    }
                     if (lj >= 1 && lj <= TYB + 2 && li >= 1 && li <= TX + 2) {
                         const int o = (lj - 1) * W1 + (li - 1);
                         const T du = rc[b] - rd[b];
@@ -453,7 +471,14 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
         const int lj1 = q / W1, li1 = q % W1;
         const T* b = sbar + (lj1 + 1) * W2 + li1 + 1;
         const T C = b[0];
-        slb[q] = (((b[1] - C) + (b[-1] - C)) + ((b[W2] - C) + (b[-W2] - C))) * ih2;
+        if constexpr (kBarLo<T>) {
+            const T* bl = slo + (lj1 + 1) * W2 + li1 + 1;
+            const T Cl = bl[0];
+            const T lapl = ((bl[1] - Cl) + (bl[-1] - Cl)) + ((bl[W2] - Cl) + (bl[-W2] - Cl));
+            slb[q] = ((((b[1] - C) + (b[-1] - C)) + ((b[W2] - C) + (b[-W2] - C))) + lapl) * ih2;
+        } else {
+            slb[q] = (((b[1] - C) + (b[-1] - C)) + ((b[W2] - C) + (b[-W2] - C))) * ih2;
+        }
         const T ph = sph[q], ps = sps[q];
         T sp, cp;
         sincospi_<T>((T)0.5 * ph, &sp, &cp);
@@ -500,7 +525,8 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
         const T LP = (mE * (sP[o + 1] - PC) - mW * (PC - sP[o - 1])
                       + mN * (sP[o + W1] - PC) - mS * (PC - sP[o - W1])) * ih2;
         const T bC = sbar[(lj + 1) * W2 + li + 1];
-        const T f0 = c.C2 * lbC - c.C3 * lap2b - c.Mth * lapp - c.betap * bC;
+        T f0 = c.C2 * lbC - c.C3 * lap2b - c.Mth * lapp - c.betap * bC;
+        if constexpr (kBarLo<T>) f0 = fmaf(-c.betap, slo[(lj + 1) * W2 + li + 1], f0);
         const T g0 = c.lam * lapd;
         if (inside && CCM_OK(7 * NN + g, 8 * NN)) {
             out[0 * NN + g] = f0;
@@ -571,7 +597,7 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
 }
 
 template <typename T> __host__ __device__ constexpr size_t stencil_smem_bytes() {
-    return ((size_t)(TYB + 4) * (TX + 4) + 4 * (size_t)(TYB + 2) * (TX + 2)) * sizeof(T);
+    return ((size_t)(kBarLo<T> ? 2 : 1) * (TYB + 4) * (TX + 4) + 4 * (size_t)(TYB + 2) * (TX + 2)) * sizeof(T);
 }
 
 // The pair k (0 <= k <= M/2) of the line transforms touches the modes
