@@ -315,7 +315,8 @@ def run_reference(args, world, rank):
 
 def extra_workloads(sh, stream):
     """Batching form (64 simulations of N in {128, 256, 512} in one handle:
-    one stream each, BDF2 steps from one graph for the batch) and the larger
+    one stream each or one launch per kernel for a group of simulations of
+    the same N, BDF2 steps from one graph for the batch) and the larger
     single grids (N = 4096 three vesicles, N = 8192 sixteen vesicles), FP32,
     device-timed with events on the caller's stream after 6 warm-up steps."""
     import torch
@@ -338,6 +339,7 @@ def extra_workloads(sh, stream):
                 tuned.setdefault(str(w.N), {"path": "warp" if r[0] else "block", "carveout": int(r[1]),
                                             "best_ms_per_step": round(float(r[2]), 4),
                                             "default_ms_per_step": round(float(r[3]), 4)})
+            tuned["launch_group_points"] = sim.group_points()
         l0 = sim.launches()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)

@@ -136,6 +136,13 @@ int ccmsav_set_state_device(ccmsav_t* h, int sim, const void* phi, const void* p
 /* Advance every simulation by nsteps >= 0 time steps.  Asynchronous: work is
  * queued on the handle's stream; device-side errors are reported by the next
  * synchronising call (ccmsav_sync, get_state, energy, mass, get_aux).
+ * Several simulations: their BDF2 steps run three at a time from one CUDA
+ * graph per rotation phase of the three time levels.  Inside it, FP32
+ * simulations of the same N on the warp-FFT kernels (N = 128 .. 4096, no
+ * CCMSAV_CLASSICAL, no CCMSAV_TRACK_ENERGY) share each kernel launch (one
+ * launch per kernel, step and N for the whole group); the others run their
+ * own launches concurrently.  Every simulation's results are the same bits
+ * as a run of that simulation alone.
  * Returns CCMSAV_ESTATE if some simulation has no state yet or is in error. */
 int ccmsav_step(ccmsav_t* h, int nsteps);
 
@@ -226,12 +233,28 @@ int ccmsav_profile_read(ccmsav_t* h, int sim, double ms[8], long long* nsteps);
  * or 100 percent for the three 8-line transform kernels, and the CTA-level
  * Stockham FFT kernels; FP64 has only the latter.  The choice is recorded
  * for each (N, precision) of the handle in a process-wide table, from which
- * handles created later start.
+ * handles created later start.  For several simulations a second stage then
+ * times the launch-group size (ccmsav_set_group_points: the current value,
+ * no grouping, 2^17 .. 2^22 and 2^26 grid points per group) with the chosen
+ * schedule and keeps the fastest for this handle (the current value unless
+ * another is at least 2 % faster).
  * report (may be NULL) receives 4 doubles per simulation: warp path (1/0),
  * carveout, best ms/step, ms/step of the default schedule (0 when not timed).
  * Needs set_state for every simulation (CCMSAV_ESTATE otherwise); steps in
  * [1, 3000]; not for CCMSAV_CLASSICAL handles (CCMSAV_EINVAL).  Synchronises. */
 int ccmsav_autotune(ccmsav_t* h, int steps, double* report);
+
+/* Launch groups of a handle of several simulations (see ccmsav_step): FP32
+ * simulations of the same N on the warp-FFT kernels are grouped, in handle
+ * order, until a group holds about `points` grid points (at least two
+ * simulations); each group's six kernels per step are one launch each, and
+ * the groups run concurrently on different streams.  points = 0: no
+ * grouping.  Default 2^21.  Setting it synchronises and drops the handle's
+ * batch graphs (they are captured again at the next step); results do not
+ * depend on it (every simulation's bits equal its own run).
+ * ccmsav_group_points returns the current value (-1 for a NULL handle). */
+int ccmsav_set_group_points(ccmsav_t* h, long long points);
+long long ccmsav_group_points(ccmsav_t* h);
 
 /* Index checks of a library built with -DCCMSAV_BOUNDS (a separate
  * libccmsav_bounds.so, for testing): the step kernels check every element

@@ -94,6 +94,8 @@ def load(path: Optional[str] = None) -> C.CDLL:
         "ccmsav_set_pcg": (i, [vp, d, i]),
         "ccmsav_autotune": (i, [vp, i, _DP]),
         "ccmsav_bounds_flag": (i, [vp]),
+        "ccmsav_set_group_points": (i, [vp, C.c_longlong]),
+        "ccmsav_group_points": (C.c_longlong, [vp]),
         "ccmsav_pcg_stats": (i, [vp, i, _DP]),
         "ccmsav_solver_create": (i, [C.POINTER(vp), i, d, i, i, vp]),
         "ccmsav_solver_solve": (i, [vp, _DP, vp, vp]),
@@ -253,6 +255,14 @@ def ccmsav_autotune(h, steps: int, n_sims: int):
     return st, rep
 
 
+def ccmsav_set_group_points(h, points: int) -> int:
+    return load().ccmsav_set_group_points(h, int(points))
+
+
+def ccmsav_group_points(h) -> int:
+    return load().ccmsav_group_points(h)
+
+
 def ccmsav_set_pcg(h, rtol: float, max_iter: int) -> int:
     return load().ccmsav_set_pcg(h, float(rtol), int(max_iter))
 
@@ -364,6 +374,13 @@ class Simulation:
         st, rep = ccmsav_autotune(self.h, steps, len(self.N))
         self._check(st, "ccmsav_autotune")
         return rep
+
+    def set_group_points(self, points: int):
+        """Grid points per launch group of the batched step (0: no grouping)."""
+        self._check(ccmsav_set_group_points(self.h, points), "ccmsav_set_group_points")
+
+    def group_points(self) -> int:
+        return ccmsav_group_points(self.h)
 
     def set_pcg(self, rtol: float, max_iter: int = 200):
         self._check(ccmsav_set_pcg(self.h, rtol, max_iter), "ccmsav_set_pcg")

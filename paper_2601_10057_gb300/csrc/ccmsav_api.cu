@@ -1,5 +1,7 @@
 // ccmsav_api.cu -- the extern "C" entry points declared in include/ccmsav.h.
+#include <algorithm>
 #include <cmath>
+#include <map>
 #include <new>
 #include <vector>
 #include "sim.h"
@@ -10,6 +12,15 @@
 // independent simulations run concurrently.  Their BDF2 steps run from one
 // graph per rotation phase holding three steps of every simulation as
 // parallel branches: one launch per three steps for the whole batch.
+// Default size of a launch group: simulations of the same N are grouped
+// until a group holds about this many grid points; several groups run on
+// different streams, so their phases still overlap.  Measured (64 FP32
+// simulations, ms per batched step, no grouping -> 2^21): N = 128 0.222 ->
+// 0.114, N = 256 0.351 -> 0.286, the mixed 128/256/512 batch 0.549 ->
+// 0.484; at N = 512 and 1024 grouping gains nothing (0.252 -> 0.263 for 16
+// at N = 512), so the autotuner also times the group size per handle.
+constexpr long long kGroupPoints = 1LL << 21;
+
 struct ccmsav {
     std::vector<ccm::SimBase*> sims;
     cudaStream_t stream = nullptr;        // the caller's stream
@@ -21,6 +32,12 @@ struct ccmsav {
     std::vector<cudaEvent_t> join_ev;
     cudaGraphExec_t bexec[3] = {nullptr, nullptr, nullptr};
     bool batch_failed = false;
+    // grouped launches of the graph of each rotation phase: which
+    // simulations are grouped, and how many kernel launches one replay makes
+    // for the groups
+    std::vector<char> grouped[3];
+    long long group_launches[3] = {0, 0, 0};
+    long long group_points = kGroupPoints;   // grid points per launch group (0: no grouping)
 };
 
 namespace {
@@ -64,12 +81,62 @@ bool uniform_phase(const ccmsav* h) {
     return true;
 }
 
-// One graph: three steps of every simulation, each on its own stream.
+// One graph: three steps of every simulation.  Simulations that can share
+// launches (the same line length on the FP32 warp path) are grouped: each
+// group's six kernels per step run as one launch each on the stream of its
+// first member; every other simulation runs its own launches on its own
+// stream.  The groups' argument records go into the launch parameters, so
+// the graph keeps its own copy.
 int capture_batch(ccmsav* h, int ph) {
+    const size_t n = h->sims.size();
+    std::map<int, std::vector<size_t>> bykey;
+    if (h->group_points > 0)
+        for (size_t k = 0; k < n; ++k)
+            if (const int key = h->sims[k]->group_key()) bykey[key].push_back(k);
+    // launch groups: consecutive members of one key, about group_points grid
+    // points each; a group of one runs its own launches
+    std::vector<std::vector<size_t>> groups;
+    for (auto& kv : bykey) {
+        const long long pts = (long long)h->sims[kv.second[0]]->N * h->sims[kv.second[0]]->N;
+        const size_t cap = (size_t)std::min<long long>(h->sims[kv.second[0]]->max_group(),
+                                                       std::max(1LL, h->group_points / pts));
+        for (size_t i = 0; i < kv.second.size(); i += cap) {
+            std::vector<size_t> g(kv.second.begin() + i, kv.second.begin() + std::min(kv.second.size(), i + cap));
+            if (g.size() >= 2) groups.push_back(g);
+        }
+    }
+    h->grouped[ph].assign(n, 0);
+    h->group_launches[ph] = 0;
+    size_t ng = 0;
+    for (auto& g : groups) ng += g.size();
+    std::vector<unsigned char> host;
+    if (ng > 0) {
+        const size_t rb = h->sims[groups[0][0]]->batch_args_bytes();
+        host.assign(3 * ng * rb, 0);
+        size_t pos = 0;
+        for (auto& g : groups)
+            for (size_t k : g) {
+                for (int i = 0; i < 3; ++i) {
+                    const int e = h->sims[k]->fill_batch_args(i, host.data() + ((size_t)i * ng + pos) * rb);
+                    if (e) return e;
+                }
+                h->grouped[ph][k] = 1;
+                ++pos;
+            }
+        h->group_launches[ph] = 3 * 6 * (long long)groups.size();
+    }
     cudaGraph_t g = nullptr;
     if (cudaStreamBeginCapture(h->cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return CCMSAV_ECUDA;
     int r = fork_from(h, h->cap);
-    for (size_t k = 0; k < h->sims.size() && r == CCMSAV_OK; ++k) r = h->sims[k]->queue_steps_captured(3);
+    for (size_t k = 0; k < n && r == CCMSAV_OK; ++k)
+        if (!h->grouped[ph][k]) r = h->sims[k]->queue_steps_captured(3);
+    size_t pos = 0;
+    for (size_t gi = 0; gi < groups.size() && r == CCMSAV_OK; ++gi) {
+        ccm::SimBase* lead = h->sims[groups[gi][0]];
+        const size_t rb = lead->batch_args_bytes();
+        r = lead->queue_group_steps(host.data() + pos * rb, (int)groups[gi].size(), (int)ng, lead->stream());
+        pos += groups[gi].size();
+    }
     if (r == CCMSAV_OK) r = join_into(h, h->cap);
     const cudaError_t e = cudaStreamEndCapture(h->cap, &g);
     if (r != CCMSAV_OK || e != cudaSuccess || !g) { if (g) cudaGraphDestroy(g); return CCMSAV_ECUDA; }
@@ -94,7 +161,11 @@ int step_batched(ccmsav* h, int nsteps) {
             const int ph = h->sims[0]->phase();
             if (!h->bexec[ph] && capture_batch(h, ph) != CCMSAV_OK) { h->batch_failed = true; break; }
             if (cudaGraphLaunch(h->bexec[ph], h->stream) != cudaSuccess) return CCMSAV_ECUDA;
-            for (ccm::SimBase* s : h->sims) s->count_steps(3);
+            for (size_t k = 0; k < h->sims.size(); ++k) {
+                if (h->grouped[ph].size() == h->sims.size() && h->grouped[ph][k]) h->sims[k]->count_steps_grouped(3);
+                else h->sims[k]->count_steps(3);
+            }
+            h->extra_launches += h->group_launches[ph];
             nsteps -= 3;
         }
         if ((r = fork_from(h, h->stream))) return r;
@@ -280,31 +351,64 @@ int ccmsav_autotune(ccmsav_t* h, int steps, double* report) {
     const std::vector<ccm::TuneChoice> cand = ccm::tune_candidates(any_warp);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) r = CCMSAV_ECUDA;
-    double best = 1e300, dflt = 0.0;
-    size_t bi = 0;
     auto drop_batch = [&]() {
         for (int i = 0; i < 3; ++i) if (h->bexec[i]) { cudaGraphExecDestroy(h->bexec[i]); h->bexec[i] = nullptr; }
     };
-    for (size_t i = 0; i < cand.size() && !r; ++i) {
-        for (ccm::SimBase* s : h->sims) {
-            if ((r = s->tune_apply(cand[i].warp, cand[i].carveout)) || (r = s->tune_load())) break;
-        }
-        if (r) break;
+    // ms per batched step from the kept state (three warm-up steps, then k)
+    auto time_batch = [&](double& per) -> int {
+        int q;
+        for (ccm::SimBase* s : h->sims)
+            if ((q = s->tune_load())) return q;
         drop_batch();
-        if ((r = ccmsav_step(h, 3))) break;
-        if (cudaEventRecord(e0, h->stream) != cudaSuccess) { r = CCMSAV_ECUDA; break; }
-        if ((r = ccmsav_step(h, k))) break;
-        if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) { r = CCMSAV_ECUDA; break; }
-        if ((r = ccmsav_sync(h))) break;
+        h->batch_failed = false;
+        if ((q = ccmsav_step(h, 3))) return q;
+        if (cudaEventRecord(e0, h->stream) != cudaSuccess) return CCMSAV_ECUDA;
+        if ((q = ccmsav_step(h, k))) return q;
+        if (cudaEventRecord(e1, h->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) return CCMSAV_ECUDA;
+        if ((q = ccmsav_sync(h))) return q;
         float ms = 0.f;
         cudaEventElapsedTime(&ms, e0, e1);
-        const double per = ms / k;
+        per = ms / k;
+        return CCMSAV_OK;
+    };
+    double best = 1e300, dflt = 0.0;
+    size_t bi = 0;
+    for (size_t i = 0; i < cand.size() && !r; ++i) {
+        for (ccm::SimBase* s : h->sims)
+            if ((r = s->tune_apply(cand[i].warp, cand[i].carveout))) break;
+        double per = 0.0;
+        if (r || (r = time_batch(per))) break;
         if (i == 0) dflt = per;
         if (per < best) { best = per; bi = i; }
     }
+    if (bi != 0 && best > 0.98 * dflt) { bi = 0; best = dflt; }
+    // second stage, with the chosen schedule: the size of the launch groups
+    // (grid points per group; the handle's current value first)
+    bool groupable = false;
+    for (ccm::SimBase* s : h->sims) {
+        if (!r) r = s->tune_apply(cand[bi].warp, cand[bi].carveout);
+        groupable = groupable || s->group_key() != 0;
+    }
+    if (!r && groupable) {
+        const long long g0 = h->group_points;
+        std::vector<long long> gc{g0};
+        for (long long g : {0LL, 1LL << 17, 1LL << 18, 1LL << 19, 1LL << 20, 1LL << 21, 1LL << 22, 1LL << 26})
+            if (g != g0) gc.push_back(g);
+        double gbest = 1e300, gdflt = 0.0;
+        size_t gi = 0;
+        for (size_t i = 0; i < gc.size() && !r; ++i) {
+            h->group_points = gc[i];
+            double per = 0.0;
+            if ((r = time_batch(per))) break;
+            if (i == 0) gdflt = per;
+            if (per < gbest) { gbest = per; gi = i; }
+        }
+        if (gi != 0 && gbest > 0.98 * gdflt) { gi = 0; gbest = gdflt; }
+        h->group_points = gc[gi];
+        if (!r && gbest < best) best = gbest;
+    }
     if (e0) cudaEventDestroy(e0);
     if (e1) cudaEventDestroy(e1);
-    if (bi != 0 && best > 0.98 * dflt) { bi = 0; best = dflt; }
     for (ccm::SimBase* s : h->sims) {
         int e = r ? CCMSAV_OK : s->tune_record(cand[bi].warp, cand[bi].carveout, best, dflt);
         const int e2 = s->tune_load();
@@ -318,6 +422,18 @@ int ccmsav_autotune(ccmsav_t* h, int steps, double* report) {
             if ((r = h->sims[q]->autotune_report(report + 4 * q))) return r;
     return CCMSAV_OK;
 }
+
+int ccmsav_set_group_points(ccmsav_t* h, long long points) {
+    if (!h || points < 0) return CCMSAV_EINVAL;
+    int r = ccmsav_sync(h);
+    if (r) return r;
+    h->group_points = points;
+    for (cudaGraphExec_t& g : h->bexec) if (g) { cudaGraphExecDestroy(g); g = nullptr; }
+    h->batch_failed = false;
+    return CCMSAV_OK;
+}
+
+long long ccmsav_group_points(ccmsav_t* h) { return h ? h->group_points : -1; }
 
 int ccmsav_bounds_flag(ccmsav_t* h) {
     if (!h) return CCMSAV_EINVAL;

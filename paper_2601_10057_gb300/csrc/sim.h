@@ -64,6 +64,17 @@ public:
     virtual int autotune_report(double out[4]) = 0; // {warp path, carveout, best ms, default ms}
     // index-check flag of a bounds-checked build (-DCCMSAV_BOUNDS), read and cleared
     virtual int bounds_flag() = 0;
+    // grouped launches: the BDF2 steps of several simulations of the same
+    // line length from one launch per kernel (see BatchArgs in the kernels)
+    virtual int group_key() const = 0;                 // line length M, or 0: not groupable
+    virtual size_t batch_args_bytes() const = 0;       // size of one simulation's argument record
+    virtual int fill_batch_args(int i, void* rec) const = 0;   // record of the i-th step (0..2) from now
+    // queues three steps of the n simulations (2 <= n <= max_group()) whose
+    // host records (three blocks of `stride` records, one per step) start at
+    // recs; called on one member
+    virtual int max_group() const = 0;
+    virtual int queue_group_steps(const void* recs, int n, int stride, cudaStream_t s) = 0;
+    virtual void count_steps_grouped(int n3) = 0;      // host counters after grouped steps
     int N = 0;
 };
 

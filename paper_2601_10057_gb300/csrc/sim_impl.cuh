@@ -145,6 +145,84 @@ public:
     long long launches_per_step() const { return 6 + ((flags & CCMSAV_TRACK_ENERGY) ? 2 : 0); }
 
     void count_steps(int n3) override { steps_taken += n3; nlaunch += n3 * launches_per_step(); }
+    void count_steps_grouped(int n3) override { steps_taken += n3; }
+
+    // ---- grouped launches -------------------------------------------------
+    // FP32 warp path with one warp or less per line, no classical mode, no
+    // energy tracking: simulations of the same M share each kernel launch.
+    int group_key() const override {
+        if constexpr (std::is_same<T, float>::value)
+            if (warp_path && !classical && !(flags & CCMSAV_TRACK_ENERGY) && M >= 64 && M <= 2048) return M;
+        return 0;
+    }
+    size_t batch_args_bytes() const override { return sizeof(BatchArgs); }
+    int fill_batch_args(int i, void* rec) const override {
+        if constexpr (std::is_same<T, float>::value) {
+            if (i < 0 || i > 2 || !rec) return CCMSAV_EINVAL;
+            int c0 = cur, p0 = prev, s0 = spare;
+            for (int k = 0; k < i; ++k) { const int nw = s0; s0 = p0; p0 = c0; c0 = nw; }
+            StencilCoef<float> c;
+            SpecCoef sp;
+            SolveCoef so;
+            step_coefs(false, c, sp, so);
+            so.anchor = 1;
+            so.nb2 = N / wKC;
+            BatchArgs a;
+            a.phn = phi[c0]; a.pho = phi[p0]; a.psn = psi[c0]; a.pso = psi[p0];
+            a.phi_new = phi[s0]; a.psi_new = psi[s0];
+            a.bufA = reinterpret_cast<float*>(bufA); a.bufB = reinterpret_cast<float*>(bufB);
+            a.part1 = part1; a.part2 = part2; a.part3 = part3; a.sc = sc;
+            a.tw2 = tw2; a.twF = pair_tab(twF); a.twI = pair_tab(twI); a.evf = evf; a.evp = evp;
+            a.c = c;
+            a.sf = SpecCoefF{(float)sp.C1, (float)sp.C2, (float)sp.C3, (float)sp.Ct, (float)sp.lam};
+            a.so = so;
+            std::memcpy(rec, &a, sizeof a);
+            return CCMSAV_OK;
+        }
+        return CCMSAV_EINVAL;
+    }
+    int max_group() const override { return kMaxGroup; }
+    template <int MM> void group_launch(const GroupArgs<true>& ga, int n, cudaStream_t s) {
+        const int bst = g_st.x, brt = N / wRT, bcol = N / wKC, bcomb = N / wRT4;
+        const int birow = (2 * N + InvGeo<MM>::LINES - 1) / InvGeo<MM>::LINES;
+        k_stencil<float, true><<<dim3(bst * n, g_st.y), b_st, stencil_smem_bytes<float>(), s>>>(
+            nullptr, nullptr, nullptr, nullptr, nullptr, nullptr, N, StencilCoef<float>{}, ga, bst);
+        kw_rowdct_T<MM, true><<<dim3(brt * n, NF), kWarps * 32, wsm_rt, s>>>(nullptr, nullptr, nullptr, wf::PairTwTab{}, 0,
+                                                                         ga, brt);
+        kw_coldct_gram<MM, true><<<bcol * n, kWarps * 32, wsm_col, s>>>(nullptr, nullptr, nullptr, nullptr, wf::PairTwTab{},
+                                                                       nullptr, nullptr, SpecCoefF{}, ga, bcol);
+        k_solve<float2, true><<<kSolveBlocks * n, kSolveThreads, 0, s>>>(nullptr, 0, nullptr, 0, nullptr, nullptr,
+                                                                         SolveCoef{}, ga, kSolveBlocks);
+        kw_comb_icolT<MM, true><<<bcomb * n, kWarps * 32, wsm_comb, s>>>(nullptr, nullptr, nullptr, wf::PairTwTab{},
+                                                                        nullptr, nullptr, SpecCoefF{}, nullptr, 1, ga, bcomb);
+        kw_irow<MM, true><<<birow * n, InvGeo<MM>::WARPS * 32, wsm_irow, s>>>(nullptr, nullptr, nullptr, nullptr,
+            wf::PairTwTab{}, nullptr, nullptr, nullptr, nullptr, 0, nullptr, 1, ga, birow);
+    }
+    // recs: host records, three blocks of `stride` (one per step), of which
+    // this group's n are at the start of each block; copied into the launch
+    // parameters (so a stream capture keeps them with the graph)
+    int queue_group_steps(const void* recs, int n, int stride, cudaStream_t s) override {
+        if constexpr (std::is_same<T, float>::value) {
+            if (!recs || n < 2 || n > kMaxGroup || stride < n || group_key() == 0) return CCMSAV_EINVAL;
+            std::vector<GroupArgs<true>> ga(1);
+            for (int i = 0; i < 3; ++i) {
+                std::memcpy(ga[0].a, static_cast<const unsigned char*>(recs) + (size_t)i * stride * sizeof(BatchArgs),
+                            (size_t)n * sizeof(BatchArgs));
+                switch (M) {
+                    case 64: group_launch<64>(ga[0], n, s); break;
+                    case 128: group_launch<128>(ga[0], n, s); break;
+                    case 256: group_launch<256>(ga[0], n, s); break;
+                    case 512: group_launch<512>(ga[0], n, s); break;
+                    case 1024: group_launch<1024>(ga[0], n, s); break;
+                    case 2048: group_launch<2048>(ga[0], n, s); break;
+                    default: return CCMSAV_EINVAL;
+                }
+            }
+            CCM_CUDA(cudaGetLastError());
+            return CCMSAV_OK;
+        }
+        return CCMSAV_EINVAL;
+    }
     cudaStream_t stream() const override { return st; }
     int phase() const override { return cur; }
     bool batchable() const override { return have_state && !poisoned && steps_taken > 0 && !prof && !classical; }
@@ -335,11 +413,15 @@ public:
         // per-block opt-in limit minus the kernel's static shared memory); the
         // attribute is per kernel, so it must not depend on this simulation's N
         // FP32: 72 % of 228 KB, rounded up by the driver to the 196 KB
-        // configuration: four 46 KB tiles per SM and 60 KB of L1 for the halo
-        // re-reads (faster than 228 KB with a 28 KB L1, and than 164 KB with
-        // three tiles); FP64 tiles are twice the size
+        // configuration: three 55.5 KB tiles per SM (the low part of phi_bar
+        // is a second two-halo tile) and 60 KB of L1 for the halo re-reads
+        // (faster than four tiles at 228 KB with a 28 KB L1); FP64 tiles are
+        // twice the size of the FP32 ones without the low part
         if (set_smem_limit((const void*)k_stencil<T>, stencil_smem_bytes<T>(), std::is_same<T, float>::value ? 72 : 100))
             return CCMSAV_ECUDA;
+        if constexpr (std::is_same<T, float>::value)
+            if (set_smem_limit((const void*)k_stencil<float, true>, stencil_smem_bytes<float>(), 72))
+                return CCMSAV_ECUDA;
         if (set_smem_limit((const void*)k_rowdct_T<T>, sm_rt) || set_smem_limit((const void*)k_coldct_gram<T>, sm_col) ||
             set_smem_limit((const void*)k_comb_icolT<T>, sm_comb) || set_smem_limit((const void*)k_irow<T>, sm_irow))
             return CCMSAV_ECUDA;
@@ -456,6 +538,11 @@ public:
             cudaFuncSetAttribute(coldct_fn<MM>(), cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess ||
             cudaFuncSetAttribute((const void*)kw_comb_icolT<MM>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess)
             return CCMSAV_ECUDA;
+        if constexpr (WGeo<MM>::WPL == 1)
+            if (cudaFuncSetAttribute((const void*)kw_rowdct_T<MM, true>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess ||
+                cudaFuncSetAttribute((const void*)kw_coldct_gram<MM, true>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess ||
+                cudaFuncSetAttribute((const void*)kw_comb_icolT<MM, true>, cudaFuncAttributePreferredSharedMemoryCarveout, c) != cudaSuccess)
+                return CCMSAV_ECUDA;
         return CCMSAV_OK;
     }
     int apply_carveout(int c) {
@@ -658,6 +745,13 @@ public:
         if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt, kRowCarveout) || set_smem_limit(coldct_fn<MM>(), wsm_col, kColCarveout) ||
             set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb, kCombCarveout) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
             return CCMSAV_ECUDA;
+        // the grouped-launch instantiations (one warp or less per line)
+        if constexpr (WGeo<MM>::WPL == 1)
+            if (set_smem_limit((const void*)kw_rowdct_T<MM, true>, wsm_rt, kRowCarveout) ||
+                set_smem_limit((const void*)kw_coldct_gram<MM, true>, wsm_col, kColCarveout) ||
+                set_smem_limit((const void*)kw_comb_icolT<MM, true>, wsm_comb, kCombCarveout) ||
+                set_smem_limit((const void*)kw_irow<MM, true>, wsm_irow))
+                return CCMSAV_ECUDA;
         // L2 prefetch one residency ahead only where few CTAs fit per SM (one
         // at N = 4096); with three per SM (N <= 2048) it evicts rows before
         // their use and costs time (73.3 vs 71.5 us at N = 2048)
@@ -758,13 +852,14 @@ public:
         const float* fin = reinterpret_cast<const float*>(bufA);
         float* fB = reinterpret_cast<float*>(bufB);
         const cplx<float>* t2 = tw2;
-        kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, t2, pair_tab(twF), ahead_rt);
+        kw_rowdct_T<MM><<<dim3(N / wRT, NF), kWarps * 32, wsm_rt, st>>>(fin, fB, t2, pair_tab(twF), ahead_rt, GroupArgs<false>{}, 0);
         mark(1);
         if constexpr (WGeo<MM>::WPL > 1)
             kw_coldct_gram_split<MM><<<dim3(N, 2), kSplitWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2,
                                                                                   t2, pair_tab(twF), evf, evp, sf);
         else
-            kw_coldct_gram<MM><<<N / wKC, kWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2, t2, pair_tab(twF), evf, evp, sf);
+            kw_coldct_gram<MM><<<N / wKC, kWarps * 32, wsm_col, st>>>(fB, reinterpret_cast<float*>(bufA), part2, t2, pair_tab(twF), evf, evp, sf,
+                                                                     GroupArgs<false>{}, 0);
         mark(2);
     }
     int bdf1_launch = 0;
@@ -772,14 +867,14 @@ public:
     void launch_warp_inverse(const SpecCoef& s, int anchor) {
         SpecCoefF sf{(float)s.C1, (float)s.C2, (float)s.C3, (float)s.Ct, (float)s.lam};
         kw_comb_icolT<MM><<<N / wRT4, kWarps * 32, wsm_comb, st>>>(reinterpret_cast<const float*>(bufA),
-            reinterpret_cast<float*>(bufB), tw2, pair_tab(twI), evf, evp, sf, sc, anchor);
+            reinterpret_cast<float*>(bufB), tw2, pair_tab(twI), evf, evp, sf, sc, anchor, GroupArgs<false>{}, 0);
         mark(4);
         kw_irow<MM><<<(2 * N + InvGeo<MM>::LINES - 1) / InvGeo<MM>::LINES, InvGeo<MM>::WARPS * 32, wsm_irow, st>>>(
             reinterpret_cast<const float*>(bufB),
             reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), tw2, pair_tab(twI),
             reinterpret_cast<const float*>(phi[cur]), reinterpret_cast<const float*>(phi[prev]),
             reinterpret_cast<const float*>(psi[cur]), reinterpret_cast<const float*>(psi[prev]),
-            bdf1_launch, sc, anchor);
+            bdf1_launch, sc, anchor, GroupArgs<false>{}, 0);
         mark(5);
     }
     void warp_forward(const SpecCoef& s, int anchor) {
@@ -937,10 +1032,9 @@ public:
         return CCMSAV_OK;
     }
 
-    int queue_one_step() {
-        const bool bdf1 = (steps_taken == 0) || (flags & CCMSAV_BDF1_ALWAYS);
+    // Coefficients of one step's kernels (BDF1 start step or BDF2).
+    void step_coefs(bool bdf1, StencilCoef<T>& c, SpecCoef& s, SolveCoef& so) const {
         const double dt = p.dt;
-        StencilCoef<T> c;
         c.bdf1 = bdf1 ? 1 : 0;
         c.inv_h = (T)(1.0 / h()); c.inv_h2 = (T)(1.0 / (h() * h()));
         c.eps = (T)p.eps; c.inv_eps = (T)(1.0 / p.eps); c.inv_eps2 = (T)(1.0 / (p.eps * p.eps));
@@ -952,13 +1046,11 @@ public:
         c.gin = (T)p.gamma_in; c.gout = (T)p.gamma_out; c.hgin = (T)(0.5 * p.gamma_in); c.hgout = (T)(0.5 * p.gamma_out);
         c.psin = (T)p.psi_in; c.psout = (T)p.psi_out;
         c.bin = (T)p.beta_in; c.bout = (T)p.beta_out; c.M0 = (T)p.M0;
-        SpecCoef s;
         const double a = bdf1 ? 1.0 / dt : 1.5 / dt;
         s.C1 = a + p.M_phi * p.gamma_surf * 3.0 * M_SQRT2 * p.beta / (4.0 * p.eps);
         s.C2 = p.M_phi * (p.gamma_surf * 3.0 * M_SQRT2 * p.eps / 4.0 + p.theta);
         s.C3 = p.M_phi * p.gamma_bend * 3.0 * M_SQRT2 * p.eps / 8.0;
         s.Ct = a; s.lam = p.lam;
-        SolveCoef so;
         so.h2 = h() * h();
         so.cgs = p.M_phi * p.gamma_surf * 3.0 * M_SQRT2 / 2.0;
         so.cga = p.M_phi * p.gamma_area;
@@ -967,12 +1059,22 @@ public:
         so.bdf1 = bdf1 ? 1 : 0;
         so.nb1 = nb1; so.nb2 = N;
         so.inv_NN = 1.0 / (double)NN;
+    }
+
+    int queue_one_step() {
+        const bool bdf1 = (steps_taken == 0) || (flags & CCMSAV_BDF1_ALWAYS);
+        const double dt = p.dt;
+        StencilCoef<T> c;
+        SpecCoef s;
+        SolveCoef so;
+        step_coefs(bdf1, c, s, so);
         const int anchor = (sizeof(T) == sizeof(float)) ? 1 : 0;
         so.anchor = anchor;
 
         if (prof && ev_used + 16 > 4096) { int r = profile_flush(); if (r) return r; }
         mark(-1);
-        k_stencil<T><<<g_st, b_st, stencil_smem_bytes<T>(), st>>>(phi[cur], phi[prev], psi[cur], psi[prev], bufA, part1, N, c);
+        k_stencil<T><<<g_st, b_st, stencil_smem_bytes<T>(), st>>>(phi[cur], phi[prev], psi[cur], psi[prev], bufA, part1, N, c,
+                                                              GroupArgs<false>{}, 0);
         mark(0);
         if (classical) {
             int r = queue_classical_ch(bdf1);
@@ -995,7 +1097,8 @@ public:
                 ++nlaunch;
             }
             k_solve<P><<<kSolveBlocks, kSolveThreads, 0, st>>>(reinterpret_cast<const P*>(part1), so.nb1,
-                                                               reinterpret_cast<const P*>(part2), so.nb2, part3, sc, so);
+                                                               reinterpret_cast<const P*>(part2), so.nb2, part3, sc, so,
+                                                               GroupArgs<false>{}, 0);
         }
         mark(3);
         if (warp_path) {

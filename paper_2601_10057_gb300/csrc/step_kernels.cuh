@@ -45,6 +45,7 @@
 #pragma once
 #include <type_traits>
 #include "dct_device.cuh"
+#include "warp_fft.cuh"
 #include "bounds.cuh"
 
 namespace ccm {
@@ -95,6 +96,41 @@ struct SolveCoef {
     int anchor;                   // FP32 path: compute the psi mean correction
     int nb1, nb2;                 // number of partial rows
 };
+
+struct SpecCoefF {        // FP32 copy of SpecCoef for the FP32 spectral kernels
+    float C1, C2, C3, Ct, lam;
+};
+
+// Grouped launches (FP32 warp path): one launch of a step kernel serves
+// several simulations of the same N.  blockIdx.x = simulation * bps + the
+// block index the kernel has in a launch of its own (bps = that launch's
+// gridDim.x), and the kernel takes from ga.a[simulation] the pointers and
+// coefficients it otherwise receives as arguments.  Each simulation's blocks
+// do exactly what its own launch does, so the results are the same bits.
+// The records travel in the kernel parameters (__grid_constant__: read in
+// place from the parameter bank, with a CTA-uniform index, so they cost no
+// more registers than ordinary arguments); the kernels take a template flag
+// GRP, and without it ga is an empty struct and the code is that of the
+// plain kernel.
+struct BatchArgs {
+    const float* phn; const float* pho; const float* psn; const float* pso;   // levels n, n-1
+    float* phi_new; float* psi_new;                                           // level n+1
+    float* bufA; float* bufB;                                                 // the two field buffers
+    double* part1; double* part2; double* part3;                              // partial rows, solve slices
+    DevScalars* sc;
+    const cplx<float>* tw2;                                                   // four-step twiddles
+    wf::PairTwTab twF, twI;                                                   // DCT pair twiddles
+    const float* evf; const float4* evp;                                      // FP32 eigenvalues
+    StencilCoef<float> c;
+    SpecCoefF sf;
+    SolveCoef so;
+};
+
+// Simulations per grouped launch: 64 records of 328 bytes stay well inside
+// the 32764 bytes of kernel parameters.
+constexpr int kMaxGroup = 64;
+template <bool GRP> struct GroupArgs { int unused = 0; };
+template <> struct GroupArgs<true> { BatchArgs a[kMaxGroup]; };
 
 // ------------------------------------------------------------------ helpers
 template <typename T> __device__ __forceinline__ void sincospi_(T x, T* s, T* c);
@@ -372,11 +408,12 @@ __device__ __forceinline__ double bar_add(double a, double b, double du, double 
 constexpr int TX = 64, TY = 4, TYB = 32;
 template <typename T> constexpr bool kBarLo = std::is_same<T, float>::value;
 
-template <typename T>
+template <typename T, bool GRP = false>
 __global__ void __launch_bounds__(TX * TY)
 k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
           const T* __restrict__ psn, const T* __restrict__ pso,
-          T* __restrict__ out, double* __restrict__ part, int N, StencilCoef<T> c) {
+          T* __restrict__ out, double* __restrict__ part, int N, StencilCoef<T> c,
+          const __grid_constant__ GroupArgs<GRP> ga, int bps) {
     extern __shared__ __align__(16) unsigned char smraw[];
     constexpr int W2 = TX + 4, W1 = TX + 2, H1 = TYB + 2;
     T* sbar = reinterpret_cast<T*>(smraw);              // [TYB+4][W2]
@@ -389,7 +426,16 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
     __shared__ double sred[(TX * TY / 32) * 4];
     __shared__ double smean[2][TX * TY / 32];
     __shared__ T smin[TX * TY / 32];
-    const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TYB;
+    int bx = blockIdx.x, gx = gridDim.x;
+    if constexpr (GRP) {          // grouped launch (FP32)
+        static_assert(std::is_same<T, float>::value, "grouped launches are FP32");
+        const int sim = blockIdx.x / bps;
+        bx = blockIdx.x - sim * bps;
+        gx = bps;
+        const BatchArgs& A = ga.a[sim];
+        phn = A.phn; pho = A.pho; psn = A.psn; pso = A.pso; out = A.bufA; part = A.part1; c = A.c;
+    }
+    const int i0 = bx * TX, j0 = blockIdx.y * TYB;
     const int tid = threadIdx.y * TX + threadIdx.x;
     // with d = u^n - u^{n-1} (exact for nearby values): u* = u^n + d,
     // u_bar = u^n + d/3, u_bar - u* = -2d/3 (BDF1: u* = u_bar = u^n)
@@ -546,7 +592,7 @@ k_stencil(const T* __restrict__ phn, const T* __restrict__ pho,
             if (gj + 1 < N) mm = min(mm, mN);
         }
     }
-    const size_t prow_i = (size_t)(blockIdx.y * gridDim.x + blockIdx.x) * NRED1;
+    const size_t prow_i = (size_t)(blockIdx.y * gx + bx) * NRED1;
     const int lane = tid & 31, wp = tid >> 5;
     const T w0 = warp_sum(acc0), w1 = warp_sum(acc1), w2 = warp_sum(acc2);
     mm = warp_min(mm);
@@ -794,10 +840,11 @@ __device__ __forceinline__ void solve_slice(int n, int b, int& r0, int& cnt) {
     cnt = min(n, r0 + per) - r0;
 }
 
-template <typename P>
+template <typename P, bool GRP = false>
 __global__ void __launch_bounds__(kSolveThreads)
 k_solve(const P* __restrict__ p1, int nb1, const P* __restrict__ p2, int nb2,
-        double* __restrict__ slices, DevScalars* sc, SolveCoef co) {
+        double* __restrict__ slices, DevScalars* sc, SolveCoef co,
+        const __grid_constant__ GroupArgs<GRP> ga, int bps) {
     constexpr int NR = NRQ;
     constexpr unsigned FULL = 0xffffffffu;
     __shared__ double fin_[NR];
@@ -805,6 +852,16 @@ k_solve(const P* __restrict__ p1, int nb1, const P* __restrict__ p2, int nb2,
     __shared__ double s_state[10];       // V U W Z at n and n-1, conserved mean, steps
     __shared__ int s_status, is_last;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int bx = blockIdx.x, gx = gridDim.x;
+    if constexpr (GRP) {                 // grouped launch (FP32)
+        static_assert(std::is_same<P, float2>::value, "grouped launches are FP32");
+        const int sim = blockIdx.x / bps;
+        bx = blockIdx.x - sim * bps;
+        gx = bps;
+        const BatchArgs& A = ga.a[sim];
+        p1 = reinterpret_cast<const P*>(A.part1); p2 = reinterpret_cast<const P*>(A.part2);
+        nb1 = A.so.nb1; nb2 = A.so.nb2; slices = A.part3; sc = A.sc; co = A.so;
+    }
     if (threadIdx.x == 32) {             // the scalar state, read while warp 0 streams
         s_state[0] = sc->V; s_state[1] = sc->U; s_state[2] = sc->W; s_state[3] = sc->Z;
         s_state[4] = sc->Vo; s_state[5] = sc->Uo; s_state[6] = sc->Wo; s_state[7] = sc->Zo;
@@ -817,7 +874,7 @@ k_solve(const P* __restrict__ p1, int nb1, const P* __restrict__ p2, int nb2,
         const P* col = in1 ? p1 + c : p2 + (c - NRED1);
         const int stride = in1 ? NRED1 : NRED2;
         int r0, cnt;
-        solve_slice(in1 ? nb1 : nb2, blockIdx.x, r0, cnt);
+        solve_slice(in1 ? nb1 : nb2, bx, r0, cnt);
         double acc = 0.0;
         long long kmin = 0x7fffffffffffffffLL;
         if constexpr (std::is_same<P, float2>::value) {
@@ -849,11 +906,11 @@ k_solve(const P* __restrict__ p1, int nb1, const P* __restrict__ p2, int nb2,
                 }
             }
         }
-        slices[(size_t)blockIdx.x * NR + c] = (c == kSolveMinCol) ? __longlong_as_double(kmin) : acc;
+        slices[(size_t)bx * NR + c] = (c == kSolveMinCol) ? __longlong_as_double(kmin) : acc;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) is_last = atomicAdd(&sc->solve_arrivals, 1u) == gridDim.x - 1;
+    if (threadIdx.x == 0) is_last = atomicAdd(&sc->solve_arrivals, 1u) == (unsigned)gx - 1;
     __syncthreads();
     if (!is_last) return;
     __threadfence();

@@ -15,10 +15,6 @@
 
 namespace ccm {
 
-struct SpecCoefF {        // FP32 copy of SpecCoef for the FP32 spectral kernels
-    float C1, C2, C3, Ct, lam;
-};
-
 constexpr int kWarps = 8;
 
 // Exact (double-float) sum over the G lanes of one line: inside the warp for
@@ -75,16 +71,24 @@ template <int M> struct WGeo {
 // SLOTS rows of field blockIdx.y per CTA (one line per lane group).  The
 // post-processed DCT row replaces the line's complex buffer in place, so the
 // buffers double as the staging area of the transposed write.
-template <int M>
+template <int M, bool GRP = false>
 __global__ void __launch_bounds__(kWarps * 32, M <= 1024 ? 3 : 1)
 kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
-            const cplx<float>* __restrict__ tw2, wf::PairTwTab twF, int ahead) {
+            const cplx<float>* __restrict__ tw2, wf::PairTwTab twF, int ahead,
+            const __grid_constant__ GroupArgs<GRP> ga, int bps) {
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS, NP = (M / 2 + G) / G;
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
-    const int f = blockIdx.y, y0 = blockIdx.x * RT;
+    int bx = blockIdx.x;
+    if constexpr (GRP) {          // grouped launch (no prefetch ahead)
+        const int sim = blockIdx.x / bps;
+        bx = blockIdx.x - sim * bps;
+        const BatchArgs& A = ga.a[sim];
+        in = A.bufA; out = A.bufB; tw2 = A.tw2; twF = A.twF; ahead = 0;
+    }
+    const int f = blockIdx.y, y0 = bx * RT;
     {   // rows of the CTA one residency ahead
         const int t = blockIdx.y * gridDim.x + blockIdx.x + ahead;
         if (ahead > 0 && t < (int)(gridDim.x * gridDim.y) && threadIdx.x < RT)
@@ -148,17 +152,25 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
 }
 
 // ------------------------------------------------------------------ kw_coldct_gram
-template <int M>
+template <int M, bool GRP = false>
 __global__ void __launch_bounds__(kWarps * 32, M <= 1024 ? 3 : 1)
 kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* __restrict__ part,
                const cplx<float>* __restrict__ tw2, wf::PairTwTab twF,
-               const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc) {
+               const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc,
+               const __grid_constant__ GroupArgs<GRP> ga, int bps) {
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, KC = Gm::SLOTS / NF;
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
-    const int kx0 = blockIdx.x * KC;
+    int bx = blockIdx.x;
+    if constexpr (GRP) {          // grouped launch
+        const int sim = blockIdx.x / bps;
+        bx = blockIdx.x - sim * bps;
+        const BatchArgs& A = ga.a[sim];
+        in = A.bufB; spec = A.bufA; part = A.part2; tw2 = A.tw2; twF = A.twF; evf = A.evf; evp = A.evp; sc = A.sf;
+    }
+    const int kx0 = bx * KC;
     static_assert(G <= 32, "lines of one warp at most; longer lines take kw_coldct_gram_split");
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     int n2, slot;                                        // line = (kc, field)
@@ -242,7 +254,7 @@ kw_coldct_gram(const float* __restrict__ in, float* __restrict__ spec, double* _
         }
     }
     __syncthreads();       // the line buffers are free: their start holds the block reduction
-    block_sum_store_part<NRED2, float>(acc, reinterpret_cast<float2*>(part) + (size_t)blockIdx.x * NRED2,
+    block_sum_store_part<NRED2, float>(acc, reinterpret_cast<float2*>(part) + (size_t)bx * NRED2,
                                        reinterpret_cast<double*>(smraw));
 }
 
@@ -347,18 +359,26 @@ kw_coldct_gram_split(const float* __restrict__ in, float* __restrict__ spec, dou
 // Phase 1 (all threads): gather the spectra, combine, divide, pre-process
 // into the line buffers.  Phase 2 (per line): inverse four-step FFT and
 // unpack in place.  Phase 3: transposed write from the buffers.
-template <int M>
+template <int M, bool GRP = false>
 __global__ void __launch_bounds__(kWarps * 32)
 kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
               const cplx<float>* __restrict__ tw2, wf::PairTwTab twI,
               const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc,
-              DevScalars* __restrict__ dsc, int anchor_mass) {
+              DevScalars* __restrict__ dsc, int anchor_mass,
+              const __grid_constant__ GroupArgs<GRP> ga, int bps) {
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS / 2, NU = (M / 2 + G - 1) / G;
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
-    const int kx0 = blockIdx.x * RT;
+    int bx = blockIdx.x;
+    if constexpr (GRP) {          // grouped launch
+        const int sim = blockIdx.x / bps;
+        bx = blockIdx.x - sim * bps;
+        const BatchArgs& A = ga.a[sim];
+        spec = A.bufA; out = A.bufB; tw2 = A.tw2; twI = A.twI; evf = A.evf; evp = A.evp; sc = A.sf; dsc = A.sc;
+    }
+    const int kx0 = bx * RT;
     const float aS = (float)dsc->alpha[0], aH = (float)dsc->alpha[1], aQ = (float)dsc->alpha[2];
     const float aK = (float)dsc->alpha[3], aL = (float)dsc->alpha[4];
     constexpr int PAIRS = M / 2 + 1;
@@ -493,20 +513,29 @@ template <int M> struct InvGeo {
     static constexpr size_t smem_bytes() { return (size_t)LINES * BUF * sizeof(cplx<float>); }
 };
 
-template <int M>
+template <int M, bool GRP = false>
 __global__ void __launch_bounds__(inv_warps<M>() * 32, inv_min_ctas<M>())
 kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __restrict__ psi_new,
         const cplx<float>* __restrict__ tw2, wf::PairTwTab twI,
         const float* __restrict__ phn, const float* __restrict__ pho,
         const float* __restrict__ psn, const float* __restrict__ pso, int bdf1,
-        const DevScalars* __restrict__ dsc, int anchor_mass) {
+        const DevScalars* __restrict__ dsc, int anchor_mass,
+        const __grid_constant__ GroupArgs<GRP> ga, int bps) {
     using Gm = WGeo<M>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, L = InvGeo<M>::LINES, NU = (M / 2 + G - 1) / G;
+    int bx = blockIdx.x;
+    if constexpr (GRP) {          // grouped launch
+        const int sim = blockIdx.x / bps;
+        bx = blockIdx.x - sim * bps;
+        const BatchArgs& A = ga.a[sim];
+        in = A.bufB; phi_new = A.phi_new; psi_new = A.psi_new; tw2 = A.tw2; twI = A.twI;
+        phn = A.phn; pho = A.pho; psn = A.psn; pso = A.pso; dsc = A.sc;
+    }
     const uint32_t step = (uint32_t)dsc->steps;         // dither key (graph replays read it here)
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
-    const int l0 = blockIdx.x * L;                       // first line of this CTA
+    const int l0 = bx * L;                               // first line of this CTA
     constexpr int PAIRS = M / 2 + 1;
     constexpr int UNR = M >= 2048 ? 8 : 4;    // loads in flight: 8 at 64 values per lane (12 warps per SM)
 #pragma unroll UNR

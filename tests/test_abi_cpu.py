@@ -44,6 +44,8 @@ def test_strerror_and_null_handles(lib):
     assert cc.ccmsav_step(None, 1) == cc.CCMSAV_EINVAL
     assert cc.ccmsav_sync(None) == cc.CCMSAV_EINVAL
     assert cc.ccmsav_grid_size(None, 0) == cc.CCMSAV_EINVAL
+    assert cc.ccmsav_set_group_points(None, 1 << 20) == cc.CCMSAV_EINVAL
+    assert cc.ccmsav_group_points(None) == -1
     cc.ccmsav_destroy(None)
 
 

@@ -349,6 +349,38 @@ def test_batched_graph_steps_match_single_runs(caller_stream):
     sim.close()
 
 
+def test_grouped_launches_match_single_runs():
+    """FP32 simulations of the same N share each kernel launch of the batch
+    graph (three at N = 128, two at N = 256, with different parameters and
+    states); an N = 64 simulation (block-FFT kernels) runs its own launches
+    beside them.  The launch count shows the grouping (six launches per step
+    per group and per ungrouped simulation) and every simulation ends
+    bit-identical to a run of its own."""
+    ws = [I.workload("one_vesicle", N=128, dt=1e-5), I.workload("ellipse_shrink", N=128),
+          I.one_vesicle_circle(N=128, seed=77, dt=2e-5, precision="fp32", ratio=0.8),
+          I.workload("one_vesicle", N=256, dt=1e-5), I.workload("ellipse_shrink", N=256),
+          I.workload("one_vesicle", N=64, dt=1e-5)]
+    sim = cc.Simulation(None, [w.N for w in ws], per_sim=[w.params for w in ws], precision="fp32")
+    for k, w in enumerate(ws):
+        sim.set_state(w.phi0, w.psi0, sim=k)
+    sim.step(1)
+    l0 = sim.launches()
+    sim.step(12)
+    sim.sync()
+    assert sim.launches() - l0 == 12 * 6 * 3, sim.launches() - l0   # groups N = 128, 256 and the N = 64 run
+    for k, w in enumerate(ws):
+        phi, psi = sim.state(sim=k)
+        solo = cc.Simulation(w.params, w.N, precision="fp32")
+        solo.set_state(w.phi0, w.psi0)
+        solo.step(13)
+        phi1, psi1 = solo.state()
+        a1, a2 = sim.aux(sim=k), solo.aux()
+        solo.close()
+        assert np.array_equal(phi, phi1) and np.array_equal(psi, psi1), f"simulation {k} (N={w.N})"
+        assert np.array_equal(a1, a2), f"simulation {k} scalars"
+    sim.close()
+
+
 _FP32_1000 = {}
 
 
@@ -546,6 +578,7 @@ def test_autotune_keeps_state_and_records_schedule():
         assert np.array_equal(sim.aux(sim=k)[:10], before[k][3][:10])
     assert rep.shape == (3, 4) and all(r[1] in (58, 72, 100) for r in rep)
     assert rep[0][0] == rep[2][0] and rep[0][1] == rep[2][1]          # same size, same schedule
+    assert sim.group_points() in {0, 1 << 26} | {1 << q for q in range(17, 23)}, sim.group_points()
     assert all(r[2] > 0 and r[3] > 0 for r in rep[:2])
     sim.step(5)
     for k, w in enumerate(ws):
