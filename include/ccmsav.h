@@ -301,10 +301,9 @@ int ccmsav_pcg_stats(ccmsav_t* h, int sim, double out[4]);
  * Returns CCMSAV_ECUDA if a launch, the copy or the synchronisation fails.
  * Scratch is a fixed array of 1185 doubles (under 10 KB, whatever N is)
  * compiled into the library; every GPU that loads the library holds it until
- * the process exits.  The first call on a device looks up that array's
- * device address (with the device current) and keeps it; after
- * cudaDeviceReset() on that device the function must not be called there
- * again in the same process.  All calls share the array: calls whose work
+ * the process exits.  Each call looks up that array's device address for
+ * the current device and context (nothing is cached across calls).  All
+ * calls share the array: calls whose work
  * overlaps on the GPU (different streams or host threads) race and must be
  * serialised by the caller. */
 int ccmsav_mass_noalloc(const void* psi, int N, int precision, double L,

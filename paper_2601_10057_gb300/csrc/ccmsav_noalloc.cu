@@ -14,16 +14,14 @@
 //
 // The array's name, used in host code, is only a host-side stand-in for the
 // device symbol: a kernel handed it would fault or, where the GPU can reach
-// host memory, silently use the wrong memory.  So the first call on each
-// device looks up the real device address with cudaGetSymbolAddress (with
-// that device current) and keeps it for later calls on that device.  The
-// address belongs to the device's primary context: after cudaDeviceReset()
-// on a device, this entry point must not be called on it again in the same
-// process.  All calls share the array and it keeps the last call's contents:
+// host memory, silently use the wrong memory.  So every call looks up the
+// real device address with cudaGetSymbolAddress for the current device and
+// context (a lookup, not an allocation; nothing is cached, so a device reset
+// between calls leaves no stale address behind).  All calls share the array
+// and it keeps the last call's contents:
 // every slot a call reads is written earlier in the same call, so nothing
 // needs clearing, but calls whose work overlaps on the GPU (other streams,
 // other host threads) race on it.
-#include <mutex>
 #include <cuda_runtime.h>
 #include "../../include/ccmsav.h"
 
@@ -32,12 +30,9 @@ namespace {
 constexpr int kBlocks = 1184;                 // fixed reduction grid (8 blocks per SM on 148+ SMs)
 constexpr int kThreads = 256;
 constexpr int kScratchDoubles = kBlocks + 1;  // block partials, then the final sum
-constexpr int kMaxDevices = 64;
 
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
-std::mutex g_mu;
-double* g_scratch_dev[kMaxDevices] = {};
 
 // FP64 block sum in a fixed order (warp shuffles, then warps in order).
 __device__ __forceinline__ double block_sum(double v, double* sm) {
@@ -79,19 +74,9 @@ extern "C" int ccmsav_mass_noalloc(const void* psi, int N, int precision, double
     if (N < 1 || N > CCMSAV_NOALLOC_MAX_N) return CCMSAV_EINVAL;
     if (precision != CCMSAV_FP64 && precision != CCMSAV_FP32_BULK) return CCMSAV_EINVAL;
     if (!(L > 0.0) || !(L < 1e300)) return CCMSAV_EINVAL;
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return CCMSAV_ECUDA;
-    if (dev < 0 || dev >= kMaxDevices) return CCMSAV_ECUDA;
-    double* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_mu);
-        if (!g_scratch_dev[dev]) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CCMSAV_ECUDA;
-            g_scratch_dev[dev] = static_cast<double*>(p);
-        }
-        scratch = g_scratch_dev[dev];
-    }
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return CCMSAV_ECUDA;
+    double* scratch = static_cast<double*>(p);
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)N * N;
     int nb = (int)((n + kThreads - 1) / kThreads);

@@ -536,6 +536,20 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
     const int l0 = bx * L;                               // first line of this CTA
+    if constexpr (M == 2048) {
+        // the levels of the final update, into L2 while the lines are
+        // transformed (three 4-line CTAs per SM leave this kernel short of
+        // loads in flight: 396 -> 375 us at N = 4096; at M = 4096 it costs
+        // time, 1450 -> 1475 us, and at M = 1024 it did too, 41 -> 48 us)
+        if (threadIdx.x < 2 * L) {
+            const int gq = l0 + (threadIdx.x >> 1);
+            if (gq < 2 * N) {
+                const int f = gq & 1;
+                const float* lv = (threadIdx.x & 1) ? (f ? pso : pho) : (f ? psn : phn);
+                prefetch_l2(lv + (size_t)(gq >> 1) * N, N * sizeof(float));
+            }
+        }
+    }
     constexpr int PAIRS = M / 2 + 1;
     constexpr int UNR = M >= 2048 ? 8 : 4;    // loads in flight: 8 at 64 values per lane (12 warps per SM)
 #pragma unroll UNR
