@@ -207,7 +207,9 @@ import json, sys, time
 sys.path.insert(0, sys.argv[1])
 from oracle import ccmsav_oracle as O
 from paper_2601_10057_gb300 import inputs as I
-w = I.three_vesicles(N=int(sys.argv[2]), seed=int(sys.argv[3]))
+kind = sys.argv[5] if len(sys.argv) > 5 else "three_vesicles"
+w = (I.three_vesicles(N=int(sys.argv[2]), seed=int(sys.argv[3])) if kind == "three_vesicles"
+     else I.workload(kind, N=int(sys.argv[2])))
 seconds = float(sys.argv[4])
 m = O.Model.from_params(w.N, w.params)
 s = O.step(O.initial_state(w.phi0, w.psi0, m), m)   # the BDF1 start step, untimed
@@ -222,14 +224,14 @@ print(json.dumps({"value": w.N * w.N * n / el, "steps": n, "seconds": el}))
 """
 
 
-def cpu_oracle_sample(N, seed, seconds, threads=None):
+def cpu_oracle_sample(N, seed, seconds, threads=None, kind="three_vesicles"):
     """Time the FP64 oracle (as it stands) on the host cores in a child
     process (no GPU use): all cores, or `threads` BLAS/OpenMP threads."""
     env = dict(os.environ)
     if threads:
         for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS"):
             env[k] = str(threads)
-    r = subprocess.run([sys.executable, "-c", ORACLE_SAMPLE, ROOT, str(N), str(seed), str(seconds)],
+    r = subprocess.run([sys.executable, "-c", ORACLE_SAMPLE, ROOT, str(N), str(seed), str(seconds), kind],
                        capture_output=True, text=True, env=env, timeout=20 * seconds + 600)
     if r.returncode != 0:
         raise RuntimeError(r.stderr[-2000:])
@@ -627,6 +629,17 @@ def run_ours(args, world, rank, local):
                               "sample": f"{one['steps']} BDF2 step(s), {one['seconds']:.1f} s, "
                                         "OPENBLAS_NUM_THREADS=OMP_NUM_THREADS=1"},
                "complexity": "O(N^3) per 2D transform (cosine-matrix DCT), 14 one-way transforms per step"}
+        # the oracle at the small configurations' sizes too (where it runs whole workloads)
+        per = {}
+        for n_s, kind in ((64, "one_vesicle"), (512, "ellipse_shrink")):
+            sec = min(args.cpu_seconds, 3.0)
+            a = cpu_oracle_sample(n_s, seed, sec, kind=kind)
+            o = cpu_oracle_sample(n_s, seed, sec, threads=1, kind=kind)
+            per[f"{kind}_N{n_s}"] = {"all_cores": round(a["value"]), "one_thread": round(o["value"]),
+                                     "ms_per_step_all_cores": round(1e3 * a["seconds"] / a["steps"], 2),
+                                     "ms_per_step_one_thread": round(1e3 * o["seconds"] / o["steps"], 2),
+                                     "unit": "grid-point-steps/s"}
+        cpu["other_sizes"] = per
     if rank != 0:
         return
     line = {
