@@ -527,13 +527,22 @@ def run_ours(args, world, rank, local):
     barrier(world)
     torch.cuda.synchronize()
     l0 = sim.launches()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    sim.step(args.steps)
-    e1.record(stream)
+    # five windows with an event between them (each a multiple of three steps
+    # but the last, so the same graphs run as for one call of K steps); the
+    # value is the whole region, the windows give the median per-step time
+    nwin = 5 if args.steps >= 30 else 1
+    base = (args.steps // nwin) // 3 * 3
+    sizes = [base] * (nwin - 1) + [args.steps - base * (nwin - 1)]
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(nwin + 1)]
+    evs[0].record(stream)
+    for i, kw in enumerate(sizes):
+        sim.step(kw)
+        evs[i + 1].record(stream)
+    e0, e1 = evs[0], evs[-1]
     torch.cuda.synchronize()
     barrier(world)
     secs = e0.elapsed_time(e1) / 1e3
+    win_ms = [evs[i].elapsed_time(evs[i + 1]) / kw for i, kw in enumerate(sizes)]
     launches = sim.launches() - l0
     sim.sync()
     value, tmax, units = aggregate(secs, NN * args.steps, world)
@@ -648,6 +657,10 @@ def run_ours(args, world, rank, local):
         "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32" if args.precision == "fp32" else "f64", "data": "synthetic",
         "config": bench_config(w, args.precision, world),
+        "timing_windows": {"steps": sizes, "ms_per_step": [round(x, 5) for x in win_ms],
+                           "median_ms_per_step": round(sorted(win_ms)[len(win_ms) // 2], 5),
+                           "what": "this rank's timed region split by events into windows (value and ms_per_step "
+                                   "cover the whole region)"},
         "roofline": roof,
         "step_roofline": {"alg_bytes_per_point": STEP_PASSES_MIN_SCHEDULE * esize,
                           "achieved_GBps": round(value / world * STEP_PASSES_MIN_SCHEDULE * esize / 1e9, 1),
