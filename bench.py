@@ -443,7 +443,7 @@ def phase_roofline(per_launch, NN, esize, peak, peak_kind, workload):
 
 
 def dct_sweep():
-    """Per N (128 .. 4096, FP32): the line-transform kernels' event times and
+    """Per N (128 .. 8192, FP32): the line-transform kernels' event times and
     algorithmic GB/s on the warp-FFT path, and the step time with the
     warp-FFT kernels against the block-FFT kernels (the library takes the
     warp path wherever it exists)."""
@@ -458,9 +458,9 @@ def dct_sweep():
     sh = stream.cuda_stream
     peak, peak_kind = measured_peaks()
     rows = []
-    for N in (128, 256, 512, 1024, 2048, 4096):
+    for N in (128, 256, 512, 1024, 2048, 4096, 8192):
         w = I.three_vesicles(N=N) if N >= 1024 else I.workload("ellipse_shrink", N=N)
-        k = 300 if N <= 512 else (100 if N <= 2048 else 30)
+        k = 300 if N <= 512 else (100 if N <= 2048 else (30 if N <= 4096 else 9))
         rec = {"N": N, "steps": k}
         for path in ("warp", "block"):
             os.environ["CCMSAV_FORCE_BLOCK_FFT"] = "1" if path == "block" else "0"
