@@ -68,6 +68,7 @@ public:
     // FP32 warp-FFT path (N = 128 .. 2048): twiddle matrix W_M^{n2 k1} and FP32 eigenvalues
     bool warp_path = false;
     cplx<float>* tw2 = nullptr;
+    cplx<float>* tw2i = nullptr;   // the inverse transforms' table (tw2 unless their line shape differs)
     float* evf = nullptr;
     float4* evp = nullptr;   // eigenvalues in the pair order of the warp-path spectra
     float4* twF = nullptr;       // forward / inverse pair twiddles of the warp path
@@ -148,11 +149,11 @@ public:
     void count_steps_grouped(int n3) override { steps_taken += n3; }
 
     // ---- grouped launches -------------------------------------------------
-    // FP32 warp path with one warp or less per line, no classical mode, no
+    // FP32 warp path with one warp or less per line (N <= 2048), no classical mode, no
     // energy tracking: simulations of the same M share each kernel launch.
     int group_key() const override {
         if constexpr (std::is_same<T, float>::value)
-            if (warp_path && !classical && !(flags & CCMSAV_TRACK_ENERGY) && M >= 64 && M <= 2048) return M;
+            if (warp_path && !classical && !(flags & CCMSAV_TRACK_ENERGY) && M >= 64 && M <= 1024) return M;
         return 0;
     }
     size_t batch_args_bytes() const override { return sizeof(BatchArgs); }
@@ -214,7 +215,6 @@ public:
                     case 256: group_launch<256>(ga[0], n, s); break;
                     case 512: group_launch<512>(ga[0], n, s); break;
                     case 1024: group_launch<1024>(ga[0], n, s); break;
-                    case 2048: group_launch<2048>(ga[0], n, s); break;
                     default: return CCMSAV_EINVAL;
                 }
             }
@@ -304,11 +304,12 @@ public:
         for (int i = 0; i < 3; ++i) { cudaFree(phi[i]); cudaFree(psi[i]); phi[i] = psi[i] = nullptr; }
         cudaFree(bufA); cudaFree(bufB); cudaFree(part1); cudaFree(part2); cudaFree(partd); cudaFree(part3);
         cudaFree(twM); cudaFree(twP); cudaFree(ev); cudaFree(sc); cudaFree(tmp64);
+        if (tw2i && tw2i != tw2) cudaFree(tw2i);
         cudaFree(tw2); cudaFree(evf); cudaFree(evp); cudaFree(twF); cudaFree(twI);
         cudaFree(cl); cudaFree(pcg); cudaFree(cl_red);
         if (pcg_host) cudaFreeHost(pcg_host);
         cl = nullptr; pcg = nullptr; cl_red = nullptr; pcg_host = nullptr;
-        tw2 = nullptr; evf = nullptr; evp = nullptr; twF = nullptr; twI = nullptr;
+        tw2 = nullptr; tw2i = nullptr; evf = nullptr; evp = nullptr; twF = nullptr; twI = nullptr;
         if (sc_host) cudaFreeHost(sc_host);
         if (h_part) cudaFreeHost(h_part);
         if (h_up) cudaFreeHost(h_up);
@@ -721,9 +722,8 @@ public:
     static constexpr int kRowCarveout = 72;
     static constexpr int kColCarveout = 72;
     static constexpr int kCombCarveout = 72;
-    template <int MM> int setup_warp() {
-        using Gm = WGeo<MM>;
-        constexpr int G = Gm::G, E = Gm::E;
+    // four-step twiddle table W_M^{n2 k1} of an E x G line shape, entry k1 G + n2
+    int make_tw2(int MM, int E, int G, cplx<float>** out) {
         std::vector<cplx<float>> h2((size_t)MM);
         for (int k1 = 0; k1 < E; ++k1)
             for (int n2 = 0; n2 < G; ++n2) {
@@ -731,8 +731,19 @@ public:
                 h2[(size_t)k1 * G + n2].x = (float)std::cos(a);
                 h2[(size_t)k1 * G + n2].y = (float)(-std::sin(a));
             }
-        if (cudaMalloc(&tw2, MM * sizeof(cplx<float>)) != cudaSuccess) return CCMSAV_ENOMEM;
-        CCM_CUDA(cudaMemcpyAsync(tw2, h2.data(), MM * sizeof(cplx<float>), cudaMemcpyHostToDevice, st));
+        if (cudaMalloc(out, MM * sizeof(cplx<float>)) != cudaSuccess) { *out = nullptr; return CCMSAV_ENOMEM; }
+        CCM_CUDA(cudaMemcpyAsync(*out, h2.data(), MM * sizeof(cplx<float>), cudaMemcpyHostToDevice, st));
+        return CCMSAV_OK;
+    }
+    template <int MM> int setup_warp() {
+        using Gm = WGeo<MM>;
+        using Gi = WGeo<MM, inv_shape<MM>()>;       // the inverse transforms' line shape
+        if (int r = make_tw2(MM, Gm::E, Gm::G, &tw2)) return r;
+        if constexpr (inv_shape<MM>() != 0) {
+            if (int r = make_tw2(MM, Gi::E, Gi::G, &tw2i)) return r;
+        } else {
+            tw2i = tw2;
+        }
         const size_t bb = Gm::buf_bytes();
         wRT = Gm::SLOTS; wsm_rt = bb;
         wKC = Gm::SLOTS / NF; wsm_col = bb;
@@ -740,7 +751,7 @@ public:
             wKC = 1;
             wsm_col = (size_t)5 * Gm::BUF * sizeof(cplx<float>);
         }
-        wRT4 = Gm::SLOTS / 2; wsm_comb = Gm::bufp_bytes();
+        wRT4 = Gi::SLOTS / 2; wsm_comb = Gi::bufp_bytes();
         wsm_irow = InvGeo<MM>::smem_bytes();
         if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt, kRowCarveout) || set_smem_limit(coldct_fn<MM>(), wsm_col, kColCarveout) ||
             set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb, kCombCarveout) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
@@ -867,11 +878,11 @@ public:
     void launch_warp_inverse(const SpecCoef& s, int anchor) {
         SpecCoefF sf{(float)s.C1, (float)s.C2, (float)s.C3, (float)s.Ct, (float)s.lam};
         kw_comb_icolT<MM><<<N / wRT4, kWarps * 32, wsm_comb, st>>>(reinterpret_cast<const float*>(bufA),
-            reinterpret_cast<float*>(bufB), tw2, pair_tab(twI), evf, evp, sf, sc, anchor, GroupArgs<false>{}, 0);
+            reinterpret_cast<float*>(bufB), tw2i, pair_tab(twI), evf, evp, sf, sc, anchor, GroupArgs<false>{}, 0);
         mark(4);
         kw_irow<MM><<<(2 * N + InvGeo<MM>::LINES - 1) / InvGeo<MM>::LINES, InvGeo<MM>::WARPS * 32, wsm_irow, st>>>(
             reinterpret_cast<const float*>(bufB),
-            reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), tw2, pair_tab(twI),
+            reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), tw2i, pair_tab(twI),
             reinterpret_cast<const float*>(phi[cur]), reinterpret_cast<const float*>(phi[prev]),
             reinterpret_cast<const float*>(psi[cur]), reinterpret_cast<const float*>(psi[prev]),
             bdf1_launch, sc, anchor, GroupArgs<false>{}, 0);

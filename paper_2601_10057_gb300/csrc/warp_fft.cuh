@@ -173,19 +173,25 @@ template <int R> __host__ __device__ constexpr int bitrev(int r) {
     return o;
 }
 
-template <int M> struct Shape;
-template <> struct Shape<64>   { static constexpr int E = 8,  G = 8;  };
-template <> struct Shape<128>  { static constexpr int E = 16, G = 8;  };
-template <> struct Shape<256>  { static constexpr int E = 16, G = 16; };
-template <> struct Shape<512>  { static constexpr int E = 32, G = 16; };
-template <> struct Shape<1024> { static constexpr int E = 32, G = 32; };
-template <> struct Shape<2048> { static constexpr int E = 64, G = 32; };
-template <> struct Shape<4096> { static constexpr int E = 64, G = 64; };
+// Line shapes M = E x G (E values on each of G lanes).  S selects a variant:
+// 2048-point lines run as 64 x 32 (one warp per line) in the forward
+// transforms and as 32 x 64 (two warps per line, fourstep_half) in the
+// inverse ones, which wait on memory and gain from the lower register use.
+template <int M> struct ShapeBase;
+template <> struct ShapeBase<64>   { static constexpr int E = 8,  G = 8;  };
+template <> struct ShapeBase<128>  { static constexpr int E = 16, G = 8;  };
+template <> struct ShapeBase<256>  { static constexpr int E = 16, G = 16; };
+template <> struct ShapeBase<512>  { static constexpr int E = 32, G = 16; };
+template <> struct ShapeBase<1024> { static constexpr int E = 32, G = 32; };
+template <> struct ShapeBase<2048> { static constexpr int E = 64, G = 32; };
+template <> struct ShapeBase<4096> { static constexpr int E = 64, G = 64; };
+template <int M, int S = 0> struct Shape : ShapeBase<M> {};
+template <> struct Shape<2048, 1> { static constexpr int E = 32, G = 64; };
 
 // Lane n2 of its line's group and the line's slot in the CTA: G <= 32 puts
 // 32 / G lines in a warp; G = 64 spreads a line over two consecutive warps.
-template <int M> __device__ __forceinline__ void lane_geo(int& n2, int& slot) {
-    constexpr int G = Shape<M>::G;
+template <int M, int S = 0> __device__ __forceinline__ void lane_geo(int& n2, int& slot) {
+    constexpr int G = Shape<M, S>::G;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if constexpr (G <= 32) {
         n2 = lane % G;
@@ -212,8 +218,9 @@ template <int G> __device__ __forceinline__ void line_sync(int slot) {
 // that, as float rows, consecutive line buffers sit 4 banks apart (the
 // strided reads of the transposed writes).  Swizzled (SWZ = true): M values
 // + 2, for kernels that need more lines per SM.
-template <int M, bool SWZ = false> __host__ __device__ constexpr int buf_len() {
-    return SWZ ? M + 2 : Shape<M>::E * (Shape<M>::G + 1) + 2;
+template <int M, bool SWZ = false, int S = 0> __host__ __device__ constexpr int buf_len() {
+    return Shape<M, S>::E < Shape<M, S>::G ? Shape<M, S>::E * (Shape<M, S>::G + 2)   // fourstep_half's rows
+         : SWZ ? M + 2 : Shape<M, S>::E * (Shape<M, S>::G + 1) + 2;
 }
 
 // Position of element c of transpose row R (E rows of G values).  Padded:
@@ -224,17 +231,59 @@ template <int M, bool SWZ = false> __host__ __device__ constexpr int buf_len() {
 // values of its row (n2 J + j) with one 16-byte load, on distinct banks within
 // each quarter-warp for G >= 16.  For E = 64, swz(R) = (R / J) mod G with
 // 8-byte reads (measured faster there).
-template <int M> __host__ __device__ constexpr bool wide_reads() { return Shape<M>::E <= 32; }
-template <int M, bool SWZ> __device__ __forceinline__ int tpos(int R, int c) {
-    constexpr int G = Shape<M>::G, J = Shape<M>::E / Shape<M>::G, S = wide_reads<M>() ? 2 : 1;
-    return SWZ ? R * G + (c ^ ((S * (R / J)) & (G - 1))) : R * (G + 1) + c;
+template <int M, int S = 0> __host__ __device__ constexpr bool wide_reads() { return Shape<M, S>::E <= 32; }
+template <int M, bool SWZ, int S = 0> __device__ __forceinline__ int tpos(int R, int c) {
+    constexpr int G = Shape<M, S>::G, J = Shape<M, S>::E / Shape<M, S>::G, W = wide_reads<M, S>() ? 2 : 1;
+    return SWZ ? R * G + (c ^ ((W * (R / J)) & (G - 1))) : R * (G + 1) + c;
+}
+
+// The four steps for lines of G = 2E lanes (E values each): the E-point
+// DFTs and the twiddles as below, then each G-point row of the transpose is
+// split over a pair of adjacent lanes (lane 2 k1 + h takes the columns
+// 2t + h, t = 0 .. E-1), each lane takes an E-point DFT of its half, and the
+// pair combines them in one radix-2 step through shuffles:
+//   X[k1 + E (k + E h)] = Y_0[k] + (-1)^h W_G^k Y_1[k]   (W_G^-k for INV),
+// Y_h the half-row DFTs, so lane h writes the outputs of its own sign.
+// Transpose rows are padded to G + 2 values: the row writes (one row, all
+// lanes) and the half-row reads (eight rows and both halves per half-warp,
+// 8-byte words) touch distinct banks.
+template <typename T, int M, bool INV, int S = 0>
+__device__ __forceinline__ void fourstep_half(cplx<T>* v, cplx<T>* buf, const cplx<T>* __restrict__ tw2, int n2, int slot) {
+    constexpr int E = Shape<M, S>::E, G = Shape<M, S>::G, P = G + 2;
+    static_assert(G == 2 * E, "two lanes per transpose row");
+    DIF<T, E, INV, 0>::run(v);                   // v[r] = X1[k1 = bitrev(r)] of column n2
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int k1 = bitrev<E>(r);
+        const cplx<T> w = tw2[k1 * G + n2];
+        buf[k1 * P + n2] = INV ? cmulc(v[r], w) : cmul(v[r], w);
+    }
+    line_sync<G>(slot);
+    const int k1 = n2 >> 1, h = n2 & 1;
+#pragma unroll
+    for (int t = 0; t < E; ++t) v[t] = buf[k1 * P + 2 * t + h];
+    line_sync<G>(slot);
+    DIF<T, E, INV, 0>::run(v);                   // v[r] = Y_h[k = bitrev(r)]
+#pragma unroll
+    for (int r = 0; r < E; ++r) {
+        const int k = bitrev<E>(r);
+        const T px = __shfl_xor_sync(0xffffffffu, v[r].x, 1);
+        const T py = __shfl_xor_sync(0xffffffffu, v[r].y, 1);
+        const cplx<T> y0 = h ? mk(px, py) : v[r];
+        const cplx<T> y1 = twid<T, G, INV>(h ? v[r] : mk(px, py), k);
+        buf[k1 + E * (k + E * h)] = h ? y0 - y1 : y0 + y1;
+    }
+    line_sync<G>(slot);
 }
 
 // Steps 1-4.  v: this lane's E values in four-step order.  buf: this line's
 // buffer.  On return buf[k] = Z[k], k = 0..M-1 (visible to the warp).
-template <typename T, int M, bool INV, bool SWZ = false>
+template <typename T, int M, bool INV, bool SWZ = false, int S = 0>
 __device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>* __restrict__ tw2, int n2, int slot) {
-    constexpr int E = Shape<M>::E, G = Shape<M>::G, J = E / G;
+  if constexpr (Shape<M, S>::E < Shape<M, S>::G) {
+    fourstep_half<T, M, INV, S>(v, buf, tw2, n2, slot);
+  } else {
+    constexpr int E = Shape<M, S>::E, G = Shape<M, S>::G, J = E / G;
     DIF<T, E, INV, 0>::run(v);
     if constexpr (!INV) {
         // twiddles W_M^{n2 k1}: k1 = bitrev(r) is below E/2 for even r; for odd
@@ -246,23 +295,23 @@ __device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>
         for (int r = 0; r < E; r += 2) {
             const int k1 = bitrev<E>(r);
             const cplx<T> w = tw2[k1 * G + n2];
-            buf[tpos<M, SWZ>(k1, n2)] = cmul(v[r], w);
-            buf[tpos<M, SWZ>(k1 + E / 2, n2)] = cmul(v[r + 1], cmul(w, wh));
+            buf[tpos<M, SWZ, S>(k1, n2)] = cmul(v[r], w);
+            buf[tpos<M, SWZ, S>(k1 + E / 2, n2)] = cmul(v[r + 1], cmul(w, wh));
         }
     } else {
 #pragma unroll
         for (int r = 0; r < E; ++r) {
             const int k1 = bitrev<E>(r);
-            buf[tpos<M, SWZ>(k1, n2)] = cmulc(v[r], tw2[k1 * G + n2]);
+            buf[tpos<M, SWZ, S>(k1, n2)] = cmulc(v[r], tw2[k1 * G + n2]);
         }
     }
     line_sync<G>(slot);
-    if constexpr (SWZ && wide_reads<M>() && std::is_same<T, float>::value) {
+    if constexpr (SWZ && wide_reads<M, S>() && std::is_same<T, float>::value) {
 #pragma unroll
         for (int j = 0; j < J; ++j)
 #pragma unroll
             for (int m = 0; m < G; m += 2) {
-                const float4 q = *reinterpret_cast<const float4*>(buf + tpos<M, SWZ>(n2 * J + j, m));
+                const float4 q = *reinterpret_cast<const float4*>(buf + tpos<M, SWZ, S>(n2 * J + j, m));
                 v[j * G + m] = mk(q.x, q.y);
                 v[j * G + m + 1] = mk(q.z, q.w);
             }
@@ -270,7 +319,7 @@ __device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>
 #pragma unroll
         for (int j = 0; j < J; ++j)
 #pragma unroll
-            for (int m = 0; m < G; ++m) v[j * G + m] = buf[tpos<M, SWZ>(n2 * J + j, m)];
+            for (int m = 0; m < G; ++m) v[j * G + m] = buf[tpos<M, SWZ, S>(n2 * J + j, m)];
     }
     line_sync<G>(slot);
 #pragma unroll
@@ -283,6 +332,7 @@ __device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>
 #pragma unroll
         for (int r = 0; r < G; ++r) buf[(n2 * J + j) + E * bitrev<G>(r)] = v[j * G + r];
     line_sync<G>(slot);
+  }
 }
 
 // Forward pack from a real line x in global memory (16-byte aligned):

@@ -52,8 +52,8 @@ template <int M> struct SpecRow {
     static constexpr size_t KS = (size_t)7 * RS;      // next kx
 };
 
-template <int M> struct WGeo {
-    static constexpr int E = wf::Shape<M>::E, G = wf::Shape<M>::G;
+template <int M, int S = 0> struct WGeo {
+    static constexpr int E = wf::Shape<M, S>::E, G = wf::Shape<M, S>::G;
     static constexpr int WPL = G > 32 ? G / 32 : 1;     // warps per line
     static constexpr int LPW = G > 32 ? 1 : 32 / G;     // lines per warp (one line spans WPL warps)
     static constexpr int SLOTS = kWarps * LPW / WPL;    // line buffers per CTA
@@ -61,8 +61,8 @@ template <int M> struct WGeo {
     // three 8-line CTAs of the forward kernels fit the 196 KB shared-memory
     // configuration; padded rows (G + 1 values) for the recovery kernel (two
     // CTAs per SM, measured faster than three)
-    static constexpr int BUF = wf::buf_len<M, true>();
-    static constexpr int BUFP = wf::buf_len<M>();
+    static constexpr int BUF = wf::buf_len<M, true, S>();
+    static constexpr int BUFP = wf::buf_len<M, false, S>();
     static constexpr size_t buf_bytes() { return (size_t)SLOTS * BUF * sizeof(cplx<float>); }
     static constexpr size_t bufp_bytes() { return (size_t)SLOTS * BUFP * sizeof(cplx<float>); }
 };
@@ -359,6 +359,11 @@ kw_coldct_gram_split(const float* __restrict__ in, float* __restrict__ spec, dou
 // Phase 1 (all threads): gather the spectra, combine, divide, pre-process
 // into the line buffers.  Phase 2 (per line): inverse four-step FFT and
 // unpack in place.  Phase 3: transposed write from the buffers.
+// Line shape of the inverse transforms (the recovery and inverse-row
+// kernels): 2048-point lines over two warps of 32 values per lane (variant
+// 1), the others as in the forward transforms.
+template <int M> __host__ __device__ constexpr int inv_shape() { return M == 2048 ? 1 : 0; }
+
 template <int M, bool GRP = false>
 __global__ void __launch_bounds__(kWarps * 32)
 kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
@@ -366,7 +371,8 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
               const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc,
               DevScalars* __restrict__ dsc, int anchor_mass,
               const __grid_constant__ GroupArgs<GRP> ga, int bps) {
-    using Gm = WGeo<M>;
+    constexpr int SV = inv_shape<M>();
+    using Gm = WGeo<M, SV>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS / 2, NU = (M / 2 + G - 1) / G;
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
@@ -429,14 +435,14 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
     __syncthreads();
     __shared__ float2 lsum[2 * Gm::SLOTS];
     int n2, slot;                                        // line = slot: row slot/2, field slot%2
-    wf::lane_geo<M>(n2, slot);
+    wf::lane_geo<M, SV>(n2, slot);
     cplx<float>* buf = bufs + (size_t)slot * Gm::BUFP;
     {
         cplx<float> v[E];
 #pragma unroll
         for (int n1 = 0; n1 < E; ++n1) v[n1] = buf[G * n1 + n2];
         wf::line_sync<G>(slot);
-        wf::fourstep<float, M, true>(v, buf, tw2, n2, slot);
+        wf::fourstep<float, M, true, false, SV>(v, buf, tw2, n2, slot);
     }
     float dhi = 0.f, dlo = 0.f;
 #pragma unroll
@@ -503,13 +509,14 @@ template <int M> __host__ __device__ constexpr int inv_warps() {
     return M == 1024 ? 9 : M >= 2048 ? 4 : M == 512 ? 4 : M == 256 ? 2 : 1;
 }
 template <int M> __host__ __device__ constexpr int inv_min_ctas() {
-    return M == 1024 || M >= 2048 ? 3 : 4;
+    return M == 2048 ? 4 : M == 1024 || M > 2048 ? 3 : 4;
 }
 
 template <int M> struct InvGeo {
+    using W = WGeo<M, inv_shape<M>()>;
     static constexpr int WARPS = inv_warps<M>();
-    static constexpr int LINES = WARPS * WGeo<M>::LPW / WGeo<M>::WPL;   // lines per CTA
-    static constexpr int BUF = wf::buf_len<M, true>();         // unpadded, swizzled transpose
+    static constexpr int LINES = WARPS * W::LPW / W::WPL;     // lines per CTA
+    static constexpr int BUF = wf::buf_len<M, true, inv_shape<M>()>();   // unpadded, swizzled transpose
     static constexpr size_t smem_bytes() { return (size_t)LINES * BUF * sizeof(cplx<float>); }
 };
 
@@ -521,7 +528,8 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
         const float* __restrict__ psn, const float* __restrict__ pso, int bdf1,
         const DevScalars* __restrict__ dsc, int anchor_mass,
         const __grid_constant__ GroupArgs<GRP> ga, int bps) {
-    using Gm = WGeo<M>;
+    constexpr int SV = inv_shape<M>();
+    using Gm = WGeo<M, SV>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, L = InvGeo<M>::LINES, NU = (M / 2 + G - 1) / G;
     int bx = blockIdx.x;
     if constexpr (GRP) {          // grouped launch
@@ -568,7 +576,7 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
     __syncthreads();
     __shared__ float2 lsum[2 * L];
     int n2, slot;
-    wf::lane_geo<M>(n2, slot);
+    wf::lane_geo<M, SV>(n2, slot);
     const int gl = l0 + slot;
     const bool valid = gl < 2 * N;                       // the last CTA has fewer lines
     const int fld = gl & 1;
@@ -578,7 +586,7 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
 #pragma unroll
         for (int n1 = 0; n1 < E; ++n1) v[n1] = buf[G * n1 + n2];
         wf::line_sync<G>(slot);
-        wf::fourstep<float, M, true, true>(v, buf, tw2, n2, slot);
+        wf::fourstep<float, M, true, true, SV>(v, buf, tw2, n2, slot);
     }
     const size_t roff = valid ? (size_t)(gl >> 1) * N : 0;
     // FP32 path, psi: the row's increments should sum to sqrt(N) x0 (x0 the

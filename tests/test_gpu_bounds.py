@@ -2,7 +2,7 @@
 library built with -DCCMSAV_BOUNDS (libccmsav_bounds.so) runs the small and
 ragged grids (N = 8 ... 256, FP64 and FP32, block- and warp-FFT paths, start
 and BDF2 steps, graph-launched steps, the classical and BDF1 modes, a batched
-handle with grouped launches; and N = 8192 on the two-warp-line kernels) in a
+handle with grouped launches; and N = 4096, 8192 on the two-warp-line kernels) in a
 child process; no access may leave its array (ccmsav_bounds_flag() = 0) and
 the results stay those of the oracle (the shrinking ellipse: the single
 perturbed circle at N = 256 amplifies a 1e-10 perturbation to 1e-5 within
@@ -47,20 +47,21 @@ for N, prec, mode in cases:
               classical=(mode == "classical"))
     e = max(float(np.abs(phi - s.phi).max() / np.abs(s.phi).max()), float(np.abs(psi - s.psi).max() / np.abs(s.psi).max()))
     out.append({"N": N, "precision": prec, "mode": mode, "flag": flag, "err": e})
-# the largest grid on the FP32 warp path (two warps per 4096-point line), against FP64 on the GPU
-w = I.lattice_16(N=8192)
-res = {}
-for prec in ("fp64", "fp32"):
-    sim = cc.Simulation(w.params, 8192, precision=prec)
-    sim.set_state(w.phi0, w.psi0)
-    sim.step(1)
-    sim.step(3)
-    res[prec] = sim.state()
-    flag = cc.ccmsav_bounds_flag(sim.h) if prec == "fp32" else 0
-    sim.close()
-e = max(float(np.abs(res["fp32"][0] - res["fp64"][0]).max() / np.abs(res["fp64"][0]).max()),
-        float(np.abs(res["fp32"][1] - res["fp64"][1]).max() / np.abs(res["fp64"][1]).max()))
-out.append({"N": 8192, "precision": "fp32", "mode": "cc-vs-fp64", "flag": flag, "err": e})
+# the FP32 warp path with lines over two warps (2048- and 4096-point lines),
+# against FP64 on the GPU
+for NB, w in ((4096, I.three_vesicles(N=4096)), (8192, I.lattice_16(N=8192))):
+    res = {}
+    for prec in ("fp64", "fp32"):
+        sim = cc.Simulation(w.params, NB, precision=prec)
+        sim.set_state(w.phi0, w.psi0)
+        sim.step(1)
+        sim.step(3)
+        res[prec] = sim.state()
+        flag = cc.ccmsav_bounds_flag(sim.h) if prec == "fp32" else 0
+        sim.close()
+    e = max(float(np.abs(res["fp32"][0] - res["fp64"][0]).max() / np.abs(res["fp64"][0]).max()),
+            float(np.abs(res["fp32"][1] - res["fp64"][1]).max() / np.abs(res["fp64"][1]).max()))
+    out.append({"N": NB, "precision": "fp32", "mode": "cc-vs-fp64", "flag": flag, "err": e})
 # a batched handle with grouped launches (three N = 128 and two N = 256 FP32
 # simulations sharing each kernel launch, an N = 64 one on its own), against
 # each simulation run alone in the same library
@@ -96,6 +97,6 @@ def test_bounds_checked_build_small_grids():
     for c in res:
         print(c)
     assert all(c["flag"] == 0 for c in res), [c for c in res if c["flag"]]
-    tol = {"fp64": 1e-11, "fp32": 2e-5}      # N = 8192: FP32 against FP64 after 4 steps
+    tol = {"fp64": 1e-11, "fp32": 2e-5}      # N = 4096, 8192: FP32 against FP64 after 4 steps
     bad = [c for c in res if c["err"] > (0.0 if c["mode"] == "grouped-vs-solo" else tol[c["precision"]])]
     assert not bad, bad
