@@ -68,7 +68,7 @@ public:
     // FP32 warp-FFT path (N = 128 .. 2048): twiddle matrix W_M^{n2 k1} and FP32 eigenvalues
     bool warp_path = false;
     cplx<float>* tw2 = nullptr;
-    cplx<float>* tw2i = nullptr;   // the inverse transforms' table (tw2 unless their line shape differs)
+    cplx<float>* tw2i = nullptr;   // table of the inverse kernels' variant line shape (or tw2)
     float* evf = nullptr;
     float4* evp = nullptr;   // eigenvalues in the pair order of the warp-path spectra
     float4* twF = nullptr;       // forward / inverse pair twiddles of the warp path
@@ -737,10 +737,11 @@ public:
     }
     template <int MM> int setup_warp() {
         using Gm = WGeo<MM>;
-        using Gi = WGeo<MM, inv_shape<MM>()>;       // the inverse transforms' line shape
+        using Gc = WGeo<MM, comb_shape<MM>()>;      // the recovery kernel's line shape
+        using Gv = WGeo<MM, 1>;                     // the variant of the inverse kernels
         if (int r = make_tw2(MM, Gm::E, Gm::G, &tw2)) return r;
-        if constexpr (inv_shape<MM>() != 0) {
-            if (int r = make_tw2(MM, Gi::E, Gi::G, &tw2i)) return r;
+        if constexpr (comb_shape<MM>() != 0 || irow_shape<MM>() != 0) {
+            if (int r = make_tw2(MM, Gv::E, Gv::G, &tw2i)) return r;
         } else {
             tw2i = tw2;
         }
@@ -751,7 +752,7 @@ public:
             wKC = 1;
             wsm_col = (size_t)5 * Gm::BUF * sizeof(cplx<float>);
         }
-        wRT4 = Gi::SLOTS / 2; wsm_comb = Gi::bufp_bytes();
+        wRT4 = Gc::SLOTS / 2; wsm_comb = Gc::bufp_bytes();
         wsm_irow = InvGeo<MM>::smem_bytes();
         if (set_smem_limit((const void*)kw_rowdct_T<MM>, wsm_rt, kRowCarveout) || set_smem_limit(coldct_fn<MM>(), wsm_col, kColCarveout) ||
             set_smem_limit((const void*)kw_comb_icolT<MM>, wsm_comb, kCombCarveout) || set_smem_limit((const void*)kw_irow<MM>, wsm_irow))
@@ -878,11 +879,13 @@ public:
     void launch_warp_inverse(const SpecCoef& s, int anchor) {
         SpecCoefF sf{(float)s.C1, (float)s.C2, (float)s.C3, (float)s.Ct, (float)s.lam};
         kw_comb_icolT<MM><<<N / wRT4, kWarps * 32, wsm_comb, st>>>(reinterpret_cast<const float*>(bufA),
-            reinterpret_cast<float*>(bufB), tw2i, pair_tab(twI), evf, evp, sf, sc, anchor, GroupArgs<false>{}, 0);
+            reinterpret_cast<float*>(bufB), comb_shape<MM>() ? tw2i : tw2, pair_tab(twI), evf, evp, sf, sc, anchor,
+            GroupArgs<false>{}, 0);
         mark(4);
         kw_irow<MM><<<(2 * N + InvGeo<MM>::LINES - 1) / InvGeo<MM>::LINES, InvGeo<MM>::WARPS * 32, wsm_irow, st>>>(
             reinterpret_cast<const float*>(bufB),
-            reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), tw2i, pair_tab(twI),
+            reinterpret_cast<float*>(phi[spare]), reinterpret_cast<float*>(psi[spare]), irow_shape<MM>() ? tw2i : tw2,
+            pair_tab(twI),
             reinterpret_cast<const float*>(phi[cur]), reinterpret_cast<const float*>(phi[prev]),
             reinterpret_cast<const float*>(psi[cur]), reinterpret_cast<const float*>(psi[prev]),
             bdf1_launch, sc, anchor, GroupArgs<false>{}, 0);

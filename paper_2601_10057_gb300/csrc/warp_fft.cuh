@@ -174,9 +174,10 @@ template <int R> __host__ __device__ constexpr int bitrev(int r) {
 }
 
 // Line shapes M = E x G (E values on each of G lanes).  S selects a variant:
-// 2048-point lines run as 64 x 32 (one warp per line) in the forward
-// transforms and as 32 x 64 (two warps per line, fourstep_half) in the
-// inverse ones, which wait on memory and gain from the lower register use.
+// the forward transforms run 2048-point lines as 64 x 32 (one warp per line)
+// and 4096-point lines as 64 x 64; the inverse kernels, which wait on memory
+// and gain from the lower register use, take 32 x 64 and 32 x 128 (two and
+// four warps per line, fourstep_split).
 template <int M> struct ShapeBase;
 template <> struct ShapeBase<64>   { static constexpr int E = 8,  G = 8;  };
 template <> struct ShapeBase<128>  { static constexpr int E = 16, G = 8;  };
@@ -187,6 +188,7 @@ template <> struct ShapeBase<2048> { static constexpr int E = 64, G = 32; };
 template <> struct ShapeBase<4096> { static constexpr int E = 64, G = 64; };
 template <int M, int S = 0> struct Shape : ShapeBase<M> {};
 template <> struct Shape<2048, 1> { static constexpr int E = 32, G = 64; };
+template <> struct Shape<4096, 1> { static constexpr int E = 32, G = 128; };
 
 // Lane n2 of its line's group and the line's slot in the CTA: G <= 32 puts
 // 32 / G lines in a warp; G = 64 spreads a line over two consecutive warps.
@@ -219,7 +221,8 @@ template <int G> __device__ __forceinline__ void line_sync(int slot) {
 // strided reads of the transposed writes).  Swizzled (SWZ = true): M values
 // + 2, for kernels that need more lines per SM.
 template <int M, bool SWZ = false, int S = 0> __host__ __device__ constexpr int buf_len() {
-    return Shape<M, S>::E < Shape<M, S>::G ? Shape<M, S>::E * (Shape<M, S>::G + 2)   // fourstep_half's rows
+    return Shape<M, S>::E < Shape<M, S>::G                                          // fourstep_split's rows
+             ? Shape<M, S>::E * (Shape<M, S>::G + Shape<M, S>::G / Shape<M, S>::E)
          : SWZ ? M + 2 : Shape<M, S>::E * (Shape<M, S>::G + 1) + 2;
 }
 
@@ -237,20 +240,23 @@ template <int M, bool SWZ, int S = 0> __device__ __forceinline__ int tpos(int R,
     return SWZ ? R * G + (c ^ ((W * (R / J)) & (G - 1))) : R * (G + 1) + c;
 }
 
-// The four steps for lines of G = 2E lanes (E values each): the E-point
-// DFTs and the twiddles as below, then each G-point row of the transpose is
-// split over a pair of adjacent lanes (lane 2 k1 + h takes the columns
-// 2t + h, t = 0 .. E-1), each lane takes an E-point DFT of its half, and the
-// pair combines them in one radix-2 step through shuffles:
-//   X[k1 + E (k + E h)] = Y_0[k] + (-1)^h W_G^k Y_1[k]   (W_G^-k for INV),
-// Y_h the half-row DFTs, so lane h writes the outputs of its own sign.
-// Transpose rows are padded to G + 2 values: the row writes (one row, all
-// lanes) and the half-row reads (eight rows and both halves per half-warp,
-// 8-byte words) touch distinct banks.
+// The four steps for lines of G = R E lanes (E values each, R = 2 or 4): the
+// E-point DFTs and the twiddles as below, then each G-point row k1 of the
+// transpose is split over R adjacent lanes (lane R k1 + q takes the columns
+// R t + q, t = 0 .. E-1), each lane takes an E-point DFT Y_q of its part,
+// multiplies it by W_G^{q k} (U_q), and the R lanes combine by an R-point DFT
+// through shuffles:
+//   X[k1 + E (k + E s)] = sum_q W_R^{q s} U_q[k]        (conjugates for INV),
+// R = 2 in one radix-2 step (lane q keeps s = q), R = 4 in two (pairs q, q^2,
+// then q, q^1; lane q keeps s = bit-reversed q).  W_G^{q k} = W_M^{E q k} is
+// the table entry of k1 = k, n2 = E q: tw2[k G + E q].  Transpose rows are
+// padded to G + R values:
+// the row writes (one row, all lanes) and the part-row reads (16 / R rows and
+// all R parts per half-warp, 8-byte words) touch distinct banks.
 template <typename T, int M, bool INV, int S = 0>
-__device__ __forceinline__ void fourstep_half(cplx<T>* v, cplx<T>* buf, const cplx<T>* __restrict__ tw2, int n2, int slot) {
-    constexpr int E = Shape<M, S>::E, G = Shape<M, S>::G, P = G + 2;
-    static_assert(G == 2 * E, "two lanes per transpose row");
+__device__ __forceinline__ void fourstep_split(cplx<T>* v, cplx<T>* buf, const cplx<T>* __restrict__ tw2, int n2, int slot) {
+    constexpr int E = Shape<M, S>::E, G = Shape<M, S>::G, R = G / E, P = G + R;
+    static_assert(R == 2 || R == 4, "two or four lanes per transpose row");
     DIF<T, E, INV, 0>::run(v);                   // v[r] = X1[k1 = bitrev(r)] of column n2
 #pragma unroll
     for (int r = 0; r < E; ++r) {
@@ -259,19 +265,39 @@ __device__ __forceinline__ void fourstep_half(cplx<T>* v, cplx<T>* buf, const cp
         buf[k1 * P + n2] = INV ? cmulc(v[r], w) : cmul(v[r], w);
     }
     line_sync<G>(slot);
-    const int k1 = n2 >> 1, h = n2 & 1;
+    const int k1 = n2 / R, q = n2 % R;
 #pragma unroll
-    for (int t = 0; t < E; ++t) v[t] = buf[k1 * P + 2 * t + h];
+    for (int t = 0; t < E; ++t) v[t] = buf[k1 * P + R * t + q];
     line_sync<G>(slot);
-    DIF<T, E, INV, 0>::run(v);                   // v[r] = Y_h[k = bitrev(r)]
+    DIF<T, E, INV, 0>::run(v);                   // v[r] = Y_q[k = bitrev(r)]
+    constexpr unsigned FULL = 0xffffffffu;
+    if constexpr (R == 2) {
 #pragma unroll
-    for (int r = 0; r < E; ++r) {
-        const int k = bitrev<E>(r);
-        const T px = __shfl_xor_sync(0xffffffffu, v[r].x, 1);
-        const T py = __shfl_xor_sync(0xffffffffu, v[r].y, 1);
-        const cplx<T> y0 = h ? mk(px, py) : v[r];
-        const cplx<T> y1 = twid<T, G, INV>(h ? v[r] : mk(px, py), k);
-        buf[k1 + E * (k + E * h)] = h ? y0 - y1 : y0 + y1;
+        for (int r = 0; r < E; ++r) {
+            const int k = bitrev<E>(r);
+            const T px = __shfl_xor_sync(FULL, v[r].x, 1);
+            const T py = __shfl_xor_sync(FULL, v[r].y, 1);
+            const cplx<T> y0 = q ? mk(px, py) : v[r];
+            const cplx<T> y1 = twid<T, G, INV>(q ? v[r] : mk(px, py), k);
+            buf[k1 + E * (k + E * q)] = q ? y0 - y1 : y0 + y1;
+        }
+    } else {
+        const int s = ((q & 1) << 1) | (q >> 1);  // output index of this lane
+#pragma unroll
+        for (int r = 0; r < E; ++r) {
+            const int k = bitrev<E>(r);
+            const cplx<T> w = tw2[k * G + E * q];            // W_G^{q k}
+            cplx<T> u = INV ? cmulc(v[r], w) : cmul(v[r], w);
+            // pairs (q, q ^ 2): lanes q < 2 keep U_q + U_{q^2}, lanes q >= 2 keep U_{q^2} - U_q
+            T px = __shfl_xor_sync(FULL, u.x, 2), py = __shfl_xor_sync(FULL, u.y, 2);
+            u = (q & 2) ? mk(px - u.x, py - u.y) : mk(u.x + px, u.y + py);
+            // pairs (q, q ^ 1): even lanes X = A_q + w4 A_{q^1}, odd lanes X = A_{q^1} - w4 A_q,
+            // w4 = 1 for q < 2 and W_4 (-i; +i for INV) for q >= 2
+            px = __shfl_xor_sync(FULL, u.x, 1); py = __shfl_xor_sync(FULL, u.y, 1);
+            const cplx<T> a = (q & 1) ? mk(px, py) : u, b = (q & 1) ? u : mk(px, py);
+            const cplx<T> wb = (q & 2) ? (INV ? mk(-b.y, b.x) : mk(b.y, -b.x)) : b;
+            buf[k1 + E * (k + E * s)] = (q & 1) ? a - wb : a + wb;
+        }
     }
     line_sync<G>(slot);
 }
@@ -281,7 +307,7 @@ __device__ __forceinline__ void fourstep_half(cplx<T>* v, cplx<T>* buf, const cp
 template <typename T, int M, bool INV, bool SWZ = false, int S = 0>
 __device__ __forceinline__ void fourstep(cplx<T>* v, cplx<T>* buf, const cplx<T>* __restrict__ tw2, int n2, int slot) {
   if constexpr (Shape<M, S>::E < Shape<M, S>::G) {
-    fourstep_half<T, M, INV, S>(v, buf, tw2, n2, slot);
+    fourstep_split<T, M, INV, S>(v, buf, tw2, n2, slot);
   } else {
     constexpr int E = Shape<M, S>::E, G = Shape<M, S>::G, J = E / G;
     DIF<T, E, INV, 0>::run(v);

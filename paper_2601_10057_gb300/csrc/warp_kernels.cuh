@@ -18,21 +18,26 @@ namespace ccm {
 constexpr int kWarps = 8;
 
 // Exact (double-float) sum over the G lanes of one line: inside the warp for
-// G <= 32; for G = 64 each warp sums its half, the halves go through `sm`
-// (two float2 per line slot) and both warps add them in the same order.
+// G <= 32; for G = 32 W each of the W warps sums its part, the parts go
+// through `sm` (W float2 per line slot) and every warp adds them in the same
+// order.
 template <int G>
 __device__ __forceinline__ double line_sum_exact(float hi, float lo, int slot, float2* sm) {
     if constexpr (G <= 32) {
         return group_sum_exact<G>(hi, lo);
     } else {
+        constexpr int W = G / 32;
         const float2 h = group_sum_df<32>(hi, lo);
-        const int half = (threadIdx.x >> 5) & 1;
-        if ((threadIdx.x & 31) == 0) sm[2 * slot + half] = h;
+        const int part = (threadIdx.x >> 5) % W;
+        if ((threadIdx.x & 31) == 0) sm[W * slot + part] = h;
         wf::line_sync<G>(slot);
-        float2 a = sm[2 * slot];
-        const float2 b = sm[2 * slot + 1];
-        wf::line_sync<G>(slot);        // the two slots may be written again by a later call
-        df_add2(a.x, a.y, b.x, b.y);
+        float2 a = sm[W * slot];
+#pragma unroll
+        for (int w = 1; w < W; ++w) {
+            const float2 b = sm[W * slot + w];
+            df_add2(a.x, a.y, b.x, b.y);
+        }
+        wf::line_sync<G>(slot);        // the slots may be written again by a later call
         return (double)a.x + (double)a.y;
     }
 }
@@ -359,10 +364,14 @@ kw_coldct_gram_split(const float* __restrict__ in, float* __restrict__ spec, dou
 // Phase 1 (all threads): gather the spectra, combine, divide, pre-process
 // into the line buffers.  Phase 2 (per line): inverse four-step FFT and
 // unpack in place.  Phase 3: transposed write from the buffers.
-// Line shape of the inverse transforms (the recovery and inverse-row
-// kernels): 2048-point lines over two warps of 32 values per lane (variant
-// 1), the others as in the forward transforms.
-template <int M> __host__ __device__ constexpr int inv_shape() { return M == 2048 ? 1 : 0; }
+// Line shapes of the inverse transforms (variant 1: 32 values per lane):
+// the recovery kernel takes 2048-point lines over two warps, the inverse-row
+// kernel 2048- and 4096-point lines over two and four warps; the other lines
+// are shaped as in the forward transforms.  (At 4096 points the recovery
+// kernel keeps 64 x 64: four warps per line would leave it one spectral row
+// per CTA.)
+template <int M> __host__ __device__ constexpr int comb_shape() { return M == 2048 ? 1 : 0; }
+template <int M> __host__ __device__ constexpr int irow_shape() { return M == 2048 || M == 4096 ? 1 : 0; }
 
 template <int M, bool GRP = false>
 __global__ void __launch_bounds__(kWarps * 32)
@@ -371,7 +380,7 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
               const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc,
               DevScalars* __restrict__ dsc, int anchor_mass,
               const __grid_constant__ GroupArgs<GRP> ga, int bps) {
-    constexpr int SV = inv_shape<M>();
+    constexpr int SV = comb_shape<M>();
     using Gm = WGeo<M, SV>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS / 2, NU = (M / 2 + G - 1) / G;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -433,7 +442,7 @@ kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
         if (k > 0) b[M - k] = zMk;
     }
     __syncthreads();
-    __shared__ float2 lsum[2 * Gm::SLOTS];
+    __shared__ float2 lsum[4 * Gm::SLOTS];
     int n2, slot;                                        // line = slot: row slot/2, field slot%2
     wf::lane_geo<M, SV>(n2, slot);
     cplx<float>* buf = bufs + (size_t)slot * Gm::BUFP;
@@ -509,14 +518,14 @@ template <int M> __host__ __device__ constexpr int inv_warps() {
     return M == 1024 ? 9 : M >= 2048 ? 4 : M == 512 ? 4 : M == 256 ? 2 : 1;
 }
 template <int M> __host__ __device__ constexpr int inv_min_ctas() {
-    return M == 2048 ? 4 : M == 1024 || M > 2048 ? 3 : 4;
+    return M == 2048 || M == 4096 ? 4 : M == 1024 ? 3 : 4;
 }
 
 template <int M> struct InvGeo {
-    using W = WGeo<M, inv_shape<M>()>;
+    using W = WGeo<M, irow_shape<M>()>;
     static constexpr int WARPS = inv_warps<M>();
     static constexpr int LINES = WARPS * W::LPW / W::WPL;     // lines per CTA
-    static constexpr int BUF = wf::buf_len<M, true, inv_shape<M>()>();   // unpadded, swizzled transpose
+    static constexpr int BUF = wf::buf_len<M, true, irow_shape<M>()>();   // swizzled or split-row transpose
     static constexpr size_t smem_bytes() { return (size_t)LINES * BUF * sizeof(cplx<float>); }
 };
 
@@ -528,7 +537,7 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
         const float* __restrict__ psn, const float* __restrict__ pso, int bdf1,
         const DevScalars* __restrict__ dsc, int anchor_mass,
         const __grid_constant__ GroupArgs<GRP> ga, int bps) {
-    constexpr int SV = inv_shape<M>();
+    constexpr int SV = irow_shape<M>();
     using Gm = WGeo<M, SV>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, L = InvGeo<M>::LINES, NU = (M / 2 + G - 1) / G;
     int bx = blockIdx.x;
@@ -544,22 +553,8 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
     const int l0 = bx * L;                               // first line of this CTA
-    if constexpr (M == 2048) {
-        // the levels of the final update, into L2 while the lines are
-        // transformed (three 4-line CTAs per SM leave this kernel short of
-        // loads in flight: 396 -> 375 us at N = 4096; at M = 4096 it costs
-        // time, 1450 -> 1475 us, and at M = 1024 it did too, 41 -> 48 us)
-        if (threadIdx.x < 2 * L) {
-            const int gq = l0 + (threadIdx.x >> 1);
-            if (gq < 2 * N) {
-                const int f = gq & 1;
-                const float* lv = (threadIdx.x & 1) ? (f ? pso : pho) : (f ? psn : phn);
-                prefetch_l2(lv + (size_t)(gq >> 1) * N, N * sizeof(float));
-            }
-        }
-    }
     constexpr int PAIRS = M / 2 + 1;
-    constexpr int UNR = M >= 2048 ? 8 : 4;    // loads in flight: 8 at 64 values per lane (12 warps per SM)
+    constexpr int UNR = M >= 2048 ? 8 : 4;    // loads in flight per thread in the pre-process
 #pragma unroll UNR
     for (int q = threadIdx.x; q < L * PAIRS; q += blockDim.x) {
         const int l = q / PAIRS, k = q % PAIRS;
@@ -574,7 +569,7 @@ kw_irow(const float* __restrict__ in, float* __restrict__ phi_new, float* __rest
         if (k > 0) b[M - k] = zMk;
     }
     __syncthreads();
-    __shared__ float2 lsum[2 * L];
+    __shared__ float2 lsum[4 * L];
     int n2, slot;
     wf::lane_geo<M, SV>(n2, slot);
     const int gl = l0 + slot;
