@@ -194,7 +194,7 @@ public:
                                                                        nullptr, nullptr, SpecCoefF{}, ga, bcol);
         k_solve<float2, true><<<kSolveBlocks * n, kSolveThreads, 0, s>>>(nullptr, 0, nullptr, 0, nullptr, nullptr,
                                                                          SolveCoef{}, ga, kSolveBlocks);
-        kw_comb_icolT<MM, true><<<bcomb * n, kWarps * 32, wsm_comb, s>>>(nullptr, nullptr, nullptr, wf::PairTwTab{},
+        kw_comb_icolT<MM, true><<<bcomb * n, comb_warps<MM>() * 32, wsm_comb, s>>>(nullptr, nullptr, nullptr, wf::PairTwTab{},
                                                                         nullptr, nullptr, SpecCoefF{}, nullptr, 1, ga, bcomb);
         kw_irow<MM, true><<<birow * n, InvGeo<MM>::WARPS * 32, wsm_irow, s>>>(nullptr, nullptr, nullptr, nullptr,
             wf::PairTwTab{}, nullptr, nullptr, nullptr, nullptr, 0, nullptr, 1, ga, birow);
@@ -737,7 +737,7 @@ public:
     }
     template <int MM> int setup_warp() {
         using Gm = WGeo<MM>;
-        using Gc = WGeo<MM, comb_shape<MM>()>;      // the recovery kernel's line shape
+        using Gc = WGeo<MM, comb_shape<MM>(), comb_warps<MM>()>;   // the recovery kernel's geometry
         using Gv = WGeo<MM, 1>;                     // the variant of the inverse kernels
         if (int r = make_tw2(MM, Gm::E, Gm::G, &tw2)) return r;
         if constexpr (comb_shape<MM>() != 0 || irow_shape<MM>() != 0) {
@@ -878,7 +878,7 @@ public:
     template <int MM>
     void launch_warp_inverse(const SpecCoef& s, int anchor) {
         SpecCoefF sf{(float)s.C1, (float)s.C2, (float)s.C3, (float)s.Ct, (float)s.lam};
-        kw_comb_icolT<MM><<<N / wRT4, kWarps * 32, wsm_comb, st>>>(reinterpret_cast<const float*>(bufA),
+        kw_comb_icolT<MM><<<N / wRT4, comb_warps<MM>() * 32, wsm_comb, st>>>(reinterpret_cast<const float*>(bufA),
             reinterpret_cast<float*>(bufB), comb_shape<MM>() ? tw2i : tw2, pair_tab(twI), evf, evp, sf, sc, anchor,
             GroupArgs<false>{}, 0);
         mark(4);

@@ -57,11 +57,11 @@ template <int M> struct SpecRow {
     static constexpr size_t KS = (size_t)7 * RS;      // next kx
 };
 
-template <int M, int S = 0> struct WGeo {
+template <int M, int S = 0, int WARPS = kWarps> struct WGeo {
     static constexpr int E = wf::Shape<M, S>::E, G = wf::Shape<M, S>::G;
     static constexpr int WPL = G > 32 ? G / 32 : 1;     // warps per line
     static constexpr int LPW = G > 32 ? 1 : 32 / G;     // lines per warp (one line spans WPL warps)
-    static constexpr int SLOTS = kWarps * LPW / WPL;    // line buffers per CTA
+    static constexpr int SLOTS = WARPS * LPW / WPL;     // line buffers per CTA
     // complex per buffer: unpadded, XOR-swizzled transpose (M + 2), so that
     // three 8-line CTAs of the forward kernels fit the 196 KB shared-memory
     // configuration; padded rows (G + 1 values) for the recovery kernel (two
@@ -365,23 +365,23 @@ kw_coldct_gram_split(const float* __restrict__ in, float* __restrict__ spec, dou
 // into the line buffers.  Phase 2 (per line): inverse four-step FFT and
 // unpack in place.  Phase 3: transposed write from the buffers.
 // Line shapes of the inverse transforms (variant 1: 32 values per lane):
-// the recovery kernel takes 2048-point lines over two warps, the inverse-row
-// kernel 2048- and 4096-point lines over two and four warps; the other lines
-// are shaped as in the forward transforms.  (At 4096 points the recovery
-// kernel keeps 64 x 64: four warps per line would leave it one spectral row
-// per CTA.)
-template <int M> __host__ __device__ constexpr int comb_shape() { return M == 2048 ? 1 : 0; }
+// 2048- and 4096-point lines over two and four warps in both inverse
+// kernels; the other lines are shaped as in the forward transforms.  The
+// recovery kernel runs sixteen warps per CTA at 4096 points, so that a CTA
+// still holds two spectral rows (8-byte transposed stores).
+template <int M> __host__ __device__ constexpr int comb_shape() { return M == 2048 || M == 4096 ? 1 : 0; }
 template <int M> __host__ __device__ constexpr int irow_shape() { return M == 2048 || M == 4096 ? 1 : 0; }
+template <int M> __host__ __device__ constexpr int comb_warps() { return M == 4096 ? 16 : kWarps; }
 
 template <int M, bool GRP = false>
-__global__ void __launch_bounds__(kWarps * 32)
+__global__ void __launch_bounds__(comb_warps<M>() * 32)
 kw_comb_icolT(const float* __restrict__ spec, float* __restrict__ out,
               const cplx<float>* __restrict__ tw2, wf::PairTwTab twI,
               const float* __restrict__ evf, const float4* __restrict__ evp, SpecCoefF sc,
               DevScalars* __restrict__ dsc, int anchor_mass,
               const __grid_constant__ GroupArgs<GRP> ga, int bps) {
     constexpr int SV = comb_shape<M>();
-    using Gm = WGeo<M, SV>;
+    using Gm = WGeo<M, SV, comb_warps<M>()>;
     constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS / 2, NU = (M / 2 + G - 1) / G;
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
