@@ -138,7 +138,7 @@ int ccmsav_set_state_device(ccmsav_t* h, int sim, const void* phi, const void* p
  * synchronising call (ccmsav_sync, get_state, energy, mass, get_aux).
  * Several simulations: their BDF2 steps run three at a time from one CUDA
  * graph per rotation phase of the three time levels.  Inside it, FP32
- * simulations of the same N on the warp-FFT kernels (N = 128 .. 4096, no
+ * simulations of the same N on the warp-FFT kernels (N = 128 .. 2048, no
  * CCMSAV_CLASSICAL, no CCMSAV_TRACK_ENERGY) share each kernel launch (one
  * launch per kernel, step and N for the whole group); the others run their
  * own launches concurrently.  Every simulation's results are the same bits
