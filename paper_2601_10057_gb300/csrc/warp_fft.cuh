@@ -11,10 +11,11 @@
 //      written to the buffer in natural order.
 // One smem round trip per stage pair instead of one per radix-8 stage, no
 // block barriers (only __syncwarp), and 32 independent values per lane.
-// Supported lines: M in {64, ..., 4096} (N = 2M in 128 .. 8192);
-// G = 2^floor(log2(M)/2), E = M / G <= 64.  A group of G = 64 lanes spans
-// two warps (M = 4096): its lanes synchronise through a named barrier of the
-// line (id 1 + line slot, 64 threads) instead of __syncwarp.
+// Supported lines: M in {64, ..., 4096} (N = 2M in 128 .. 8192); the shapes
+// E x G are listed below (Shape).  A group of G = 32 W lanes (W = 2, 4)
+// spans W warps: its lanes synchronise through a named barrier of the line
+// (id 1 + line slot, G threads) instead of __syncwarp.  Shapes with E < G
+// take fourstep_split for steps 3-4.
 #pragma once
 #include <type_traits>
 #include "dct_device.cuh"
@@ -191,7 +192,8 @@ template <> struct Shape<2048, 1> { static constexpr int E = 32, G = 64; };
 template <> struct Shape<4096, 1> { static constexpr int E = 32, G = 128; };
 
 // Lane n2 of its line's group and the line's slot in the CTA: G <= 32 puts
-// 32 / G lines in a warp; G = 64 spreads a line over two consecutive warps.
+// 32 / G lines in a warp; G = 64, 128 spreads a line over 2, 4 consecutive
+// warps.
 template <int M, int S = 0> __device__ __forceinline__ void lane_geo(int& n2, int& slot) {
     constexpr int G = Shape<M, S>::G;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -205,8 +207,8 @@ template <int M, int S = 0> __device__ __forceinline__ void lane_geo(int& n2, in
 }
 
 // Barrier of one line's lane group: the warp's own lanes for G <= 32, the
-// two warps of the line (named barrier 1 + slot; every one of their 64
-// threads arrives) for G = 64.
+// warps of the line (named barrier 1 + slot; every one of their G threads
+// arrives) for G = 64, 128.
 template <int G> __device__ __forceinline__ void line_sync(int slot) {
     if constexpr (G <= 32) {
         __syncwarp();

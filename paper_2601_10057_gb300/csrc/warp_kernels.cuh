@@ -1,5 +1,5 @@
 // warp_kernels.cuh -- FP32 step kernels built on the warp-level line FFT
-// (N = 2M in 128 .. 2048).  Same data flow as the block-FFT kernels of
+// (N = 2M in 128 .. 8192).  Same data flow as the block-FFT kernels of
 // step_kernels.cuh:
 //   kw_rowdct_T    forward DCT-II along x, transposed write (RT rows per CTA)
 //   kw_coldct_gram forward DCT-II along y of the 8 fields of KC spectral rows,
