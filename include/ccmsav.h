@@ -139,7 +139,8 @@ int ccmsav_set_state_device(ccmsav_t* h, int sim, const void* phi, const void* p
  * Several simulations: their BDF2 steps run three at a time from one CUDA
  * graph per rotation phase of the three time levels.  Inside it, FP32
  * simulations of the same N on the warp-FFT kernels (N = 128 .. 2048, no
- * CCMSAV_CLASSICAL, no CCMSAV_TRACK_ENERGY) share each kernel launch (one
+ * CCMSAV_CLASSICAL, CCMSAV_TRACK_ENERGY or CCMSAV_BDF1_ALWAYS) share each
+ * kernel launch (one
  * launch per kernel, step and N for the whole group); the others run their
  * own launches concurrently.  Every simulation's results are the same bits
  * as a run of that simulation alone.

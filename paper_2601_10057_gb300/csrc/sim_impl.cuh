@@ -149,11 +149,13 @@ public:
     void count_steps_grouped(int n3) override { steps_taken += n3; }
 
     // ---- grouped launches -------------------------------------------------
-    // FP32 warp path with one warp or less per line (N <= 2048), no classical mode, no
-    // energy tracking: simulations of the same M share each kernel launch.
+    // FP32 warp path with one warp or less per line (N <= 2048), BDF2 steps (not
+    // CCMSAV_BDF1_ALWAYS), no classical mode, no energy tracking: simulations of
+    // the same M share each kernel launch.
     int group_key() const override {
         if constexpr (std::is_same<T, float>::value)
-            if (warp_path && !classical && !(flags & CCMSAV_TRACK_ENERGY) && M >= 64 && M <= 1024) return M;
+            if (warp_path && !classical && !(flags & (CCMSAV_TRACK_ENERGY | CCMSAV_BDF1_ALWAYS)) && M >= 64 && M <= 1024)
+                return M;
         return 0;
     }
     size_t batch_args_bytes() const override { return sizeof(BatchArgs); }

@@ -381,6 +381,27 @@ def test_grouped_launches_match_single_runs():
     sim.close()
 
 
+def test_bdf1_mode_batch_matches_single_runs():
+    """A batched handle in the BDF1 product mode (CCMSAV_BDF1_ALWAYS: every
+    step first order, so its simulations stay out of the grouped launches,
+    which take BDF2 steps) gives each simulation's own bits."""
+    ws = [I.workload("one_vesicle", N=128, dt=1e-5), I.workload("ellipse_shrink", N=128)]
+    sim = cc.Simulation(None, [w.N for w in ws], per_sim=[w.params for w in ws], precision="fp32",
+                        bdf1_always=True)
+    for k, w in enumerate(ws):
+        sim.set_state(w.phi0, w.psi0, sim=k)
+    sim.step(7)
+    for k, w in enumerate(ws):
+        phi, psi = sim.state(sim=k)
+        solo = cc.Simulation(w.params, w.N, precision="fp32", bdf1_always=True)
+        solo.set_state(w.phi0, w.psi0)
+        solo.step(7)
+        phi1, psi1 = solo.state()
+        solo.close()
+        assert np.array_equal(phi, phi1) and np.array_equal(psi, psi1), f"simulation {k}"
+    sim.close()
+
+
 _FP32_1000 = {}
 
 
