@@ -48,7 +48,11 @@ extern "C" {
 #define CCMSAV_ESTATE      -4   /* call out of order (e.g. step before set_state) */
 #define CCMSAV_ENONFINITE  -5   /* NaN/Inf input or state, a SAV radicand <= 0,
                                    or a face mobility M_psi(A phi*) <= 0 */
-#define CCMSAV_ETIMEOUT    -6   /* a bounded device-side wait gave up */
+#define CCMSAV_ETIMEOUT    -6   /* reserved for a bounded device-side wait that
+                                   gives up; no kernel of this library waits on
+                                   another (stream order and last-block arrival
+                                   counters order the phases), so no call
+                                   returns it */
 
 /* Precision of the field arithmetic. */
 #define CCMSAV_FP64       0     /* fields, stencils, DCTs and reductions in FP64 */

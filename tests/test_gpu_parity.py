@@ -381,6 +381,34 @@ def test_grouped_launches_match_single_runs():
     sim.close()
 
 
+def test_launch_group_size_does_not_change_results():
+    """The same batch (four N = 128 and two N = 256 FP32 simulations) with
+    no grouping, groups of two (2^15 points) and whole-size groups ends with
+    the same bits, and the launch count follows the grouping."""
+    ws = ([I.one_vesicle_circle(N=128, seed=300 + i, dt=1e-5, precision="fp32") for i in range(4)]
+          + [I.workload("ellipse_shrink", N=256), I.workload("one_vesicle", N=256, dt=1e-5)])
+    out, launches = {}, {}
+    for pts in (0, 1 << 15, 1 << 26):
+        sim = cc.Simulation(None, [w.N for w in ws], per_sim=[w.params for w in ws], precision="fp32")
+        sim.set_group_points(pts)
+        assert sim.group_points() == pts
+        for k, w in enumerate(ws):
+            sim.set_state(w.phi0, w.psi0, sim=k)
+        sim.step(1)
+        l0 = sim.launches()
+        sim.step(6)
+        launches[pts] = sim.launches() - l0
+        out[pts] = [sim.state(sim=k) for k in range(len(ws))]
+        sim.close()
+    for pts in (1 << 15, 1 << 26):
+        for k in range(len(ws)):
+            assert np.array_equal(out[pts][k][0], out[0][k][0]) and np.array_equal(out[pts][k][1], out[0][k][1])
+    # six launches per step for each group and each simulation outside one:
+    # no grouping (6 simulations); 2^15 points (two N = 128 pairs, the two
+    # N = 256 grids of 2^16 points each run alone); 2^26 (one group per N)
+    assert launches == {0: 6 * 6 * 6, 1 << 15: 6 * 6 * 4, 1 << 26: 6 * 6 * 2}, launches
+
+
 def test_bdf1_mode_batch_matches_single_runs():
     """A batched handle in the BDF1 product mode (CCMSAV_BDF1_ALWAYS: every
     step first order, so its simulations stay out of the grouped launches,
