@@ -409,6 +409,58 @@ def test_launch_group_size_does_not_change_results():
     assert launches == {0: 6 * 6 * 6, 1 << 15: 6 * 6 * 4, 1 << 26: 6 * 6 * 2}, launches
 
 
+def test_group_points_changed_between_steps():
+    """Grouping switched off and on again between steps (the batch graphs are
+    captured anew each time) leaves every simulation bit-identical to a run
+    of its own."""
+    ws = [I.one_vesicle_circle(N=256, seed=500 + i, dt=1e-5, precision="fp32") for i in range(3)]
+    sim = cc.Simulation(None, [w.N for w in ws], per_sim=[w.params for w in ws], precision="fp32")
+    for k, w in enumerate(ws):
+        sim.set_state(w.phi0, w.psi0, sim=k)
+    for pts, n in ((1 << 21, 4), (0, 2), (1 << 21, 5)):
+        sim.set_group_points(pts)
+        sim.step(n)
+    sim.sync()
+    for k, w in enumerate(ws):
+        phi, psi = sim.state(sim=k)
+        solo = cc.Simulation(w.params, w.N, precision="fp32")
+        solo.set_state(w.phi0, w.psi0)
+        solo.step(11)
+        phi1, psi1 = solo.state()
+        solo.close()
+        assert np.array_equal(phi, phi1) and np.array_equal(psi, psi1), f"simulation {k}"
+    sim.close()
+
+
+def test_largest_launch_group():
+    """65 FP32 simulations of N = 128 with no limit on the group's points: the
+    first 64 (the most one launch's parameter block carries) share every
+    launch and the last runs its own, so a graph-launched step is 12
+    launches; members across the group, and the one outside it, end
+    bit-identical to runs of their own."""
+    ws = [I.one_vesicle_circle(N=128, seed=900 + i, dt=1e-5, precision="fp32", ratio=0.8 + 0.01 * i)
+          for i in range(65)]
+    sim = cc.Simulation(None, [w.N for w in ws], per_sim=[w.params for w in ws], precision="fp32")
+    sim.set_group_points(1 << 30)
+    for k, w in enumerate(ws):
+        sim.set_state(w.phi0, w.psi0, sim=k)
+    sim.step(1)
+    l0 = sim.launches()
+    sim.step(6)           # two graph launches of three steps each
+    sim.sync()
+    assert sim.launches() - l0 == 6 * 6 * 2, sim.launches() - l0
+    for k in (0, 1, 31, 62, 63, 64):
+        w = ws[k]
+        phi, psi = sim.state(sim=k)
+        solo = cc.Simulation(w.params, w.N, precision="fp32")
+        solo.set_state(w.phi0, w.psi0)
+        solo.step(7)
+        phi1, psi1 = solo.state()
+        solo.close()
+        assert np.array_equal(phi, phi1) and np.array_equal(psi, psi1), f"simulation {k}"
+    sim.close()
+
+
 def test_bdf1_mode_batch_matches_single_runs():
     """A batched handle in the BDF1 product mode (CCMSAV_BDF1_ALWAYS: every
     step first order, so its simulations stay out of the grouped launches,
