@@ -73,16 +73,17 @@ template <int M, int S = 0, int WARPS = kWarps> struct WGeo {
 };
 
 // ------------------------------------------------------------------ kw_rowdct_T
-// SLOTS rows of field blockIdx.y per CTA (one line per lane group).  The
-// post-processed DCT row replaces the line's complex buffer in place, so the
-// buffers double as the staging area of the transposed write.
+// SLOTS rows of field blockIdx.y per CTA (one line per lane group).  Each
+// line's natural-order half-length spectrum stays in its buffer; the DCT
+// post-process reads it from there pair by pair while writing the transposed
+// output, so the buffers double as the staging area of that write.
 template <int M, bool GRP = false>
 __global__ void __launch_bounds__(kWarps * 32, M <= 1024 ? 3 : 1)
 kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
             const cplx<float>* __restrict__ tw2, wf::PairTwTab twF, int ahead,
             const __grid_constant__ GroupArgs<GRP> ga, int bps) {
     using Gm = WGeo<M>;
-    constexpr int N = 2 * M, G = Gm::G, E = Gm::E, RT = Gm::SLOTS, NP = (M / 2 + G) / G;
+    constexpr int N = 2 * M, E = Gm::E, RT = Gm::SLOTS;
     extern __shared__ __align__(16) unsigned char smraw[];
     cplx<float>* bufs = reinterpret_cast<cplx<float>*>(smraw);
     const size_t NN = (size_t)N * N;
@@ -107,52 +108,56 @@ kw_rowdct_T(const float* __restrict__ in, float* __restrict__ out,
         wf::pack_fwd_global<M>(in + CCM_IXW(f * NN + (size_t)(y0 + slot) * N, N, NF * NN), v, n2);
         wf::fourstep<float, M, false, true>(v, buf, tw2, n2, slot);
     }
-    // DCT post-process in place, one pair at a time: pair k reads the complex
-    // slots k and M-k and writes its four modes back into them (slot k: modes
-    // k, N-k; slot M-k: modes M-k, M+k; pair 0: modes 0, M in slot 0; pair
-    // M/2: modes M/2, 3M/2 in slot M/2).  No two pairs share a slot, so no
-    // pair has to be held in registers while another is written.  The
-    // pairs go in batches of PB: all loads of a batch are issued before its
-    // stores (the compiler cannot see that the slots are disjoint).
-    constexpr int PB = 8;
-#pragma unroll
-    for (int i0 = 0; i0 < NP; i0 += PB) {
-        cplx<float> A[PB], B[PB];
-#pragma unroll
-        for (int b = 0; b < PB; ++b) {
-            const int k = n2 + G * (i0 + b);
-            if (i0 + b < NP && k <= M / 2) { A[b] = buf[k]; B[b] = buf[(M - k) & (M - 1)]; }
-        }
-#pragma unroll
-        for (int b = 0; b < PB; ++b) {
-            const int k = n2 + G * (i0 + b);
-            if (i0 + b < NP && k <= M / 2) {
-                const Quad<float> X = wf::post_pair_lean(A[b], B[b], wf::load_pair_tw<false>(twF, k));
-                if (k == 0) {
-                    buf[0] = mk(X.xk, X.xMk);
-                } else {
-                    buf[k] = mk(X.xk, X.xNk);
-                    if (k < M / 2) buf[M - k] = mk(X.xMk, X.xMpk);
-                }
-            }
-        }
-    }
     __syncthreads();
-    // transposed write: slot j of each row holds modes j and N - j (j = 0:
-    // modes 0 and M); one float4 of 4 rows per mode
+    // DCT post-process fused into the transposed write.  Item (r4, k) takes
+    // the pair k (slots k and M-k of the natural-order spectra) of the rows
+    // 4 r4 .. 4 r4 + 3 and writes its four modes k, N-k, M-k, M+k, each as one
+    // float4 of the four rows; the item k = 0 also takes the pair M/2, so
+    // that every item loads eight slots and stores four float4 (pair 0 gives
+    // the modes 0 and M, pair M/2 the modes M/2 and 3M/2).  Consecutive
+    // threads take the two halves of one 32-byte row segment when R4 = 2.
     const float2* stage = reinterpret_cast<const float2*>(bufs);
     constexpr int BC = Gm::BUF;                      // float2 per line buffer
     float* dst = out + f * NN + y0;
     constexpr int R4 = RT / 4;
-    for (int q = threadIdx.x; q < R4 * M; q += blockDim.x) {
-        const int r4 = q % R4, j = q / R4;
-        const float2* sp = stage + (size_t)(4 * r4) * BC + j;
-        const float2 v0 = sp[0], v1 = sp[BC], v2 = sp[2 * BC], v3 = sp[3 * BC];
-        const int mb = j == 0 ? M : N - j;
-        if (!CCM_OKW(f * NN + y0 + (size_t)j * N + 4 * r4, 4, NF * NN) ||
-            !CCM_OKW(f * NN + y0 + (size_t)mb * N + 4 * r4, 4, NF * NN)) continue;
-        *reinterpret_cast<float4*>(dst + (size_t)j * N + 4 * r4) = make_float4(v0.x, v1.x, v2.x, v3.x);
-        *reinterpret_cast<float4*>(dst + (size_t)mb * N + 4 * r4) = make_float4(v0.y, v1.y, v2.y, v3.y);
+    static_assert(RT % 4 == 0, "rows of a CTA in groups of four");
+    auto put = [&](int mode, int r4, float a, float b, float c, float d) {
+        if (CCM_OKW(f * NN + y0 + (size_t)mode * N + 4 * r4, 4, NF * NN))
+            *reinterpret_cast<float4*>(dst + (size_t)mode * N + 4 * r4) = make_float4(a, b, c, d);
+    };
+    for (int q = threadIdx.x; q < R4 * (M / 2); q += blockDim.x) {
+        const int r4 = q % R4, k = q / R4;
+        const float2* sp = stage + (size_t)(4 * r4) * BC;
+        const int ka = k == 0 ? M / 2 : M - k;       // second slot: M - k, or the pair M/2
+        cplx<float> A[4], B[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            const float2 a = sp[(size_t)r * BC + k], b = sp[(size_t)r * BC + ka];
+            A[r] = mk(a.x, a.y);
+            B[r] = mk(b.x, b.y);
+        }
+        if (k == 0) {
+            const wf::PairTw t0 = wf::load_pair_tw<false>(twF, 0), th = wf::load_pair_tw<false>(twF, M / 2);
+            Quad<float> X[4], Y[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                X[r] = wf::post_pair_lean(A[r], A[r], t0);
+                Y[r] = wf::post_pair_lean(B[r], B[r], th);
+            }
+            put(0, r4, X[0].xk, X[1].xk, X[2].xk, X[3].xk);
+            put(M, r4, X[0].xMk, X[1].xMk, X[2].xMk, X[3].xMk);
+            put(M / 2, r4, Y[0].xk, Y[1].xk, Y[2].xk, Y[3].xk);
+            put(N - M / 2, r4, Y[0].xNk, Y[1].xNk, Y[2].xNk, Y[3].xNk);
+        } else {
+            const wf::PairTw t = wf::load_pair_tw<false>(twF, k);
+            Quad<float> X[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) X[r] = wf::post_pair_lean(A[r], B[r], t);
+            put(k, r4, X[0].xk, X[1].xk, X[2].xk, X[3].xk);
+            put(N - k, r4, X[0].xNk, X[1].xNk, X[2].xNk, X[3].xNk);
+            put(M - k, r4, X[0].xMk, X[1].xMk, X[2].xMk, X[3].xMk);
+            put(M + k, r4, X[0].xMpk, X[1].xMpk, X[2].xMpk, X[3].xMpk);
+        }
     }
 }
 
