@@ -33,3 +33,26 @@ def test_source_hash_ignores_comments_and_whitespace():
     assert bench.code_text(a) == bench.code_text(b)
     assert bench.code_text(a) != bench.code_text(c)
     assert "//" not in bench.code_text(a) and "/*" not in bench.code_text(a)
+
+
+def test_phase_roofline_figures():
+    """The bench line's roofline: the dominant phase of the 40-pass schedule
+    (the one with the longest kernel time among phases that move field
+    data), its algorithmic bytes over that time against the peak; with the
+    per-kernel times of an N = 2048 FP32 step the stencil + row DCT phase
+    (12 passes of 4-byte fields) dominates."""
+    import bench
+    per_launch = {"k_stencil": 0.0633, "k_rowdct_T": 0.06278, "k_coldct_gram": 0.06363, "k_solve": 0.01434,
+                  "k_comb_icolT": 0.06049, "k_irow": 0.0409}
+    NN = 2048 * 2048
+    r = bench.phase_roofline(per_launch, NN, 4, 6783.8, "measured", "no_such_workload")
+    assert bench.STEP_PASSES_MIN_SCHEDULE == 40
+    assert r["phase"].startswith("K1") and r["kernels"] == ["k_stencil", "k_rowdct_T"]
+    assert r["alg_bytes_per_launch"] == 48 * NN
+    assert abs(r["achieved"] - 48 * NN / (0.12608e-3) / 1e9) < 0.1
+    assert abs(r["frac"] - r["achieved"] / 6783.8) < 1e-4
+    assert r["traffic"] is None and r["traffic_ratio_step"] is None    # no capture for that workload
+    # a solve-only slowdown never makes the zero-pass phase dominant
+    slow = dict(per_launch, k_solve=10.0)
+    assert bench.phase_roofline(slow, NN, 4, 6783.8, "measured", "x")["phase"].startswith("K1")
+    assert abs(r["phases"]["K5 inverse row DCT"]["frac"] - 16 * NN / 0.0409e-3 / 1e9 / 6783.8) < 1e-4
