@@ -83,3 +83,21 @@ def test_solver_calls_reject_null_handles(lib):
     assert cc.ccmsav_solver_sync(None) == cc.CCMSAV_EINVAL
     assert cc.ccmsav_solver_launch_count(None) == 0
     cc.ccmsav_solver_destroy(None)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built library the binding raises at once: there is no CPU
+    fallback for any call of the product path."""
+    import subprocess
+    import sys
+    code = ("import sys\n"
+            "from paper_2601_10057_gb300 import ccmsav as cc, inputs as I\n"
+            f"cc.LIB_PATH = {str(tmp_path / 'libccmsav.so')!r}\n"
+            "try:\n"
+            "    cc.Simulation(I.growth_params(), 64, precision='fp32')\n"
+            "except RuntimeError as e:\n"
+            "    print('raised', 'missing' in str(e)); sys.exit(0)\n"
+            "sys.exit(3)\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "raised True" in r.stdout
